@@ -1,0 +1,233 @@
+/*
+ * rfd.h -- C ABI of the GB300 ratio-filter dechirping library (librfd.so).
+ *
+ * Method: A. H. Nitz, K. Kacanja, K. Soni, "Beyond FINDCHIRP: ... Ratio-Filter
+ * Dechirping" (arXiv 2601.18835).  The data are matched-filtered once per reference
+ * template (Eq. 1: point-wise d conj(h_ref) / S, then an inverse FFT), giving a complex
+ * series q_ref.  Each target template's SNR series comes from a short complex FIR applied
+ * to q_ref (Eq. 3); the FIR is the windowed, truncated inverse transform of conj(h/h_ref)
+ * (Eq. 2, Sec. V).  The SNR series is reduced to |z|^2 threshold crossings and
+ * per-window maxima (Table II: peak find, trigger accumulation).
+ *
+ * Conventions for every call:
+ *   - Plain C99 types only.  Pointers named *_dev are device pointers, *_host host
+ *     pointers.  All data buffers are allocated and owned by the caller; the library owns
+ *     only contexts, plans and their workspaces, released by the matching *_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Every call
+ *     is stream-ordered and asynchronous unless its comment says it synchronises.
+ *   - Errors are return codes; nothing throws.  Arguments are checked before any launch
+ *     (RFD_ERR_ARG / RFD_ERR_SHAPE).  rfd_last_error() gives a message for the calling
+ *     thread's last failing call.
+ *   - Complex arrays are interleaved (re, im) float32 ("complex64") unless stated.
+ *   - Frequency grid: f_k = k df, df = fs / n, k = 0 .. n/2 (one-sided, n/2+1 bins).
+ *     n is a power of two, 2^10 <= n <= 2^22.  A template is non-zero for
+ *     ceil(f_low/df) <= k <= min(n/2 - 1, floor(f_ISCO/df)).
+ *   - Time index m = 0 .. n-1; every convolution is circular over the segment.
+ */
+#ifndef RFD_H
+#define RFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RFD_VERSION 1
+
+typedef enum {
+    RFD_OK = 0,
+    RFD_ERR_ARG = -1,          /* null pointer, bad enum, non-finite parameter */
+    RFD_ERR_SHAPE = -2,        /* sizes inconsistent or out of the supported range */
+    RFD_ERR_UNSUPPORTED = -3,  /* valid request this build does not implement */
+    RFD_ERR_CUDA = -4,         /* a CUDA runtime call failed (message has the CUDA error) */
+    RFD_ERR_NOMEM = -5,        /* workspace allocation failed */
+    RFD_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
+    RFD_ERR_OVERFLOW = -7      /* an output list was too small; the required size is returned */
+} rfd_status;
+
+/* Post-Newtonian phase terms beyond 0/1/1.5PN. */
+enum { RFD_PN_SO = 1,          /* aligned-spin 1.5PN spin-orbit term (beta) */
+       RFD_PN_TIDAL = 2 };     /* 5PN tidal term -(39/2) Lambda v^10 */
+
+/* Arithmetic of the ratio-filter contraction (and the layout of the q_ref buffer). */
+enum { RFD_PREC_FP32 = 0,      /* complex64 q_ref, FP32 CUDA-core FIR */
+       RFD_PREC_FP16X3 = 1,    /* fp16 hi+lo planes, 3-product tensor-core contraction */
+       RFD_PREC_BF16X3 = 2 };  /* bf16 hi+lo planes, 3-product tensor-core contraction */
+
+typedef struct rfd_ctx rfd_ctx;    /* opaque: device, FFT tables, workspaces */
+typedef struct rfd_plan rfd_plan;  /* opaque: one bank's filtering schedule and packed taps */
+
+/* Sampling grid of one data segment. */
+typedef struct {
+    double fs;          /* sample rate, Hz */
+    int64_t n;          /* samples per segment (power of two) */
+    double f_low;       /* lower frequency cutoff, Hz */
+    int32_t pn_flags;   /* RFD_PN_* bits applied to every template and reference */
+    int32_t reserved;   /* must be 0 */
+} rfd_grid;
+
+/* Intrinsic parameters of one TaylorF2 template (masses in solar masses). */
+typedef struct {
+    double m1, m2, chi1, chi2, lambda_tilde;
+} rfd_params;
+
+/* One candidate from the fused epilogue: the maximum over a run of samples that share a
+ * (template, window) pair.  key = (float bits of |z|^2) << 32 | (0xFFFFFFFF - t), so the
+ * larger key is the larger |z|^2 and, on equal |z|^2, the smaller t.  24 bytes. */
+typedef struct {
+    uint64_t key;
+    uint32_t j;         /* template index */
+    uint32_t w;         /* window index floor(t / window) */
+    float zr, zi;       /* complex SNR at that sample */
+} rfd_candidate;
+
+/* One trigger: the per-window maximum of |z|^2 above threshold.  20 bytes. */
+typedef struct {
+    int32_t j;          /* template index */
+    int32_t t;          /* sample index of the maximum, 0 .. n-1 */
+    float snr2;         /* |z|^2 at t */
+    float zr, zi;       /* complex SNR at t */
+} rfd_trigger;
+
+/* ------------------------------------------------------------------ housekeeping */
+int32_t rfd_version(void);
+const char *rfd_status_string(rfd_status s);
+/* Message of the calling thread's last failing call ("" if none).  Owned by the library,
+ * valid until the thread's next failing call. */
+const char *rfd_last_error(void);
+
+/* Number of kernels this library has launched in the process so far (all contexts). */
+int64_t rfd_kernel_launches(void);
+
+/* Create a context on CUDA device `device` (made current for the calling thread).
+ * The context is not thread-safe: use one per host thread. */
+rfd_status rfd_ctx_create(int32_t device, rfd_ctx **out);
+void rfd_ctx_destroy(rfd_ctx *ctx);
+
+/* Elements per reference row of a q_ref buffer: n + halo rounded up to a multiple of 64.
+ * A q_ref buffer holds n_ref * 8 * rfd_qref_ld(n, halo) bytes in every precision. */
+int64_t rfd_qref_ld(int64_t n, int32_t halo);
+
+/* ------------------------------------------------------------------ templates
+ * TaylorF2 templates (the h(f) of Eq. 1) evaluated with FP64 phase:
+ *   h(f_k) = f_k^(-7/6) exp(-i Psi(f_k)),
+ *   Psi = -pi/4 + 3/(128 eta v^5) [1 + (3715/756 + 55 eta/9) v^2 + (4 beta - 16 pi) v^3
+ *                                  - (39/2) Lambda v^10],  v = (pi M f)^(1/3),
+ * zero outside the template's band.  h_dev: complex64 [n_tmpl][n/2+1], caller-allocated. */
+rfd_status rfd_gen_templates(rfd_ctx *ctx, const rfd_grid *grid, const rfd_params *params_host,
+                             int32_t n_tmpl, void *h_dev, void *stream);
+
+/* ------------------------------------------------------------------ make_taps
+ * Ratio-filter taps for each template against its reference (Eq. 2, Eq. 3, Sec. V;
+ * normalisation Eqs. 5-6).  All arithmetic before the final cast is FP64 on the device:
+ *   G[k]   = exp(+i (Psi_j - Psi_r)) in the reference band up to the template's cutoff,
+ *            0 above the template's cutoff, and a linear magnitude / shortest-arc phase
+ *            fill from G[k_hi] round the out-of-band arc to G[k_lo];
+ *   g      = (1/n) IDFT_n(G)                              (hand-written FP64 Stockham FFT);
+ *   s_j    = argmax over s in [-n/2, n/2) of E[s] = sum_k w[k]^2 |g[(s+k) mod n]|^2,
+ *            w = symmetric Tukey(K, tukey_alpha); values within 1e-9 relative of the maximum
+ *            tie, and ties go to the s closest to -K/2, then to the smaller s;
+ *   rho[k] = w[k] g[(s_j + k) mod n], k < K;
+ *   sigma_eff^2 = sum_{a,b} rho[a] conj(rho[b]) C_r[b - a],
+ *            C_r[l] = 4 df sum_{k in band_r} |h_r,k|^2 / S_k exp(+2 pi i k l / n);
+ *   match  = |<h_j, h_eff>| / (|h_j| |h_eff|), h_eff = h_r conj(A), A = DFT of the placed taps.
+ * Inputs: psd_dev float64 [n/2+1]; refs_host [n_ref]; tmpl_host [n_tmpl];
+ *   ref_of_tmpl_host int32 [n_tmpl] in [0, n_ref); k_host int32 [n_tmpl], 1 <= K <= k_stride.
+ * Outputs (device, caller-allocated): taps_dev complex64 [n_tmpl][k_stride] (entries past K
+ *   are zeroed), lag_dev int32 [n_tmpl] (s_j), sigma_dev float64 [n_tmpl],
+ *   match_dev float64 [n_tmpl] or NULL to skip the match (it costs one more FFT per template).
+ * Synchronises the stream before returning (its FP64 workspace is sized per batch). */
+rfd_status rfd_make_taps(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_dev,
+                         const rfd_params *refs_host, int32_t n_ref,
+                         const rfd_params *tmpl_host, const int32_t *ref_of_tmpl_host,
+                         int32_t n_tmpl, const int32_t *k_host, int32_t k_stride,
+                         double tukey_alpha, void *taps_dev, int32_t *lag_dev,
+                         double *sigma_dev, double *match_dev, void *stream);
+
+/* ------------------------------------------------------------------ filter_reference
+ * The reference SNR series of Eq. 3, (s|h)_ref, one per reference (Eq. 1 discretised):
+ *   c_r[k] = 4 df d[k] conj(h_r[k]) / S[k] for k in the reference band, 0 for all other
+ *            k in [0, n);
+ *   q_r[m] = sum_k c_r[k] exp(+2 pi i k m / n)   (hand-written FP32 Stockham inverse FFT),
+ * stored with a wrap halo q_r[n + i] = q_r[i], i < halo, so every FIR window
+ * [u, u + K) with u < n is contiguous (halo >= K_max - 1).
+ * Inputs: dtilde_dev complex64 [n/2+1]; psd_dev float64 [n/2+1]; refs_host [n_ref].
+ * Output qref_dev, row length ld = rfd_qref_ld(n, halo):
+ *   RFD_PREC_FP32:   complex64 q[r * ld + m];
+ *   RFD_PREC_FP16X3 / BF16X3: four 2-byte planes per reference, plane p of reference r at
+ *     element offset (4 r + p) ld, p = 0 re_hi, 1 im_hi, 2 re_lo, 3 im_lo, with
+ *     hi = round(x 2^e_r), lo = round(x 2^e_r - hi).
+ * qscale_dev int32 [n_ref] receives e_r (0 for FP32); e_r puts the rms of the scaled series
+ *   near 2^10.  Deterministic: no atomics in any floating-point reduction. */
+rfd_status rfd_filter_reference(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev,
+                                const double *psd_dev, const rfd_params *refs_host,
+                                int32_t n_ref, int32_t halo, int32_t precision,
+                                void *qref_dev, int32_t *qscale_dev, void *stream);
+
+/* ------------------------------------------------------------------ plans
+ * A plan fixes one bank's schedule: templates grouped by reference into tiles of the
+ * contraction Z[J_r x T] = P[J_r x K] Q[K x T] (Eq. 3 for all templates that share a
+ * reference), the arithmetic, the trigger window and the threshold.
+ * ref_of_tmpl_host int32 [n_tmpl]; k_host int32 [n_tmpl] (taps per template, as given to
+ * rfd_make_taps); window >= 1 samples; threshold on |z|^2 (strict >); halo as for
+ * rfd_filter_reference (>= max K - 1).  Copies everything it needs. */
+rfd_status rfd_plan_create(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
+                           const int32_t *ref_of_tmpl_host, const int32_t *k_host,
+                           int32_t precision, int32_t window, float threshold, int32_t halo,
+                           rfd_plan **out);
+void rfd_plan_destroy(rfd_plan *plan);
+
+/* Packs the taps from rfd_make_taps into the plan's own layout (reversed, scaled, split
+ * into hi/lo parts for the tensor-core path) and stores 1/sigma_eff and the lags.
+ * taps_dev complex64 [n_tmpl][k_stride]; lag_dev int32 [n_tmpl]; sigma_dev float64 [n_tmpl].
+ * Must be called before rfd_ratio_filter_batch; stream-ordered. */
+rfd_status rfd_plan_set_taps(rfd_plan *plan, const void *taps_dev, int32_t k_stride,
+                             const int32_t *lag_dev, const double *sigma_dev, void *stream);
+
+/* ------------------------------------------------------------------ ratio_filter_batch
+ * Eq. 3 for every template of the plan, with the trigger reduction fused in:
+ *   qhat_j[m] = sum_{k<K_j} rho_j[k] q_r[(m - s_j - k) mod n],  z_j = qhat_j / sigma_eff,j,
+ * computed as Y[j, u] = sum_k rho_j[K_j-1-k] q_r[u + k] at true time m = (u + s_j + K_j - 1)
+ * mod n; |z|^2 is compared with the threshold in registers and, for each run of samples
+ * sharing (j, window), the maximum key is appended to cand_dev.  No SNR series is written.
+ * qref_dev / qscale_dev as written by rfd_filter_reference in the plan's precision.
+ * cand_dev rfd_candidate [cand_capacity]; cand_count_dev int64 (device) is reset to 0 by this
+ * call, then counts every candidate produced, including those past the capacity (which are
+ * dropped; rfd_find_triggers reports RFD_ERR_OVERFLOW and the needed capacity). */
+rfd_status rfd_ratio_filter_batch(rfd_plan *plan, const void *qref_dev,
+                                  const int32_t *qscale_dev, rfd_candidate *cand_dev,
+                                  int64_t cand_capacity, int64_t *cand_count_dev, void *stream);
+
+/* ------------------------------------------------------------------ find_triggers
+ * Merges candidates into triggers: per (j, w) the maximum key (the largest |z|^2, ties to the
+ * smallest t), emitted sorted by (j, w).  Integer-only, deterministic.
+ * cand_dev / cand_count_dev / cand_capacity as filled by a filtering call; n_tmpl templates;
+ * trig_dev rfd_trigger [trig_capacity].  *n_trig_host receives the number of triggers.
+ * Synchronises the stream (it reads the counts back).  Returns RFD_ERR_OVERFLOW when the
+ * candidate list overflowed (then *n_trig_host = the candidate capacity needed) or when
+ * trig_capacity is too small (then *n_trig_host = the trigger capacity needed). */
+rfd_status rfd_find_triggers(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand_dev,
+                             const int64_t *cand_count_dev, int64_t cand_capacity,
+                             rfd_trigger *trig_dev, int64_t trig_capacity,
+                             int64_t *n_trig_host, void *stream);
+
+/* ------------------------------------------------------------------ FINDCHIRP baseline
+ * The standard frequency-domain matched filter of Eq. 1 for every template (Sec. II-III):
+ * per template, h_j on the grid (FP64 phase), c = 4 df d conj(h_j) / S, an n-point FP32
+ * Stockham inverse FFT, z = q / sigma(h_j), and the same threshold / window reduction into
+ * candidates as rfd_ratio_filter_batch.  The comparison path for the ratio filter. */
+rfd_status rfd_findchirp(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev,
+                         const double *psd_dev, const rfd_params *tmpl_host, int32_t n_tmpl,
+                         int32_t window, float threshold, rfd_candidate *cand_dev,
+                         int64_t cand_capacity, int64_t *cand_count_dev, void *stream);
+
+/* Inverse FFT (unnormalised, exp(+2 pi i k m / n)) of `batch` complex64 rows of length n
+ * with the library's Stockham kernels: in_dev and out_dev may not overlap. */
+rfd_status rfd_ifft_c2c(rfd_ctx *ctx, int64_t n, int32_t batch, const void *in_dev,
+                        void *out_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RFD_H */

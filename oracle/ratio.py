@@ -156,8 +156,11 @@ def autocorrelation(h_ref, psd, df, n, max_lag):
     nz = np.nonzero(h_ref)[0]
     wgt = 4.0 * df * np.abs(h_ref[nz]) ** 2 / psd[nz]
     lags = np.arange(-max_lag, max_lag + 1)
-    ph = np.exp(2j * math.pi * np.outer(lags, nz) / n)
-    return ph @ wgt
+    out = np.empty(len(lags), dtype=np.complex128)
+    for i0 in range(0, len(lags), 16):          # a few lags at a time bounds the memory
+        ph = np.exp(2j * math.pi * np.outer(lags[i0:i0 + 16], nz) / n)
+        out[i0:i0 + 16] = ph @ wgt
+    return out
 
 
 def sigma_eff_sq_parseval(rho, C):

@@ -1,0 +1,187 @@
+"""Ratio-Filter Dechirping on GB300: Python binding over the librfd C ABI.
+
+The binding only marshals arguments (torch tensors for device memory, torch streams); every
+step of the method runs in the library's CUDA kernels.  Names follow include/rfd.h:
+
+  gen_templates      TaylorF2 templates h(f) (FP64 phase)                      Eq. 1
+  make_taps          ratio-filter taps, lags, sigma_eff, match                 Eqs. 2-3, Sec. V, Eqs. 5-6
+  filter_reference   reference SNR series q_ref (pointwise + Stockham IFFT)    Eqs. 1, 3
+  Plan.ratio_filter_batch   FIR of every template on q_ref + fused triggers    Eq. 3, Table II
+  find_triggers      per-window maxima above threshold                         Table II
+  findchirp          the FINDCHIRP comparison path                             Eq. 1
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native
+from ._native import (CANDIDATE_DTYPE, PN_SO, PN_TIDAL, PREC_BF16X3, PREC_FP16X3, PREC_FP32,  # noqa: F401
+                      TRIGGER_DTYPE, RfdError, check)
+
+__all__ = ["Context", "Plan", "grid", "gen_templates", "make_taps", "filter_reference",
+           "find_triggers", "findchirp", "ifft_c2c", "qref_ld", "candidates_to_numpy",
+           "triggers_to_numpy", "CANDIDATE_DTYPE", "TRIGGER_DTYPE"]
+
+
+def _lib():
+    return _native.load()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return ctypes.c_void_p(t.data_ptr())
+    return t
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def grid(fs, n, f_low, pn_flags=0):
+    return _native.Grid(float(fs), int(n), float(f_low), int(pn_flags), 0)
+
+
+def _params(p):
+    p = np.ascontiguousarray(np.asarray(p, dtype=np.float64).reshape(-1, 5))
+    arr = (_native.Params * max(1, len(p)))()
+    ctypes.memmove(arr, p.ctypes.data, p.nbytes)
+    return arr, len(p)
+
+
+def _i32_host(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def kernel_launches():
+    """Kernels launched by librfd in this process so far."""
+    return int(_lib().rfd_kernel_launches())
+
+
+def qref_ld(n, halo):
+    return int(_lib().rfd_qref_ld(int(n), int(halo)))
+
+
+class Context:
+    """A librfd context on one CUDA device (FFT tables and workspaces)."""
+
+    def __init__(self, device=0):
+        lib = _lib()
+        h = ctypes.c_void_p()
+        check(lib.rfd_ctx_create(int(device), ctypes.byref(h)))
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            _lib().rfd_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gen_templates(ctx, g, params, out, stream=None):
+    pa, n = _params(params)
+    check(_lib().rfd_gen_templates(ctx.handle, ctypes.byref(g), pa, n, _ptr(out), _stream(stream)))
+    return out
+
+
+def make_taps(ctx, g, psd, refs, tmpl, ref_of, k, k_stride, alpha, taps, lag, sigma, match=None,
+              stream=None):
+    ra, nr = _params(refs)
+    ta, nt = _params(tmpl)
+    ro, rop = _i32_host(ref_of)
+    kk, kp = _i32_host(k)
+    check(_lib().rfd_make_taps(ctx.handle, ctypes.byref(g), _ptr(psd), ra, nr, ta, rop, nt, kp,
+                               int(k_stride), float(alpha), _ptr(taps), _ptr(lag), _ptr(sigma),
+                               _ptr(match), _stream(stream)))
+
+
+def filter_reference(ctx, g, dtilde, psd, refs, halo, precision, qref, qscale, stream=None):
+    ra, nr = _params(refs)
+    check(_lib().rfd_filter_reference(ctx.handle, ctypes.byref(g), _ptr(dtilde), _ptr(psd), ra, nr,
+                                      int(halo), int(precision), _ptr(qref), _ptr(qscale),
+                                      _stream(stream)))
+
+
+class Plan:
+    """One bank's ratio-filter schedule (templates tiled per reference) and packed taps."""
+
+    def __init__(self, ctx, g, n_ref, ref_of, k, precision, window, threshold, halo):
+        ro, rop = _i32_host(ref_of)
+        kk, kp = _i32_host(k)
+        h = ctypes.c_void_p()
+        check(_lib().rfd_plan_create(ctx.handle, ctypes.byref(g), int(n_ref), len(ro), rop, kp,
+                                     int(precision), int(window), float(threshold), int(halo),
+                                     ctypes.byref(h)))
+        self.handle = h
+        self.ctx = ctx
+        self.n_tmpl = len(ro)
+
+    def set_taps(self, taps, k_stride, lag, sigma, stream=None):
+        check(_lib().rfd_plan_set_taps(self.handle, _ptr(taps), int(k_stride), _ptr(lag), _ptr(sigma),
+                                       _stream(stream)))
+
+    def ratio_filter_batch(self, qref, qscale, cand, cand_count, stream=None):
+        cap = cand.numel() * cand.element_size() // CANDIDATE_DTYPE.itemsize
+        check(_lib().rfd_ratio_filter_batch(self.handle, _ptr(qref), _ptr(qscale), _ptr(cand), int(cap),
+                                            _ptr(cand_count), _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            _lib().rfd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def find_triggers(ctx, n_tmpl, cand, cand_count, trig, stream=None):
+    """Returns the number of triggers written to `trig` (synchronises the stream)."""
+    cap = cand.numel() * cand.element_size() // CANDIDATE_DTYPE.itemsize
+    tcap = trig.numel() * trig.element_size() // TRIGGER_DTYPE.itemsize
+    n = ctypes.c_int64(0)
+    st = _lib().rfd_find_triggers(ctx.handle, int(n_tmpl), _ptr(cand), _ptr(cand_count), int(cap),
+                                  _ptr(trig), int(tcap), ctypes.byref(n), _stream(stream))
+    check(st, needed=n.value)
+    return int(n.value)
+
+
+def findchirp(ctx, g, dtilde, psd, tmpl, window, threshold, cand, cand_count, stream=None):
+    ta, nt = _params(tmpl)
+    cap = cand.numel() * cand.element_size() // CANDIDATE_DTYPE.itemsize
+    check(_lib().rfd_findchirp(ctx.handle, ctypes.byref(g), _ptr(dtilde), _ptr(psd), ta, nt, int(window),
+                               float(threshold), _ptr(cand), int(cap), _ptr(cand_count), _stream(stream)))
+
+
+def ifft_c2c(ctx, x, out, stream=None):
+    n = x.shape[-1]
+    batch = x.numel() // n
+    check(_lib().rfd_ifft_c2c(ctx.handle, int(n), int(batch), _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+def candidates_to_numpy(buf, count):
+    raw = buf[: count * CANDIDATE_DTYPE.itemsize].cpu().numpy().view(np.uint8)
+    return raw.view(CANDIDATE_DTYPE)
+
+
+def triggers_to_numpy(buf, count):
+    raw = buf[: count * TRIGGER_DTYPE.itemsize].cpu().numpy().view(np.uint8)
+    return raw.view(TRIGGER_DTYPE)

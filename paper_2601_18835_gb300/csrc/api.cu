@@ -1,0 +1,421 @@
+// C ABI entry points of librfd: argument checks, host-side planning, dispatch to kernels.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <numeric>
+
+#include "internal.cuh"
+
+namespace rfd {
+
+// implemented in the kernel files
+rfd_status gen_templates_impl(rfd_ctx *, const Grid &, const std::vector<PNParams> &, float2 *,
+                              cudaStream_t);
+rfd_status filter_reference_impl(rfd_ctx *, const Grid &, const float2 *, const double *,
+                                 const std::vector<PNParams> &, int32_t, int32_t, void *,
+                                 int32_t *, cudaStream_t);
+rfd_status findchirp_impl(rfd_ctx *, const Grid &, const float2 *, const double *,
+                          const std::vector<PNParams> &, int32_t, float, rfd_candidate *,
+                          int64_t, int64_t *, cudaStream_t);
+rfd_status make_taps_impl(rfd_ctx *, const Grid &, const double *, const std::vector<PNParams> &,
+                          const std::vector<PNParams> &, const std::vector<int32_t> &,
+                          const std::vector<int32_t> &, int32_t, double, float2 *, int32_t *,
+                          double *, double *, cudaStream_t);
+int fir32_tile_templates();
+rfd_status fir32_launch(const rfd_plan *, const float2 *, rfd_candidate *, int64_t, int64_t *,
+                        cudaStream_t);
+rfd_status pack_taps_fp32(rfd_plan *, const float2 *, int32_t, const int32_t *, const double *,
+                          cudaStream_t);
+
+namespace {
+thread_local char g_err[1024] = {0};
+std::atomic<int64_t> g_launches{0};
+}
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+rfd_status ensure(DevBuf &b, size_t bytes) {
+    if (bytes <= b.bytes && b.p) return RFD_OK;
+    if (b.p) {
+        // earlier stream work may still use the old block
+        RFD_TRY_CUDA(cudaDeviceSynchronize());
+        RFD_TRY_CUDA(cudaFree(b.p));
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    const size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        b.p = nullptr;
+        set_error("workspace allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+        return RFD_ERR_NOMEM;
+    }
+    b.bytes = want;
+    return RFD_OK;
+}
+
+void release(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+rfd_status check_grid(const rfd_grid *g, Grid *out) {
+    RFD_REQUIRE(g != nullptr, RFD_ERR_ARG, "grid is NULL");
+    RFD_REQUIRE(std::isfinite(g->fs) && g->fs > 0, RFD_ERR_ARG, "grid.fs must be finite and > 0");
+    RFD_REQUIRE(g->n >= 1024 && g->n <= (int64_t(1) << 22) && (g->n & (g->n - 1)) == 0, RFD_ERR_SHAPE,
+                "grid.n=%lld must be a power of two in [2^10, 2^22]", (long long)g->n);
+    RFD_REQUIRE(std::isfinite(g->f_low) && g->f_low > 0 && g->f_low < 0.5 * g->fs, RFD_ERR_ARG,
+                "grid.f_low must lie in (0, fs/2)");
+    RFD_REQUIRE(g->reserved == 0, RFD_ERR_ARG, "grid.reserved must be 0");
+    RFD_REQUIRE((g->pn_flags & ~(RFD_PN_SO | RFD_PN_TIDAL)) == 0, RFD_ERR_ARG, "unknown pn_flags bits");
+    out->fs = g->fs;
+    out->n = g->n;
+    out->nf = g->n / 2 + 1;
+    out->f_low = g->f_low;
+    out->df = g->fs / (double)g->n;
+    out->k_lo = (int64_t)std::ceil(g->f_low / out->df - 1e-12);
+    out->pn_flags = g->pn_flags;
+    int l = 0;
+    while ((int64_t(1) << l) < g->n) ++l;
+    out->log2n = l;
+    RFD_REQUIRE(out->k_lo >= 1 && out->k_lo <= g->n / 2 - 1, RFD_ERR_ARG, "empty data band");
+    return RFD_OK;
+}
+
+rfd_status make_pn(const Grid &g, const rfd_params *p, PNParams *out) {
+    RFD_REQUIRE(std::isfinite(p->m1) && std::isfinite(p->m2) && p->m1 > 0 && p->m2 > 0, RFD_ERR_ARG,
+                "masses must be finite and > 0");
+    RFD_REQUIRE(std::isfinite(p->chi1) && std::isfinite(p->chi2) && std::isfinite(p->lambda_tilde),
+                RFD_ERR_ARG, "spins and lambda must be finite");
+    const double mtot = p->m1 + p->m2;
+    out->mt = mtot * kTSun;
+    out->eta = p->m1 * p->m2 / (mtot * mtot);
+    out->beta = 0.0;
+    if (g.pn_flags & RFD_PN_SO) {
+        const double q1 = p->m1 / mtot, q2 = p->m2 / mtot;
+        out->beta = ((113.0 * (q1 * q1) + 75.0 * out->eta) * p->chi1 +
+                     (113.0 * (q2 * q2) + 75.0 * out->eta) * p->chi2) / 12.0;
+    }
+    out->lam = (g.pn_flags & RFD_PN_TIDAL) ? p->lambda_tilde : 0.0;
+    const double fisco = 1.0 / (std::pow(6.0, 1.5) * kPi * out->mt);
+    out->k_hi = std::min<int64_t>(g.n / 2 - 1, (int64_t)std::floor(fisco / g.df));
+    out->pad = 0;
+    return RFD_OK;
+}
+
+static rfd_status make_pn_vec(const Grid &g, const rfd_params *p, int32_t count,
+                              std::vector<PNParams> *out) {
+    out->resize(count);
+    for (int32_t i = 0; i < count; ++i) RFD_TRY(make_pn(g, &p[i], &(*out)[i]));
+    return RFD_OK;
+}
+
+}  // namespace rfd
+
+using namespace rfd;
+
+extern "C" {
+
+int32_t rfd_version(void) { return RFD_VERSION; }
+
+const char *rfd_status_string(rfd_status s) {
+    switch (s) {
+        case RFD_OK: return "ok";
+        case RFD_ERR_ARG: return "invalid argument";
+        case RFD_ERR_SHAPE: return "invalid shape";
+        case RFD_ERR_UNSUPPORTED: return "unsupported";
+        case RFD_ERR_CUDA: return "CUDA error";
+        case RFD_ERR_NOMEM: return "out of device memory";
+        case RFD_ERR_TIMEOUT: return "device wait timed out";
+        case RFD_ERR_OVERFLOW: return "output capacity exceeded";
+    }
+    return "unknown status";
+}
+
+const char *rfd_last_error(void) { return g_err; }
+
+int64_t rfd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int64_t rfd_qref_ld(int64_t n, int32_t halo) { return ((n + (int64_t)halo + 63) / 64) * 64; }
+
+rfd_status rfd_ctx_create(int32_t device, rfd_ctx **out) {
+    RFD_REQUIRE(out != nullptr, RFD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    RFD_TRY_CUDA(cudaGetDeviceCount(&ndev));
+    RFD_REQUIRE(device >= 0 && device < ndev, RFD_ERR_ARG, "device %d not present (%d devices)", device, ndev);
+    RFD_TRY_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    RFD_TRY_CUDA(cudaGetDeviceProperties(&prop, device));
+    RFD_REQUIRE(prop.major == 10 && prop.minor == 3, RFD_ERR_UNSUPPORTED,
+                "librfd is built for sm_103a (GB300); device %d is sm_%d%d", device, prop.major, prop.minor);
+    rfd_ctx *c = new rfd_ctx();
+    c->device = device;
+    c->num_sms = prop.multiProcessorCount;
+    *out = c;
+    return RFD_OK;
+}
+
+void rfd_ctx_destroy(rfd_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->tw32) cudaFree(kv.second);
+    for (auto &kv : ctx->tw64) cudaFree(kv.second);
+    for (auto &b : ctx->ws) release(b);
+    delete ctx;
+}
+
+rfd_status rfd_gen_templates(rfd_ctx *ctx, const rfd_grid *grid, const rfd_params *params_host,
+                             int32_t n_tmpl, void *h_dev, void *stream) {
+    RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
+    Grid g;
+    RFD_TRY(check_grid(grid, &g));
+    RFD_REQUIRE(n_tmpl >= 0, RFD_ERR_SHAPE, "n_tmpl < 0");
+    if (n_tmpl == 0) return RFD_OK;
+    RFD_REQUIRE(params_host && h_dev, RFD_ERR_ARG, "NULL params or output");
+    RFD_TRY_CUDA(cudaSetDevice(ctx->device));
+    std::vector<PNParams> pn;
+    RFD_TRY(make_pn_vec(g, params_host, n_tmpl, &pn));
+    return gen_templates_impl(ctx, g, pn, (float2 *)h_dev, (cudaStream_t)stream);
+}
+
+rfd_status rfd_make_taps(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_dev,
+                         const rfd_params *refs_host, int32_t n_ref, const rfd_params *tmpl_host,
+                         const int32_t *ref_of_tmpl_host, int32_t n_tmpl, const int32_t *k_host,
+                         int32_t k_stride, double tukey_alpha, void *taps_dev, int32_t *lag_dev,
+                         double *sigma_dev, double *match_dev, void *stream) {
+    RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
+    Grid g;
+    RFD_TRY(check_grid(grid, &g));
+    RFD_REQUIRE(n_ref >= 1 && n_tmpl >= 0, RFD_ERR_SHAPE, "need n_ref >= 1 and n_tmpl >= 0");
+    if (n_tmpl == 0) return RFD_OK;
+    RFD_REQUIRE(psd_dev && refs_host && tmpl_host && ref_of_tmpl_host && k_host && taps_dev && lag_dev &&
+                    sigma_dev,
+                RFD_ERR_ARG, "NULL argument");
+    RFD_REQUIRE(k_stride >= 1 && k_stride <= 4096 && k_stride <= g.n, RFD_ERR_SHAPE,
+                "k_stride=%d out of [1, min(4096, n)]", k_stride);
+    RFD_REQUIRE(std::isfinite(tukey_alpha) && tukey_alpha >= 0.0, RFD_ERR_ARG, "tukey_alpha must be >= 0");
+    std::vector<int32_t> ref_of(ref_of_tmpl_host, ref_of_tmpl_host + n_tmpl), K(k_host, k_host + n_tmpl);
+    for (int32_t j = 0; j < n_tmpl; ++j) {
+        RFD_REQUIRE(ref_of[j] >= 0 && ref_of[j] < n_ref, RFD_ERR_ARG, "ref_of_tmpl[%d]=%d out of range", j,
+                    ref_of[j]);
+        RFD_REQUIRE(K[j] >= 1 && K[j] <= k_stride, RFD_ERR_SHAPE, "K[%d]=%d not in [1, k_stride]", j, K[j]);
+    }
+    RFD_TRY_CUDA(cudaSetDevice(ctx->device));
+    std::vector<PNParams> refs, tmpl;
+    RFD_TRY(make_pn_vec(g, refs_host, n_ref, &refs));
+    RFD_TRY(make_pn_vec(g, tmpl_host, n_tmpl, &tmpl));
+    for (int32_t r = 0; r < n_ref; ++r)
+        RFD_REQUIRE(refs[r].k_hi >= g.k_lo, RFD_ERR_ARG, "reference %d has an empty band (ISCO below f_low)", r);
+    return make_taps_impl(ctx, g, psd_dev, refs, tmpl, ref_of, K, k_stride, tukey_alpha, (float2 *)taps_dev,
+                          lag_dev, sigma_dev, match_dev, (cudaStream_t)stream);
+}
+
+rfd_status rfd_filter_reference(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev,
+                                const double *psd_dev, const rfd_params *refs_host, int32_t n_ref,
+                                int32_t halo, int32_t precision, void *qref_dev, int32_t *qscale_dev,
+                                void *stream) {
+    RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
+    Grid g;
+    RFD_TRY(check_grid(grid, &g));
+    RFD_REQUIRE(n_ref >= 0, RFD_ERR_SHAPE, "n_ref < 0");
+    if (n_ref == 0) return RFD_OK;
+    RFD_REQUIRE(dtilde_dev && psd_dev && refs_host && qref_dev && qscale_dev, RFD_ERR_ARG, "NULL argument");
+    RFD_REQUIRE(halo >= 0 && halo < g.n, RFD_ERR_SHAPE, "halo=%d must be in [0, n)", halo);
+    RFD_REQUIRE(precision >= RFD_PREC_FP32 && precision <= RFD_PREC_BF16X3, RFD_ERR_ARG, "bad precision %d",
+                precision);
+    RFD_TRY_CUDA(cudaSetDevice(ctx->device));
+    std::vector<PNParams> refs;
+    RFD_TRY(make_pn_vec(g, refs_host, n_ref, &refs));
+    return filter_reference_impl(ctx, g, (const float2 *)dtilde_dev, psd_dev, refs, halo, precision, qref_dev,
+                                 qscale_dev, (cudaStream_t)stream);
+}
+
+rfd_status rfd_plan_create(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
+                           const int32_t *ref_of_tmpl_host, const int32_t *k_host, int32_t precision,
+                           int32_t window, float threshold, int32_t halo, rfd_plan **out) {
+    RFD_REQUIRE(ctx && out, RFD_ERR_ARG, "NULL ctx or out");
+    *out = nullptr;
+    Grid g;
+    RFD_TRY(check_grid(grid, &g));
+    RFD_REQUIRE(n_ref >= 1 && n_tmpl >= 1, RFD_ERR_SHAPE, "need n_ref >= 1 and n_tmpl >= 1");
+    RFD_REQUIRE(ref_of_tmpl_host && k_host, RFD_ERR_ARG, "NULL ref_of or k");
+    RFD_REQUIRE(window >= 1, RFD_ERR_ARG, "window must be >= 1");
+    RFD_REQUIRE(std::isfinite(threshold) && threshold >= 0.f, RFD_ERR_ARG, "threshold must be finite, >= 0");
+    RFD_REQUIRE(precision >= RFD_PREC_FP32 && precision <= RFD_PREC_BF16X3, RFD_ERR_ARG, "bad precision");
+    RFD_REQUIRE(precision == RFD_PREC_FP32, RFD_ERR_UNSUPPORTED,
+                "tensor-core precisions are not built into this library version");
+    int32_t kmax = 0;
+    for (int32_t j = 0; j < n_tmpl; ++j) {
+        RFD_REQUIRE(ref_of_tmpl_host[j] >= 0 && ref_of_tmpl_host[j] < n_ref, RFD_ERR_ARG,
+                    "ref_of_tmpl[%d] out of range", j);
+        RFD_REQUIRE(k_host[j] >= 1 && k_host[j] <= 4096, RFD_ERR_SHAPE, "K[%d]=%d out of [1, 4096]", j, k_host[j]);
+        kmax = std::max(kmax, k_host[j]);
+    }
+    RFD_REQUIRE(halo >= kmax - 1 && halo < g.n, RFD_ERR_SHAPE, "halo=%d must be >= max K - 1 = %d and < n",
+                halo, kmax - 1);
+    RFD_TRY_CUDA(cudaSetDevice(ctx->device));
+    rfd_plan *p = new rfd_plan();
+    p->ctx = ctx;
+    p->grid = g;
+    p->n_ref = n_ref;
+    p->n_tmpl = n_tmpl;
+    p->precision = precision;
+    p->window = window;
+    p->threshold = threshold;
+    p->halo = halo;
+    p->ld = rfd_qref_ld(g.n, halo);
+    p->k_max = kmax;
+    p->ref_of.assign(ref_of_tmpl_host, ref_of_tmpl_host + n_tmpl);
+    p->k_of.assign(k_host, k_host + n_tmpl);
+    p->tile_j = fir32_tile_templates();
+    // tiles: per reference, templates ordered by K (stable), cut into groups of tile_j
+    std::vector<int32_t> order(n_tmpl);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (p->ref_of[a] != p->ref_of[b]) return p->ref_of[a] < p->ref_of[b];
+        return p->k_of[a] < p->k_of[b];
+    });
+    int32_t slot = 0;
+    for (size_t i = 0; i < order.size();) {
+        const int32_t r = p->ref_of[order[i]];
+        size_t e = i;
+        while (e < order.size() && p->ref_of[order[e]] == r && (int32_t)(e - i) < p->tile_j) ++e;
+        RfdTile t;
+        t.ref = r;
+        t.first = slot;
+        t.count = (int32_t)(e - i);
+        t.k_tile = 0;
+        for (size_t q = i; q < e; ++q) {
+            t.k_tile = std::max(t.k_tile, p->k_of[order[q]]);
+            p->perm.push_back(order[q]);
+        }
+        slot += t.count;
+        p->tiles.push_back(t);
+        i = e;
+    }
+    p->n_slots = slot;
+    rfd_status st = RFD_OK;
+    do {
+        if ((st = ensure(p->d_tiles, p->tiles.size() * sizeof(RfdTile))) != RFD_OK) break;
+        if ((st = ensure(p->d_perm, p->n_slots * sizeof(int32_t))) != RFD_OK) break;
+        if ((st = ensure(p->d_kslot, p->n_slots * sizeof(int32_t))) != RFD_OK) break;
+        if ((st = ensure(p->d_off, p->n_slots * sizeof(int32_t))) != RFD_OK) break;
+        if ((st = ensure(p->d_scale, p->n_slots * sizeof(float))) != RFD_OK) break;
+        if ((st = ensure(p->d_taps, (size_t)p->n_slots * p->k_max * sizeof(float2))) != RFD_OK) break;
+        std::vector<int32_t> kslot(p->n_slots);
+        for (int64_t s = 0; s < p->n_slots; ++s) kslot[s] = p->k_of[p->perm[s]];
+        cudaError_t e1 = cudaMemcpy(p->d_tiles.p, p->tiles.data(), p->tiles.size() * sizeof(RfdTile),
+                                    cudaMemcpyHostToDevice);
+        cudaError_t e2 = cudaMemcpy(p->d_perm.p, p->perm.data(), p->n_slots * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice);
+        cudaError_t e3 = cudaMemcpy(p->d_kslot.p, kslot.data(), p->n_slots * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            set_error("plan upload failed: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
+            st = RFD_ERR_CUDA;
+        }
+    } while (0);
+    if (st != RFD_OK) {
+        rfd_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return RFD_OK;
+}
+
+void rfd_plan_destroy(rfd_plan *plan) {
+    if (!plan) return;
+    cudaSetDevice(plan->ctx->device);
+    cudaDeviceSynchronize();
+    release(plan->d_tiles);
+    release(plan->d_perm);
+    release(plan->d_taps);
+    release(plan->d_off);
+    release(plan->d_scale);
+    release(plan->d_kslot);
+    delete plan;
+}
+
+rfd_status rfd_plan_set_taps(rfd_plan *plan, const void *taps_dev, int32_t k_stride, const int32_t *lag_dev,
+                             const double *sigma_dev, void *stream) {
+    RFD_REQUIRE(plan, RFD_ERR_ARG, "plan is NULL");
+    RFD_REQUIRE(taps_dev && lag_dev && sigma_dev, RFD_ERR_ARG, "NULL argument");
+    RFD_REQUIRE(k_stride >= plan->k_max, RFD_ERR_SHAPE, "k_stride=%d < max K=%d", k_stride, plan->k_max);
+    RFD_TRY_CUDA(cudaSetDevice(plan->ctx->device));
+    RFD_TRY(pack_taps_fp32(plan, (const float2 *)taps_dev, k_stride, lag_dev, sigma_dev, (cudaStream_t)stream));
+    plan->taps_set = true;
+    return RFD_OK;
+}
+
+rfd_status rfd_ratio_filter_batch(rfd_plan *plan, const void *qref_dev, const int32_t *qscale_dev,
+                                  rfd_candidate *cand_dev, int64_t cand_capacity, int64_t *cand_count_dev,
+                                  void *stream) {
+    RFD_REQUIRE(plan, RFD_ERR_ARG, "plan is NULL");
+    RFD_REQUIRE(plan->taps_set, RFD_ERR_ARG, "rfd_plan_set_taps has not been called");
+    RFD_REQUIRE(qref_dev && cand_count_dev && (cand_dev || cand_capacity == 0), RFD_ERR_ARG, "NULL argument");
+    RFD_REQUIRE(cand_capacity >= 0, RFD_ERR_SHAPE, "negative capacity");
+    (void)qscale_dev;
+    RFD_TRY_CUDA(cudaSetDevice(plan->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    RFD_TRY_CUDA(cudaMemsetAsync(cand_count_dev, 0, sizeof(int64_t), s));
+    return fir32_launch(plan, (const float2 *)qref_dev, cand_dev, cand_capacity, cand_count_dev, s);
+}
+
+rfd_status rfd_find_triggers(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand_dev,
+                             const int64_t *cand_count_dev, int64_t cand_capacity, rfd_trigger *trig_dev,
+                             int64_t trig_capacity, int64_t *n_trig_host, void *stream) {
+    RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
+    RFD_REQUIRE(n_tmpl >= 1, RFD_ERR_SHAPE, "n_tmpl must be >= 1");
+    RFD_REQUIRE(cand_count_dev && n_trig_host && (cand_dev || cand_capacity == 0) &&
+                    (trig_dev || trig_capacity == 0),
+                RFD_ERR_ARG, "NULL argument");
+    RFD_REQUIRE(cand_capacity >= 0 && trig_capacity >= 0, RFD_ERR_SHAPE, "negative capacity");
+    RFD_TRY_CUDA(cudaSetDevice(ctx->device));
+    return find_triggers_impl(ctx, n_tmpl, cand_dev, cand_count_dev, cand_capacity, trig_dev, trig_capacity,
+                              n_trig_host, (cudaStream_t)stream);
+}
+
+rfd_status rfd_findchirp(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev, const double *psd_dev,
+                         const rfd_params *tmpl_host, int32_t n_tmpl, int32_t window, float threshold,
+                         rfd_candidate *cand_dev, int64_t cand_capacity, int64_t *cand_count_dev,
+                         void *stream) {
+    RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
+    Grid g;
+    RFD_TRY(check_grid(grid, &g));
+    RFD_REQUIRE(n_tmpl >= 1, RFD_ERR_SHAPE, "n_tmpl must be >= 1");
+    RFD_REQUIRE(dtilde_dev && psd_dev && tmpl_host && cand_count_dev && (cand_dev || cand_capacity == 0),
+                RFD_ERR_ARG, "NULL argument");
+    RFD_REQUIRE(window >= 1 && std::isfinite(threshold) && threshold >= 0.f, RFD_ERR_ARG, "bad window/threshold");
+    RFD_TRY_CUDA(cudaSetDevice(ctx->device));
+    std::vector<PNParams> pn;
+    RFD_TRY(make_pn_vec(g, tmpl_host, n_tmpl, &pn));
+    return findchirp_impl(ctx, g, (const float2 *)dtilde_dev, psd_dev, pn, window, threshold, cand_dev,
+                          cand_capacity, cand_count_dev, (cudaStream_t)stream);
+}
+
+rfd_status rfd_ifft_c2c(rfd_ctx *ctx, int64_t n, int32_t batch, const void *in_dev, void *out_dev, void *stream) {
+    RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
+    RFD_REQUIRE(n >= 4 && n <= (int64_t(1) << 24) && (n & (n - 1)) == 0, RFD_ERR_SHAPE, "n must be a power of two");
+    RFD_REQUIRE(batch >= 0, RFD_ERR_SHAPE, "batch < 0");
+    if (batch == 0) return RFD_OK;
+    RFD_REQUIRE(in_dev && out_dev && in_dev != out_dev, RFD_ERR_ARG, "NULL or aliased buffers");
+    RFD_TRY_CUDA(cudaSetDevice(ctx->device));
+    RFD_TRY(ensure(ctx->ws[14], (size_t)batch * n * sizeof(float2)));
+    return fft_c2c<float>(ctx, n, batch, (const float2 *)in_dev, n, (float2 *)out_dev, n, (float2 *)ctx->ws[14].p,
+                          true, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,150 @@
+// Internal declarations of librfd (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <vector>
+
+#include "rfd.h"
+
+namespace rfd {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kTSun = 4.925490947641267e-6;   // G Msun / c^3, seconds
+
+void set_error(const char *fmt, ...);
+
+#define RFD_TRY_CUDA(expr)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            ::rfd::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                             __LINE__);                                                      \
+            return RFD_ERR_CUDA;                                                             \
+        }                                                                                    \
+    } while (0)
+
+#define RFD_REQUIRE(cond, code, ...)                                                         \
+    do {                                                                                     \
+        if (!(cond)) {                                                                       \
+            ::rfd::set_error(__VA_ARGS__);                                                   \
+            return code;                                                                     \
+        }                                                                                    \
+    } while (0)
+
+#define RFD_TRY(expr)                                                                        \
+    do {                                                                                     \
+        rfd_status s_ = (expr);                                                              \
+        if (s_ != RFD_OK) return s_;                                                         \
+    } while (0)
+
+// Every kernel launch site is followed by RFD_LAUNCH_CHECK(), which also counts the launch
+// (rfd_kernel_launches() reports the running total).
+void count_launch();
+#define RFD_LAUNCH_CHECK()                                                                   \
+    do {                                                                                     \
+        ::rfd::count_launch();                                                               \
+        RFD_TRY_CUDA(cudaGetLastError());                                                    \
+    } while (0)
+
+// ------------------------------------------------------------------ grid
+struct Grid {
+    double fs, f_low, df;
+    int64_t n, nf;    // samples, one-sided bins n/2+1
+    int64_t k_lo;     // first in-band bin
+    int32_t pn_flags;
+    int32_t log2n;
+};
+rfd_status check_grid(const rfd_grid *g, Grid *out);
+
+// Per-template constants of the TaylorF2 phase, evaluated on the host in FP64.
+struct PNParams {
+    double mt;        // total mass in seconds
+    double eta;       // symmetric mass ratio
+    double beta;      // spin-orbit coefficient (0 unless RFD_PN_SO)
+    double lam;       // tidal deformability (0 unless RFD_PN_TIDAL)
+    int64_t k_hi;     // last non-zero bin: min(n/2 - 1, floor(f_ISCO / df))
+    int64_t pad;
+};
+rfd_status make_pn(const Grid &g, const rfd_params *p, PNParams *out);
+
+// FP64 TaylorF2 phase Psi(f) (t_c = phi_c = 0).
+__device__ __forceinline__ double pn_phase(double f, const PNParams &p, int flags) {
+    const double v = cbrt(kPi * p.mt * f);
+    const double v2 = v * v, v3 = v2 * v, v5 = v3 * v2;
+    double br = 1.0 + (3715.0 / 756.0 + 55.0 * p.eta / 9.0) * v2 + (4.0 * p.beta - 16.0 * kPi) * v3;
+    if (flags & RFD_PN_TIDAL) br -= 19.5 * p.lam * (v5 * v5);
+    return -0.25 * kPi + 3.0 / (128.0 * p.eta * v5) * br;
+}
+
+// ------------------------------------------------------------------ workspaces
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+// Grow-only device buffer.  Growing synchronises the device before freeing the old block.
+rfd_status ensure(DevBuf &b, size_t bytes);
+void release(DevBuf &b);
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+// ------------------------------------------------------------------ FFT (fft.cu)
+// Unnormalised complex FFT of `batch` rows of length n (power of two) by Stockham passes.
+// in: rows at stride in_stride; out: rows at stride out_stride; tmp: batch * n elements.
+// in, out, tmp must not overlap.  inverse: exp(+2 pi i k m / n), forward: exp(-...).
+template <typename T>
+rfd_status fft_c2c(rfd_ctx *ctx, int64_t n, int64_t batch, const typename Cplx<T>::type *in,
+                   int64_t in_stride, typename Cplx<T>::type *out, int64_t out_stride,
+                   typename Cplx<T>::type *tmp, bool inverse, cudaStream_t s);
+
+// ------------------------------------------------------------------ triggers (triggers.cu)
+rfd_status find_triggers_impl(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand,
+                              const int64_t *cand_count, int64_t cap, rfd_trigger *trig,
+                              int64_t trig_cap, int64_t *n_trig_host, cudaStream_t s);
+
+}  // namespace rfd
+
+// ------------------------------------------------------------------ opaque handles
+struct rfd_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::map<int64_t, void *> tw32, tw64;   // twiddle tables exp(+2 pi i m / n), m < n
+    rfd::DevBuf ws[16];                      // scratch slots, see the users for their roles
+};
+
+// Tile of the ratio-filter contraction: templates [first, first + count) of the plan's
+// permuted template order, all assigned to reference `ref`, padded to k_tile taps.
+struct RfdTile {
+    int32_t ref;
+    int32_t first;
+    int32_t count;
+    int32_t k_tile;
+};
+
+struct rfd_plan {
+    rfd_ctx *ctx = nullptr;
+    rfd::Grid grid{};
+    int32_t n_ref = 0, n_tmpl = 0, precision = 0, window = 1, halo = 0;
+    float threshold = 0.f;
+    int64_t ld = 0;                  // q_ref row length
+    int32_t k_max = 0;
+    int32_t tile_j = 0;              // templates per tile
+    std::vector<int32_t> ref_of, k_of;
+    std::vector<int32_t> perm;       // permuted template order (tile-major)
+    std::vector<RfdTile> tiles;
+    // device state
+    rfd::DevBuf d_tiles;             // RfdTile [n_tiles]
+    rfd::DevBuf d_perm;              // int32 [n_slots]: template index of each slot (-1 pad)
+    rfd::DevBuf d_taps;              // packed taps (layout depends on precision)
+    rfd::DevBuf d_off;               // int32 [n_slots]: (s_j + K_j - 1) mod n
+    rfd::DevBuf d_scale;             // float [n_slots]: 1 / (sigma_eff 2^e_j)
+    rfd::DevBuf d_kslot;             // int32 [n_slots]: K_j
+    int64_t n_slots = 0;
+    bool taps_set = false;
+};

@@ -1,0 +1,269 @@
+// Templates (FP64 TaylorF2 phase), the matched-filter spectrum of Eq. 1, the reference
+// series of Eq. 3 (filter_reference) and the FINDCHIRP comparison path.
+#include <cmath>
+
+#include "epilogue.cuh"
+#include "internal.cuh"
+
+namespace rfd {
+
+namespace {
+
+// h(f_k) = f^(-7/6) exp(-i Psi(f_k)) inside the template's band, 0 elsewhere; FP64 phase.
+__global__ void k_gen_templates(const PNParams *__restrict__ pn, int flags, double df, int64_t nf,
+                                int64_t k_lo, float2 *__restrict__ h) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nf) return;
+    const int64_t row = blockIdx.y;
+    const PNParams p = pn[row];
+    float2 out = make_float2(0.f, 0.f);
+    if (k >= k_lo && k <= p.k_hi) {
+        const double f = (double)k * df;
+        const double psi = pn_phase(f, p, flags);
+        double s, c;
+        sincos(psi, &s, &c);
+        const double amp = pow(f, -7.0 / 6.0);
+        out = make_float2((float)(amp * c), (float)(-amp * s));
+    }
+    h[row * nf + k] = out;
+}
+
+// Block-wide FP64 sum in a fixed order (deterministic); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sm) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sm[i];
+    __syncthreads();
+    return r;
+}
+
+// c[row][k] = 4 df d[k] conj(h_row[k]) / S[k] for k in the row's band (k_lo .. k_hi), 0 for
+// every other k in [0, n): the discretised integrand of Eq. 1.  Per block, writes the partial
+// sums of |c|^2 and of 4 df |h|^2 / S (sigma^2 of the row's template).
+__global__ void __launch_bounds__(256) k_weighted_spectrum(
+    const float2 *__restrict__ d, const double *__restrict__ psd, const PNParams *__restrict__ pn,
+    int flags, double df, int64_t n, int64_t k_lo, float2 *__restrict__ c, int64_t c_stride,
+    double *__restrict__ part_c, double *__restrict__ part_s) {
+    __shared__ double sm[8];
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = blockIdx.y;
+    const PNParams p = pn[row];
+    double cr = 0.0, ci = 0.0, sg = 0.0;
+    if (k >= k_lo && k <= p.k_hi) {
+        const double f = (double)k * df;
+        const double psi = pn_phase(f, p, flags);
+        double s, co;
+        sincos(psi, &s, &co);
+        const double amp = pow(f, -7.0 / 6.0);
+        const double S = psd[k];
+        const double g = 4.0 * df * amp / S;
+        // conj(h) = amp (cos psi + i sin psi)
+        const double dr = (double)d[k].x, di = (double)d[k].y;
+        cr = g * (dr * co - di * s);
+        ci = g * (dr * s + di * co);
+        sg = 4.0 * df * amp * amp / S;
+    }
+    if (k < n) c[row * c_stride + k] = make_float2((float)cr, (float)ci);
+    const double pc = block_sum(cr * cr + ci * ci, sm);
+    const double ps = block_sum(sg, sm);
+    if (threadIdx.x == 0) {
+        part_c[row * gridDim.x + blockIdx.x] = pc;
+        part_s[row * gridDim.x + blockIdx.x] = ps;
+    }
+}
+
+// out[row] = sum of the row's partials, in index order.
+__global__ void k_sum_rows(const double *__restrict__ part, int64_t nparts, double *__restrict__ out) {
+    __shared__ double sm[8];
+    const int64_t row = blockIdx.x;
+    double v = 0.0;
+    // each thread sums a contiguous chunk, then a fixed-order block reduction
+    const int64_t per = (nparts + blockDim.x - 1) / blockDim.x;
+    const int64_t b = threadIdx.x * per, e = min(nparts, b + per);
+    for (int64_t i = b; i < e; ++i) v += part[row * nparts + i];
+    v = block_sum(v, sm);
+    if (threadIdx.x == 0) out[row] = v;
+}
+
+// Per-reference power-of-two scale: the rms of q is sqrt(sum_k |c_k|^2) for the unnormalised
+// inverse transform; e_r puts it near 2^8 so the fp16 hi part keeps >= 8 bits of headroom.
+__global__ void k_qscale(const double *__restrict__ pow_c, int n_ref, int precision,
+                         int32_t *__restrict__ e) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_ref) return;
+    int v = 0;
+    if (precision != RFD_PREC_FP32 && pow_c[r] > 0.0) {
+        const double rms = sqrt(pow_c[r]);
+        v = (int)nearbyint(8.0 - log2(rms));
+        v = max(-120, min(120, v));
+    }
+    e[r] = v;
+}
+
+__global__ void k_finalize_fp32(const float2 *__restrict__ q, int64_t n, int64_t ld, int64_t keep,
+                                float2 *__restrict__ out) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= ld) return;
+    const int64_t r = blockIdx.y;
+    out[r * ld + m] = (m < keep) ? q[r * n + (m & (n - 1))] : make_float2(0.f, 0.f);
+}
+
+template <typename H>
+__device__ __forceinline__ H to_h(float x);
+template <>
+__device__ __forceinline__ __half to_h<__half>(float x) { return __float2half_rn(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_h<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ float from_h(__half x) { return __half2float(x); }
+__device__ __forceinline__ float from_h(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// hi = round(x 2^e), lo = round(x 2^e - hi), separately for Re and Im; planes
+// (re_hi, im_hi, re_lo, im_lo) of ld elements each, wrap halo, zero padding.
+template <typename H>
+__global__ void k_finalize_split(const float2 *__restrict__ q, int64_t n, int64_t ld, int64_t keep,
+                                 const int32_t *__restrict__ e, H *__restrict__ out) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= ld) return;
+    const int64_t r = blockIdx.y;
+    H rh = to_h<H>(0.f), ih = rh, rl = rh, il = rh;
+    if (m < keep) {
+        const float2 x = q[r * n + (m & (n - 1))];
+        const float xr = ldexpf(x.x, e[r]), xi = ldexpf(x.y, e[r]);
+        rh = to_h<H>(xr);
+        ih = to_h<H>(xi);
+        rl = to_h<H>(xr - from_h(rh));
+        il = to_h<H>(xi - from_h(ih));
+    }
+    H *base = out + (4 * r) * ld;
+    base[m] = rh;
+    base[ld + m] = ih;
+    base[2 * ld + m] = rl;
+    base[3 * ld + m] = il;
+}
+
+// FINDCHIRP epilogue: z = q / sigma, threshold and window maximum, lanes = consecutive t.
+__global__ void __launch_bounds__(256) k_findchirp_epilogue(
+    const float2 *__restrict__ q, int64_t n, const double *__restrict__ sig2, int32_t j0,
+    float thr, uint32_t W, rfd_candidate *__restrict__ cand, int64_t cap,
+    unsigned long long *__restrict__ count) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // n multiple of 256
+    const int64_t row = blockIdx.y;
+    const float inv = (float)(1.0 / sqrt(sig2[row]));
+    const float2 x = q[row * n + m];
+    emit_window_max(true, (uint32_t)(j0 + row), (uint32_t)m, x.x * inv, x.y * inv, thr, W, cand,
+                    cap, count);
+}
+
+}  // namespace
+
+rfd_status gen_templates_impl(rfd_ctx *ctx, const Grid &g, const std::vector<PNParams> &pn,
+                              float2 *h, cudaStream_t s) {
+    const int64_t rows = (int64_t)pn.size();
+    if (rows == 0) return RFD_OK;
+    RFD_TRY(ensure(ctx->ws[0], rows * sizeof(PNParams)));
+    RFD_TRY_CUDA(cudaMemcpyAsync(ctx->ws[0].p, pn.data(), rows * sizeof(PNParams),
+                                 cudaMemcpyHostToDevice, s));
+    for (int64_t r0 = 0; r0 < rows; r0 += 65535) {
+        const unsigned gy = (unsigned)std::min<int64_t>(65535, rows - r0);
+        dim3 grid((unsigned)((g.nf + 255) / 256), gy);
+        k_gen_templates<<<grid, 256, 0, s>>>((const PNParams *)ctx->ws[0].p + r0, g.pn_flags, g.df,
+                                             g.nf, g.k_lo, h + r0 * g.nf);
+        RFD_LAUNCH_CHECK();
+    }
+    // the parameter upload must finish before ws[0] can be reused by a later call
+    RFD_TRY_CUDA(cudaStreamSynchronize(s));
+    return RFD_OK;
+}
+
+// Workspace slots: ws[0] params, ws[1] spectrum c, ws[2] FFT output, ws[3] FFT tmp,
+// ws[4] partials, ws[5] per-row sums.
+rfd_status filter_reference_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, const double *psd,
+                                 const std::vector<PNParams> &pn, int32_t halo, int32_t precision,
+                                 void *qref, int32_t *qscale, cudaStream_t s) {
+    const int64_t R = (int64_t)pn.size();
+    const int64_t n = g.n, ld = rfd_qref_ld(n, halo);
+    const unsigned nblk = (unsigned)(n / 256);
+    RFD_TRY(ensure(ctx->ws[0], R * sizeof(PNParams)));
+    RFD_TRY(ensure(ctx->ws[1], R * n * sizeof(float2)));
+    RFD_TRY(ensure(ctx->ws[2], R * n * sizeof(float2)));
+    RFD_TRY(ensure(ctx->ws[3], R * n * sizeof(float2)));
+    RFD_TRY(ensure(ctx->ws[4], 2 * R * nblk * sizeof(double)));
+    RFD_TRY(ensure(ctx->ws[5], 2 * R * sizeof(double)));
+    RFD_TRY_CUDA(cudaMemcpyAsync(ctx->ws[0].p, pn.data(), R * sizeof(PNParams),
+                                 cudaMemcpyHostToDevice, s));
+    float2 *c = (float2 *)ctx->ws[1].p;
+    double *part = (double *)ctx->ws[4].p;
+    double *sums = (double *)ctx->ws[5].p;
+    for (int64_t r0 = 0; r0 < R; r0 += 65535) {
+        const unsigned gy = (unsigned)std::min<int64_t>(65535, R - r0);
+        k_weighted_spectrum<<<dim3(nblk, gy), 256, 0, s>>>(
+            d, psd, (const PNParams *)ctx->ws[0].p + r0, g.pn_flags, g.df, n, g.k_lo, c + r0 * n, n,
+            part + r0 * nblk, part + R * nblk + r0 * nblk);
+        RFD_LAUNCH_CHECK();
+    }
+    k_sum_rows<<<(unsigned)R, 256, 0, s>>>(part, nblk, sums);
+    RFD_LAUNCH_CHECK();
+    k_qscale<<<(unsigned)((R + 127) / 128), 128, 0, s>>>(sums, (int)R, precision, qscale);
+    RFD_LAUNCH_CHECK();
+    float2 *q = (float2 *)ctx->ws[2].p;
+    RFD_TRY(fft_c2c<float>(ctx, n, R, c, n, q, n, (float2 *)ctx->ws[3].p, true, s));
+    const int64_t keep = n + halo;
+    for (int64_t r0 = 0; r0 < R; r0 += 65535) {
+        const unsigned gy = (unsigned)std::min<int64_t>(65535, R - r0);
+        dim3 grid((unsigned)((ld + 255) / 256), gy);
+        if (precision == RFD_PREC_FP32) {
+            k_finalize_fp32<<<grid, 256, 0, s>>>(q + r0 * n, n, ld, keep, (float2 *)qref + r0 * ld);
+        } else if (precision == RFD_PREC_FP16X3) {
+            k_finalize_split<__half><<<grid, 256, 0, s>>>(q + r0 * n, n, ld, keep, qscale + r0,
+                                                          (__half *)qref + 4 * r0 * ld);
+        } else {
+            k_finalize_split<__nv_bfloat16><<<grid, 256, 0, s>>>(
+                q + r0 * n, n, ld, keep, qscale + r0, (__nv_bfloat16 *)qref + 4 * r0 * ld);
+        }
+        RFD_LAUNCH_CHECK();
+    }
+    return RFD_OK;
+}
+
+// FINDCHIRP over all templates in batches; candidates as in the ratio-filter epilogue.
+rfd_status findchirp_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, const double *psd,
+                          const std::vector<PNParams> &pn, int32_t W, float thr,
+                          rfd_candidate *cand, int64_t cap, int64_t *count, cudaStream_t s) {
+    const int64_t J = (int64_t)pn.size();
+    const int64_t n = g.n;
+    const unsigned nblk = (unsigned)(n / 256);
+    // batch so that three complex64 work arrays stay near 3 GB
+    int64_t B = std::max<int64_t>(1, ((int64_t)1 << 30) / (n * (int64_t)sizeof(float2)));
+    B = std::min<int64_t>(B, J);
+    RFD_TRY(ensure(ctx->ws[0], J * sizeof(PNParams)));
+    RFD_TRY(ensure(ctx->ws[1], B * n * sizeof(float2)));
+    RFD_TRY(ensure(ctx->ws[2], B * n * sizeof(float2)));
+    RFD_TRY(ensure(ctx->ws[3], B * n * sizeof(float2)));
+    RFD_TRY(ensure(ctx->ws[4], 2 * B * nblk * sizeof(double)));
+    RFD_TRY(ensure(ctx->ws[5], 2 * B * sizeof(double)));
+    RFD_TRY_CUDA(cudaMemcpyAsync(ctx->ws[0].p, pn.data(), J * sizeof(PNParams),
+                                 cudaMemcpyHostToDevice, s));
+    RFD_TRY_CUDA(cudaMemsetAsync(count, 0, sizeof(int64_t), s));
+    float2 *c = (float2 *)ctx->ws[1].p, *q = (float2 *)ctx->ws[2].p;
+    double *part = (double *)ctx->ws[4].p, *sums = (double *)ctx->ws[5].p;
+    for (int64_t j0 = 0; j0 < J; j0 += B) {
+        const int64_t b = std::min<int64_t>(B, J - j0);
+        k_weighted_spectrum<<<dim3(nblk, (unsigned)b), 256, 0, s>>>(
+            d, psd, (const PNParams *)ctx->ws[0].p + j0, g.pn_flags, g.df, n, g.k_lo, c, n, part,
+            part + B * nblk);
+        RFD_LAUNCH_CHECK();
+        k_sum_rows<<<(unsigned)b, 256, 0, s>>>(part + B * nblk, nblk, sums);
+        RFD_LAUNCH_CHECK();
+        RFD_TRY(fft_c2c<float>(ctx, n, b, c, n, q, n, (float2 *)ctx->ws[3].p, true, s));
+        k_findchirp_epilogue<<<dim3(nblk, (unsigned)b), 256, 0, s>>>(
+            q, n, sums, (int32_t)j0, thr, (uint32_t)W, cand, cap, (unsigned long long *)count);
+        RFD_LAUNCH_CHECK();
+    }
+    return RFD_OK;
+}
+
+}  // namespace rfd

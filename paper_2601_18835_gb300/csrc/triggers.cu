@@ -1,0 +1,164 @@
+// find_triggers: candidates -> one trigger per (template, window), sorted by (j, w).
+// Table II's "trigger accumulation".  Integer keys only, so the result does not depend on
+// the order in which candidates were appended.
+//
+//   1. count candidates per template;  2. exclusive scan -> bucket offsets;
+//   3. scatter into per-template buckets;  4. per template, sort its bucket by (w, key desc)
+//      and count distinct windows;  5. exclusive scan -> trigger offsets;  6. write.
+#include "internal.cuh"
+
+namespace rfd {
+
+namespace {
+
+__global__ void k_count(const rfd_candidate *__restrict__ c, const int64_t *__restrict__ count,
+                        int64_t cap, int32_t n_tmpl, int32_t *__restrict__ cnt,
+                        int32_t *__restrict__ bad) {
+    const int64_t nc = min(*count, cap);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = c[i].j;
+        if (j < (uint32_t)n_tmpl) atomicAdd(&cnt[j], 1);
+        else atomicAdd(bad, 1);
+    }
+}
+
+// Exclusive scan of int32 counts into int64 offsets with one block; out[n] = total.
+__global__ void k_scan(const int32_t *__restrict__ in, int32_t n, int64_t *__restrict__ out) {
+    __shared__ int64_t part[1024];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int32_t per = (n + nt - 1) / nt;
+    const int32_t b = min(n, tid * per), e = min(n, b + per);
+    int64_t s = 0;
+    for (int32_t i = b; i < e; ++i) s += in[i];
+    part[tid] = s;
+    __syncthreads();
+    for (int o = 1; o < nt; o <<= 1) {       // inclusive Hillis-Steele
+        const int64_t v = tid >= o ? part[tid - o] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    int64_t run = tid ? part[tid - 1] : 0;
+    for (int32_t i = b; i < e; ++i) {
+        out[i] = run;
+        run += in[i];
+    }
+    if (tid == nt - 1) out[n] = part[nt - 1];
+}
+
+__global__ void k_scatter(const rfd_candidate *__restrict__ c, const int64_t *__restrict__ count,
+                          int64_t cap, int32_t n_tmpl, const int64_t *__restrict__ off,
+                          int32_t *__restrict__ cur, rfd_candidate *__restrict__ bucket) {
+    const int64_t nc = min(*count, cap);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const rfd_candidate v = c[i];
+        if (v.j >= (uint32_t)n_tmpl) continue;
+        const int32_t p = atomicAdd(&cur[v.j], 1);
+        bucket[off[v.j] + p] = v;
+    }
+}
+
+__device__ __forceinline__ bool before(const rfd_candidate &a, const rfd_candidate &b) {
+    return a.w < b.w || (a.w == b.w && a.key > b.key);
+}
+
+__global__ void k_merge(rfd_candidate *__restrict__ bucket, const int64_t *__restrict__ off,
+                        int32_t n_tmpl, int32_t *__restrict__ ntrig) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_tmpl) return;
+    const int64_t b = off[j], e = off[j + 1];
+    for (int64_t i = b + 1; i < e; ++i) {    // insertion sort: buckets are short
+        const rfd_candidate v = bucket[i];
+        int64_t k = i - 1;
+        while (k >= b && before(v, bucket[k])) {
+            bucket[k + 1] = bucket[k];
+            --k;
+        }
+        bucket[k + 1] = v;
+    }
+    int32_t nt = 0;
+    for (int64_t i = b; i < e; ++i)
+        if (i == b || bucket[i].w != bucket[i - 1].w) ++nt;
+    ntrig[j] = nt;
+}
+
+__global__ void k_write(const rfd_candidate *__restrict__ bucket, const int64_t *__restrict__ off,
+                        const int64_t *__restrict__ toff, int32_t n_tmpl, int64_t trig_cap,
+                        rfd_trigger *__restrict__ trig) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_tmpl) return;
+    const int64_t b = off[j], e = off[j + 1];
+    int64_t o = toff[j];
+    for (int64_t i = b; i < e; ++i) {
+        if (i != b && bucket[i].w == bucket[i - 1].w) continue;
+        if (o < trig_cap) {
+            const rfd_candidate c = bucket[i];
+            rfd_trigger t;
+            t.j = j;
+            t.t = (int32_t)(0xffffffffu - (uint32_t)(c.key & 0xffffffffull));
+            t.snr2 = __uint_as_float((uint32_t)(c.key >> 32));
+            t.zr = c.zr;
+            t.zi = c.zi;
+            trig[o] = t;
+        }
+        ++o;
+    }
+}
+
+}  // namespace
+
+// Scratch: ctx->ws[12] holds the int32 / int64 arrays, ctx->ws[13] the bucketed candidates.
+rfd_status find_triggers_impl(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand,
+                              const int64_t *cand_count, int64_t cap, rfd_trigger *trig,
+                              int64_t trig_cap, int64_t *n_trig_host, cudaStream_t s) {
+    const size_t J = (size_t)n_tmpl;
+    // layout: cnt[J] cur[J] ntrig[J] bad[1] (int32, padded) | off[J+1] toff[J+1] (int64)
+    const size_t i32_bytes = ((3 * J + 1) * sizeof(int32_t) + 15) / 16 * 16;
+    const size_t bytes = i32_bytes + 2 * (J + 1) * sizeof(int64_t);
+    RFD_TRY(ensure(ctx->ws[12], bytes));
+    RFD_TRY(ensure(ctx->ws[13], (size_t)std::max<int64_t>(cap, 1) * sizeof(rfd_candidate)));
+    char *base = (char *)ctx->ws[12].p;
+    int32_t *cnt = (int32_t *)base, *cur = cnt + J, *ntrig = cur + J, *bad = ntrig + J;
+    int64_t *off = (int64_t *)(base + i32_bytes), *toff = off + (J + 1);
+    rfd_candidate *bucket = (rfd_candidate *)ctx->ws[13].p;
+    RFD_TRY_CUDA(cudaMemsetAsync(base, 0, i32_bytes, s));
+    const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(4096, (cap + 255) / 256));
+    const unsigned gj = (unsigned)((J + 255) / 256);
+    k_count<<<gb, 256, 0, s>>>(cand, cand_count, cap, n_tmpl, cnt, bad);
+    RFD_LAUNCH_CHECK();
+    k_scan<<<1, 1024, 0, s>>>(cnt, n_tmpl, off);
+    RFD_LAUNCH_CHECK();
+    k_scatter<<<gb, 256, 0, s>>>(cand, cand_count, cap, n_tmpl, off, cur, bucket);
+    RFD_LAUNCH_CHECK();
+    k_merge<<<gj, 256, 0, s>>>(bucket, off, n_tmpl, ntrig);
+    RFD_LAUNCH_CHECK();
+    k_scan<<<1, 1024, 0, s>>>(ntrig, n_tmpl, toff);
+    RFD_LAUNCH_CHECK();
+    k_write<<<gj, 256, 0, s>>>(bucket, off, toff, n_tmpl, trig_cap, trig);
+    RFD_LAUNCH_CHECK();
+    int64_t host[3] = {0, 0, 0};
+    int32_t hbad = 0;
+    RFD_TRY_CUDA(cudaMemcpyAsync(&host[0], cand_count, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RFD_TRY_CUDA(cudaMemcpyAsync(&host[1], toff + J, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RFD_TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RFD_TRY_CUDA(cudaStreamSynchronize(s));
+    RFD_REQUIRE(hbad == 0, RFD_ERR_ARG, "find_triggers: %d candidates name a template >= n_tmpl=%d",
+                hbad, n_tmpl);
+    if (host[0] > cap) {
+        *n_trig_host = host[0];
+        ::rfd::set_error("find_triggers: %lld candidates produced, capacity %lld", (long long)host[0],
+                         (long long)cap);
+        return RFD_ERR_OVERFLOW;
+    }
+    *n_trig_host = host[1];
+    if (host[1] > trig_cap) {
+        ::rfd::set_error("find_triggers: %lld triggers, capacity %lld", (long long)host[1],
+                         (long long)trig_cap);
+        return RFD_ERR_OVERFLOW;
+    }
+    return RFD_OK;
+}
+
+}  // namespace rfd

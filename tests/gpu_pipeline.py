@@ -1,0 +1,54 @@
+"""GPU side of the parity tests: the ratio-filter path through the librfd C ABI only."""
+import numpy as np
+import torch
+
+import paper_2601_18835_gb300 as rfd
+
+
+class GpuRun:
+    def __init__(self, cfg, bank, data, n=None, ctx=None):
+        self.cfg = cfg
+        self.bank = bank
+        self.n = cfg.n if n is None else n
+        self.ctx = ctx or rfd.Context(0)
+        self.grid = rfd.grid(cfg.fs, self.n, cfg.f_low, cfg.pn_flags)
+        self.psd = torch.from_numpy(data.psd).cuda()
+        self.d = torch.from_numpy(data.dtilde.astype(np.complex64)).cuda()
+
+    def make_taps(self, K, k_stride=None, match=True, tmpl_idx=None):
+        idx = np.arange(self.bank.n_tmpl) if tmpl_idx is None else np.asarray(tmpl_idx)
+        K = np.broadcast_to(np.asarray(K, dtype=np.int32), idx.shape).copy()
+        ks = int(k_stride or K.max())
+        J = len(idx)
+        taps = torch.zeros((J, ks), dtype=torch.complex64, device="cuda")
+        lag = torch.zeros(J, dtype=torch.int32, device="cuda")
+        sig = torch.zeros(J, dtype=torch.float64, device="cuda")
+        mat = torch.zeros(J, dtype=torch.float64, device="cuda") if match else None
+        rfd.make_taps(self.ctx, self.grid, self.psd, self.bank.ref_params(), self.bank.params()[idx],
+                      self.bank.ref_of_tmpl[idx], K, ks, self.cfg.tukey_alpha, taps, lag, sig, mat)
+        torch.cuda.synchronize()
+        return {"taps": taps, "lag": lag, "sigma": sig, "match": mat, "K": K, "k_stride": ks, "idx": idx}
+
+    def filter_reference(self, halo, precision):
+        R = self.bank.n_ref
+        ld = rfd.qref_ld(self.n, halo)
+        q = torch.zeros(R * ld * 8, dtype=torch.uint8, device="cuda")
+        e = torch.zeros(R, dtype=torch.int32, device="cuda")
+        rfd.filter_reference(self.ctx, self.grid, self.d, self.psd, self.bank.ref_params(), halo, precision, q, e)
+        torch.cuda.synchronize()
+        return q, e, ld
+
+    def ratio_filter(self, taps, q, e, precision, halo, cand_cap=1 << 20, trig_cap=1 << 18):
+        idx = taps["idx"]
+        plan = rfd.Plan(self.ctx, self.grid, self.bank.n_ref, self.bank.ref_of_tmpl[idx], taps["K"], precision,
+                        self.cfg.window, self.cfg.threshold, halo)
+        plan.set_taps(taps["taps"], taps["k_stride"], taps["lag"], taps["sigma"])
+        cand = torch.zeros(cand_cap * 24, dtype=torch.uint8, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        plan.ratio_filter_batch(q, e, cand, cnt)
+        trig = torch.zeros(trig_cap * 20, dtype=torch.uint8, device="cuda")
+        nt = rfd.find_triggers(self.ctx, len(idx), cand, cnt, trig)
+        out = rfd.triggers_to_numpy(trig, nt).copy()
+        ncand = int(cnt.item())
+        plan.close()
+        return out, ncand

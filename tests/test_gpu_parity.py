@@ -1,0 +1,266 @@
+"""GPU parity: every C-ABI step against the FP64 oracle on the same seeded inputs.
+
+Tolerances (stated by the method's precision targets): SNR |z| within 1e-5 relative for the
+FP32 path; trigger (j, t) bit-exact except in windows the oracle marks ambiguous under that
+tolerance; lags bit-exact; sigma_eff and match within 1e-9 (FP64 on both sides); taps within
+the complex64 rounding of their FP64 values.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workload
+from tests.oracle_pipeline import OracleRun
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2601_18835_gb300 as rfd  # noqa: E402
+from tests.gpu_pipeline import GpuRun  # noqa: E402
+
+TOL_FP32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2601_18835_gb300 import build
+    build.build()
+    c = rfd.Context(0)
+    yield c
+    c.close()
+
+
+def compare_triggers(gpu_trig, oracle_sets, tol, js, W):
+    """gpu_trig: structured array (j, t, snr2, zr, zi); oracle_sets: {j: (triggers, ambiguous)}.
+    Every non-ambiguous window must agree in (j, w, t) and in |z| within tol.  Returns the
+    number of ambiguous windows skipped."""
+    n_amb = 0
+    for j in js:
+        ot, amb = oracle_sets[j]
+        amb = set(amb)
+        o_by_w = {x["w"]: x for x in ot}
+        g_by_w = {}
+        for r in gpu_trig[gpu_trig["j"] == j]:
+            t = int(r["t"])
+            assert t // W not in g_by_w, ("two gpu triggers in one window", j, t)
+            g_by_w[t // W] = (t, float(r["snr2"]), complex(float(r["zr"]), float(r["zi"])))
+        for w in sorted(set(o_by_w) | set(g_by_w)):
+            if w in amb:
+                n_amb += 1
+                continue
+            assert w in o_by_w, ("gpu-only trigger", j, w, g_by_w.get(w))
+            assert w in g_by_w, ("oracle-only trigger", j, w, o_by_w[w])
+            t, p, z = g_by_w[w]
+            assert t == o_by_w[w]["t"], (j, w, t, o_by_w[w]["t"])
+            za = abs(o_by_w[w]["z"])
+            assert abs(math.sqrt(p) - za) <= tol * za, (j, w, math.sqrt(p), za)
+            assert abs(z - o_by_w[w]["z"]) <= 4 * tol * za
+    return n_amb
+
+
+# --------------------------------------------------------------------------- FFT
+@pytest.mark.parametrize("n,batch", [(1024, 3), (16384, 2), (524288, 2)])
+def test_ifft_matches_numpy(ctx, n, batch):
+    rng = np.random.default_rng(n)
+    x = (rng.standard_normal((batch, n)) + 1j * rng.standard_normal((batch, n))).astype(np.complex64)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    rfd.ifft_c2c(ctx, xd, out)
+    ref = np.fft.ifft(x.astype(np.complex128), axis=1) * n
+    got = out.cpu().numpy()
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    assert np.max(np.abs(got - ref)) / rms < 2e-6
+
+
+# --------------------------------------------------------------------------- templates
+def test_gen_templates_match_oracle(ctx):
+    from oracle import waveform as wf
+    cfg = workload.get_config(1)
+    bank = workload.make_bank(cfg)
+    p = bank.params()[:8]
+    g = rfd.grid(cfg.fs, cfg.n, cfg.f_low)
+    h = torch.zeros((8, cfg.n // 2 + 1), dtype=torch.complex64, device="cuda")
+    rfd.gen_templates(ctx, g, p, h)
+    got = h.cpu().numpy()
+    for i in range(8):
+        ref = wf.template(cfg.fs, cfg.n, cfg.f_low, p[i])
+        assert np.array_equal(np.nonzero(got[i])[0], np.nonzero(ref)[0])
+        assert np.max(np.abs(got[i] - ref)) <= 1e-6 * np.max(np.abs(ref))
+
+
+# --------------------------------------------------------------------------- C1 end to end
+@pytest.fixture(scope="module")
+def c1(ctx):
+    cfg = workload.get_config(1)
+    bank, data = workload.make_workload(cfg)
+    return cfg, bank, data, OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+
+
+def test_filter_reference_fp32_and_split(c1):
+    cfg, bank, data, ora, gpu = c1
+    halo = cfg.k - 1
+    q, e, ld = gpu.filter_reference(halo, rfd.PREC_FP32)
+    qg = q.view(torch.complex64).cpu().numpy()[:ld]
+    qo = ora.q_ref(0)
+    rms = np.sqrt(np.mean(np.abs(qo) ** 2))
+    assert np.max(np.abs(qg[:cfg.n] - qo)) / rms < TOL_FP32
+    assert np.array_equal(qg[cfg.n:cfg.n + halo], qg[:halo])
+    assert int(e.item()) == 0
+    for prec, ht, tol in ((rfd.PREC_FP16X3, torch.float16, 2e-6), (rfd.PREC_BF16X3, torch.bfloat16, 2e-4)):
+        qs, es, _ = gpu.filter_reference(halo, prec)
+        planes = qs.view(ht).float().cpu().numpy().astype(np.float64).reshape(4, ld)
+        scale = 2.0 ** (-int(es.item()))
+        rec = ((planes[0] + planes[2]) + 1j * (planes[1] + planes[3])) * scale
+        assert np.max(np.abs(rec[:cfg.n] - qo)) / rms < tol
+        assert np.array_equal(planes[:, cfg.n:cfg.n + halo], planes[:, :halo])
+        assert np.all(planes[:, cfg.n + halo:] == 0)
+
+
+def test_make_taps_c1_matches_oracle(c1):
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k)
+    taps = t["taps"].cpu().numpy()
+    lag = t["lag"].cpu().numpy()
+    sig = t["sigma"].cpu().numpy()
+    mat = t["match"].cpu().numpy()
+    for j in range(bank.n_tmpl):
+        o = ora.design(j, cfg.k)
+        assert lag[j] == o["lag"], (j, lag[j], o["lag"])
+        assert np.max(np.abs(taps[j] - o["taps"])) <= 2e-7 * max(1e-30, np.max(np.abs(o["taps"]))) + 1e-12
+        assert abs(sig[j] / o["sigma_eff"] - 1) < 1e-9
+        assert abs(mat[j] - o["match"]) < 1e-9
+    # identity slot: delta taps at K/2
+    assert lag[0] == -cfg.k // 2
+    d = np.zeros(cfg.k, complex)
+    d[cfg.k // 2] = 1
+    assert np.max(np.abs(taps[0] - d)) < 1e-7
+
+
+def test_c1_triggers_fp32(c1):
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP32)
+    trig, ncand = gpu.ratio_filter(t, q, e, rfd.PREC_FP32, halo)
+    sets = {}
+    for j in range(bank.n_tmpl):
+        o = ora.design(j, cfg.k, with_match=False)
+        sets[j] = ora.triggers(ora.snr(j, o), TOL_FP32)
+    n_amb = compare_triggers(trig, sets, TOL_FP32, range(bank.n_tmpl), cfg.window)
+    assert n_amb <= 2
+    # the injected template fires at the injected sample
+    m0, snr, phi, slot = data.injections[0]
+    hit = trig[(trig["j"] == slot)]
+    assert len(hit) >= 1 and abs(int(hit["t"][np.argmax(hit["snr2"])]) - m0) <= 1
+
+
+def test_c1_findchirp_matches_oracle(c1):
+    cfg, bank, data, ora, gpu = c1
+    cap = 1 << 18
+    cand = torch.zeros(cap * 24, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rfd.findchirp(gpu.ctx, gpu.grid, gpu.d, gpu.psd, bank.params(), cfg.window, cfg.threshold, cand, cnt)
+    trig = torch.zeros(cap * 20, dtype=torch.uint8, device="cuda")
+    nt = rfd.find_triggers(gpu.ctx, bank.n_tmpl, cand, cnt, trig)
+    tr = rfd.triggers_to_numpy(trig, nt)
+    sets = {j: ora.triggers(ora.findchirp(j), TOL_FP32) for j in range(bank.n_tmpl)}
+    assert compare_triggers(tr, sets, TOL_FP32, range(bank.n_tmpl), cfg.window) <= 2
+
+
+def test_ratio_peak_within_one_percent_of_findchirp_gpu(c1):
+    cfg, bank, data, ora, gpu = c1
+    m0, snr, phi, slot = data.injections[0]
+    t = gpu.make_taps(cfg.k, match=True)
+    assert t["match"].cpu().numpy()[slot] >= 0.99
+    q, e, _ = gpu.filter_reference(cfg.k - 1, rfd.PREC_FP32)
+    trig, _ = gpu.ratio_filter(t, q, e, rfd.PREC_FP32, cfg.k - 1)
+    pr = float(trig[trig["j"] == slot]["snr2"].max())
+    cap = 1 << 16
+    cand = torch.zeros(cap * 24, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rfd.findchirp(gpu.ctx, gpu.grid, gpu.d, gpu.psd, bank.params()[slot:slot + 1], cfg.window, cfg.threshold,
+                  cand, cnt)
+    tb = torch.zeros(cap * 20, dtype=torch.uint8, device="cuda")
+    nt = rfd.find_triggers(gpu.ctx, 1, cand, cnt, tb)
+    pf = float(rfd.triggers_to_numpy(tb, nt)["snr2"].max())
+    assert abs(math.sqrt(pr / pf) - 1) < 0.01
+
+
+# --------------------------------------------------------------------------- edge cases
+def test_ragged_bank_uneven_taps_and_window(ctx):
+    """37 templates (not a multiple of the tile), per-template K from 2 to 96, a window that
+    does not divide n, and a low threshold so that many windows fire."""
+    cfg = workload.small_config(1, n_tmpl=37, window=37, threshold=6.0)
+    bank, data = workload.make_workload(cfg)
+    rng = np.random.default_rng(7)
+    K = (2 * rng.integers(1, 49, size=bank.n_tmpl)).astype(np.int32)
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(K, k_stride=128, match=False)
+    halo = int(K.max()) - 1
+    q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP32)
+    trig, ncand = gpu.ratio_filter(t, q, e, rfd.PREC_FP32, halo, cand_cap=1 << 22)
+    lag = t["lag"].cpu().numpy()
+    sets = {}
+    for j in range(bank.n_tmpl):
+        o = ora.design(j, int(K[j]), with_match=False)
+        assert lag[j] == o["lag"]
+        sets[j] = ora.triggers(ora.snr(j, o), TOL_FP32)
+    assert sum(len(s[0]) for s in sets.values()) > 1000
+    n_amb = compare_triggers(trig, sets, TOL_FP32, range(bank.n_tmpl), cfg.window)
+    assert n_amb <= 10
+
+
+def test_candidate_overflow_is_reported(c1):
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k, match=False)
+    q, e, _ = gpu.filter_reference(cfg.k - 1, rfd.PREC_FP32)
+    with pytest.raises(rfd.RfdError) as ei:
+        gpu.ratio_filter(t, q, e, rfd.PREC_FP32, cfg.k - 1, cand_cap=2)
+    assert ei.value.status == -7 and ei.value.needed > 2
+
+
+def test_bad_arguments_are_rejected(ctx):
+    g = rfd.grid(1024.0, 1000, 30.0)                      # not a power of two
+    h = torch.zeros((1, 501), dtype=torch.complex64, device="cuda")
+    with pytest.raises(rfd.RfdError) as ei:
+        rfd.gen_templates(ctx, g, np.array([[1.4, 1.4, 0, 0, 0]]), h)
+    assert ei.value.status == -2
+    g = rfd.grid(1024.0, 16384, 30.0)
+    with pytest.raises(rfd.RfdError) as ei:
+        rfd.gen_templates(ctx, g, np.array([[-1.0, 1.4, 0, 0, 0]]), torch.zeros((1, 8193), dtype=torch.complex64,
+                                                                              device="cuda"))
+    assert ei.value.status == -1
+
+
+# --------------------------------------------------------------------------- full size, sampled
+@pytest.mark.slow
+def test_c2_full_size_fp32_sampled(ctx):
+    """The 256 s / 2048 Hz bank (4096 templates, 16 references, K = 128) end to end on the GPU;
+    the oracle checks a stratified sample: every injected template plus one per reference."""
+    cfg = workload.get_config(2)
+    bank, data = workload.make_workload(cfg)
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(cfg.k, match=True)
+    halo = cfg.k - 1
+    q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP32)
+    trig, ncand = gpu.ratio_filter(t, q, e, rfd.PREC_FP32, halo)
+    lag, sig, mat = (t[k].cpu().numpy() for k in ("lag", "sigma", "match"))
+    sample = sorted({s for (_, _, _, s) in data.injections}
+                    | {int(np.nonzero(bank.ref_of_tmpl == r)[0][0]) for r in range(0, bank.n_ref, 4)})
+    sets = {}
+    for j in sample:
+        o = ora.design(j, cfg.k)
+        assert lag[j] == o["lag"]
+        assert abs(sig[j] / o["sigma_eff"] - 1) < 1e-9
+        assert abs(mat[j] - o["match"]) < 1e-8
+        z = ora.snr(j, o)
+        sets[j] = ora.triggers(z, TOL_FP32)
+        g = trig[trig["j"] == j]
+        if len(g):
+            zo = ora.snr_at(j, o, g["t"].astype(np.int64))
+            assert np.max(np.abs(np.sqrt(g["snr2"]) - np.abs(zo)) / np.abs(zo)) < TOL_FP32
+    assert compare_triggers(trig, sets, TOL_FP32, sample, cfg.window) <= 2
