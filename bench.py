@@ -1,0 +1,482 @@
+#!/usr/bin/env python3
+"""Benchmark of the ratio-filter search step on one data segment per GPU.
+
+A step is one pass of the per-segment hot path over one synthetic segment:
+  filter_reference (reference templates + matched filter + Stockham IFFT + split/halo),
+  ratio_filter_batch (FIR of every template on its reference series + fused triggers),
+  find_triggers (per-window maxima, read back to the host).
+Tap design (make_taps) is per-bank set-up, done once before timing and reported apart.
+
+Metric: template-seconds filtered per second = n_templates * segment duration / step time,
+summed over ranks (weak scaling: every rank filters its own segment with the same bank).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp16x3|bf16x3|fp32]
+  python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample
+"""
+import argparse
+import dataclasses
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "template-seconds filtered/s at ≤1e-3 SNR rel err vs FP64; vs FP32 FIR & FINDCHIRP"
+UNIT = "template-s/s"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp16x3", "bf16x3"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32-FIR / FINDCHIRP comparison runs")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--n-tmpl", type=int, default=None, help="smaller bank (profiling cases only)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ts, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            rows.append((ts, parts))
+        inside = [p for ts, p in rows if t0 <= ts <= t1] or [p for _, p in rows]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[0]) for p in inside if num(p[0]) is not None]
+        mx = [num(p[1]) for p in inside if num(p[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in inside for i in range(4) if p[4 + i].lower().startswith("active")})
+        pw = [num(p[2]) for p in inside if num(p[2]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inside), "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def kernel_source_hash(name):
+    path = os.path.join(ROOT, "paper_2601_18835_gb300", "csrc", name)
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel, source):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    with open(PROFILE_TRAFFIC) as fh:
+        rec = json.load(fh).get(kernel)
+    if not rec or rec.get("source_sha") != kernel_source_hash(source):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+PREC = {"fp32": 0, "fp16x3": 1, "bf16x3": 2}
+
+
+def workload_for_rank(c, rank, n_tmpl=None):
+    import workload
+    cfg = workload.get_config(c)
+    if n_tmpl:
+        cfg = dataclasses.replace(cfg, n_tmpl=n_tmpl, n_ref=min(cfg.n_ref, n_tmpl))
+    if rank:
+        # every rank filters its own segment: same bank, its own noise realisation
+        cfg = dataclasses.replace(cfg, seeds=(cfg.seeds[0], cfg.seeds[1] + 7919 * rank, cfg.seeds[2]))
+    bank, data = workload.make_workload(cfg)
+    return cfg, bank, data
+
+
+# ------------------------------------------------------------------------------- oracle arm
+def oracle_sample(cfg, bank, data, n_templates):
+    """Set-up for timing the FP64 oracle: one reference series and the taps of the first
+    n_templates templates assigned to it (untimed)."""
+    from tests.oracle_pipeline import OracleRun
+    ora = OracleRun(cfg, bank, data)
+    r = int(bank.ref_of_tmpl[0])
+    js = [int(j) for j in np.nonzero(bank.ref_of_tmpl == r)[0][:n_templates]]
+    designs = [ora.design(j, cfg.k, with_match=False) for j in js]
+    return ora, js, designs
+
+
+def oracle_step(cfg, ora, j, design):
+    """One template through the oracle's ratio path: direct circular FIR (Eq. 3) + triggers."""
+    from oracle import triggers
+    z = ora.snr(j, design)
+    return triggers.window_triggers(z, cfg.window, cfg.threshold)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cfg, bank, data = workload_for_rank(args.config, 0)
+    t_setup = time.perf_counter()
+    ora, js, designs = oracle_sample(cfg, bank, data, 4)
+    ora.q_ref(int(bank.ref_of_tmpl[js[0]]))
+    t_setup = time.perf_counter() - t_setup
+    for i in range(args.warmup):
+        oracle_step(cfg, ora, js[i % len(js)], designs[i % len(js)])
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(cfg, ora, js[i % len(js)], designs[i % len(js)])
+        times.append(time.perf_counter() - t0)
+    mean = sum(times) / len(times)
+    value = cfg.duration / mean
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg.name, "n_tmpl": cfg.n_tmpl, "n_ref": cfg.n_ref, "k": cfg.k, "n": cfg.n,
+                   "fs": cfg.fs},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "each step: one template of the bank through the FP64 oracle's direct "
+                                   "circular FIR (K=%d, n=%d) and window-max triggers, reference series and "
+                                   "taps precomputed (set-up %.1f s)" % (cfg.k, cfg.n, t_setup)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------- GPU arm
+class GpuSearch:
+    def __init__(self, cfg, bank, data, precision, device):
+        import torch
+        import paper_2601_18835_gb300 as rfd
+        self.torch, self.rfd = torch, rfd
+        self.cfg, self.bank = cfg, bank
+        self.prec = precision
+        self.ctx = rfd.Context(device)
+        self.grid = rfd.grid(cfg.fs, cfg.n, cfg.f_low, cfg.pn_flags)
+        self.psd = torch.from_numpy(data.psd).cuda()
+        d64 = data.dtilde.astype(np.complex64)
+        self.d_host = torch.from_numpy(d64).pin_memory()
+        self.d = self.d_host.cuda()
+        J = bank.n_tmpl
+        self.K = np.full(J, cfg.k, dtype=np.int32)
+        self.halo = cfg.k - 1
+        self.taps = torch.zeros((J, cfg.k), dtype=torch.complex64, device="cuda")
+        self.lag = torch.zeros(J, dtype=torch.int32, device="cuda")
+        self.sig = torch.zeros(J, dtype=torch.float64, device="cuda")
+        self.match = torch.zeros(J, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rfd.make_taps(self.ctx, self.grid, self.psd, bank.ref_params(), bank.params(), bank.ref_of_tmpl, self.K,
+                      cfg.k, cfg.tukey_alpha, self.taps, self.lag, self.sig, self.match)
+        torch.cuda.synchronize()
+        self.make_taps_s = time.perf_counter() - t0
+        self.ld = rfd.qref_ld(cfg.n, self.halo)
+        self.q = torch.zeros(bank.n_ref * self.ld * 8, dtype=torch.uint8, device="cuda")
+        self.e = torch.zeros(bank.n_ref, dtype=torch.int32, device="cuda")
+        self.plan = rfd.Plan(self.ctx, self.grid, bank.n_ref, bank.ref_of_tmpl, self.K, precision, cfg.window,
+                             cfg.threshold, self.halo)
+        self.plan.set_taps(self.taps, cfg.k, self.lag, self.sig)
+        self.ctx.trim()          # drop the FP64 tap-design workspaces
+        self.cand_cap = 1 << 22
+        self.cand = torch.zeros(self.cand_cap * 24, dtype=torch.uint8, device="cuda")
+        self.cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        self.trig_cap = 1 << 20
+        self.trig = torch.zeros(self.trig_cap * 20, dtype=torch.uint8, device="cuda")
+        self.trig_host = torch.zeros(self.trig_cap * 20, dtype=torch.uint8).pin_memory()
+        self.flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        self.stream = torch.cuda.current_stream()
+
+    def flush_l2(self):
+        self.flush_buf.random_(0, 255)
+
+    def step(self, ev=None):
+        rfd = self.rfd
+        if ev:
+            ev[0].record()
+        rfd.filter_reference(self.ctx, self.grid, self.d, self.psd, self.bank.ref_params(), self.halo, self.prec,
+                             self.q, self.e)
+        if ev:
+            ev[1].record()
+        self.plan.ratio_filter_batch(self.q, self.e, self.cand, self.cnt)
+        if ev:
+            ev[2].record()
+        nt = rfd.find_triggers(self.ctx, self.bank.n_tmpl, self.cand, self.cnt, self.trig)
+        if ev:
+            ev[3].record()
+        return nt
+
+    def step_e2e(self):
+        """Through host buffers: H2D of the data spectrum, the step, D2H of the triggers."""
+        self.d.copy_(self.d_host, non_blocking=True)
+        nt = self.step()
+        self.trig_host[: nt * 20].copy_(self.trig[: nt * 20], non_blocking=False)
+        return nt
+
+    def close(self):
+        self.plan.close()
+        self.ctx.close()
+
+
+def findchirp_rate(cfg, bank, data, device, steps=2):
+    """FINDCHIRP (Eq. 1 per template: PN template, pointwise, Stockham IFFT, same triggers)."""
+    import torch
+    import paper_2601_18835_gb300 as rfd
+    ctx = rfd.Context(device)
+    g = rfd.grid(cfg.fs, cfg.n, cfg.f_low, cfg.pn_flags)
+    psd = torch.from_numpy(data.psd).cuda()
+    d = torch.from_numpy(data.dtilde.astype(np.complex64)).cuda()
+    cap = 1 << 22
+    cand = torch.zeros(cap * 24, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    trig = torch.zeros((1 << 20) * 20, dtype=torch.uint8, device="cuda")
+    params = bank.params()
+
+    def one():
+        rfd.findchirp(ctx, g, d, psd, params, cfg.window, cfg.threshold, cand, cnt)
+        return rfd.find_triggers(ctx, bank.n_tmpl, cand, cnt, trig)
+    one()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        one()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    ctx.close()
+    t = sum(times) / len(times)
+    return bank.n_tmpl * cfg.duration / t, t
+
+
+def run_ours(args):
+    import torch
+    import paper_2601_18835_gb300 as rfd
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    torch.cuda.set_device(local)
+    precision_name = args.precision or getattr(rfd, "DEFAULT_PRECISION_NAME", "fp32")
+    prec = PREC[precision_name]
+    cfg, bank, data = workload_for_rank(args.config, rank, args.n_tmpl)
+    s = GpuSearch(cfg, bank, data, prec, local)
+    J, dur = bank.n_tmpl, cfg.duration
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        s.flush_l2()
+        s.step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = rfd.kernel_launches()
+    torch.cuda.profiler.start()      # ncu --profile-from-start off sees only the timed steps
+    w0 = time.perf_counter()
+    ntrig = 0
+    for i in range(args.steps):
+        s.flush_l2()
+        ntrig = s.step(evs[i])
+    torch.cuda.synchronize()
+    w1 = time.perf_counter()
+    torch.cuda.profiler.stop()
+    barrier()
+    launches = rfd.kernel_launches() - l0
+    clk = clocks.stop(w0, w1)
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    filt_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    ref_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    ms = sum(step_ms) / len(step_ms)
+    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = ws * J * dur / (ms_max / 1e3)
+
+    # end to end through host buffers
+    for _ in range(2):
+        s.step_e2e()
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        s.flush_l2()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nt = s.step_e2e()
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = torch.tensor([sum(e2e_t) / len(e2e_t)], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(e2e_s, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = ws * J * dur / float(e2e_s.item())
+
+    # roofline of the dominant kernel: the ratio-filter contraction
+    peaks, peak_kind = measured_peaks()
+    filt_s = sum(filt_ms) / len(filt_ms) / 1e3
+    alg_flops = 8.0 * cfg.k * J * cfg.n
+    if prec == 0:
+        kernel, src = "k_fir32", "fir32.cu"
+        # FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+        peak_tf = 152 * 128 * 2 * 2.07e9 / 1e12
+        roof = {"bound": "alu", "achieved": alg_flops / filt_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    else:
+        kernel, src = "k_rf_tc", "rf_tc.cu"
+        peak_tf = peaks["bf16_tflops_sustained"]
+        exec_flops = getattr(rfd, "executed_flops", lambda c: 3 * alg_flops)(cfg)
+        roof = {"bound": "tensor", "achieved": alg_flops / filt_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                "peak_source": "%s bf16 dense sustained (fp16 has the same dense rate)" % peak_kind,
+                "executed_tflops": exec_flops / filt_s / 1e12,
+                "executed_frac": exec_flops / filt_s / 1e12 / peak_tf}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = recorded_traffic(kernel, src)
+    roof["kernel"] = kernel
+    roof["kernel_ms"] = filt_s * 1e3
+    roof["algorithmic_flops_per_launch"] = alg_flops
+
+    comparisons = {}
+    if not args.no_compare and rank == 0:
+        if prec != 0:
+            s32 = GpuSearch(cfg, bank, data, 0, local)
+            for _ in range(2):
+                s32.step()
+            torch.cuda.synchronize()
+            tt = []
+            for _ in range(3):
+                s32.flush_l2()
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                s32.step(e)
+                torch.cuda.synchronize()
+                tt.append(e[0].elapsed_time(e[3]))
+            comparisons["fp32_fir_step"] = {"value": J * dur / (sum(tt) / len(tt) / 1e3), "unit": UNIT,
+                                            "ms_per_step": sum(tt) / len(tt)}
+            s32.close()
+        fc_value, fc_t = findchirp_rate(cfg, bank, data, local)
+        comparisons["findchirp"] = {"value": fc_value, "unit": UNIT, "ms_per_step": fc_t * 1e3}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        ora, js, designs = oracle_sample(cfg, bank, data, 4)
+        t0 = time.perf_counter()
+        ora.q_ref(int(bank.ref_of_tmpl[js[0]]))
+        for j, d in zip(js, designs):
+            oracle_step(cfg, ora, j, d)
+        el = time.perf_counter() - t0
+        cpu = {"value": len(js) * dur / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one reference's FP64 matched filter plus %d templates through the oracle's direct "
+                         "circular FIR (K=%d, n=%d) and triggers; taps precomputed; %.1f s" % (len(js), cfg.k,
+                                                                                              cfg.n, el)}
+
+    match = s.match.cpu().numpy()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": precision_name, "data": "synthetic",
+        "config": {"workload": cfg.name, "n_tmpl": J, "n_ref": bank.n_ref, "k": cfg.k, "n": cfg.n, "fs": cfg.fs,
+                   "segment_s": dur, "window": cfg.window, "threshold": cfg.threshold,
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if ws > 1 else "single"},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s.d_host.numel() * 8),
+                "d2h_bytes_per_step": int(nt * 20 + 8 * 3)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "comparisons": comparisons,
+        "breakdown_ms": {"filter_reference": sum(ref_ms) / len(ref_ms), "ratio_filter_batch": filt_s * 1e3,
+                         "find_triggers": ms - sum(ref_ms) / len(ref_ms) - filt_s * 1e3},
+        "setup": {"make_taps_s": s.make_taps_s, "taps_match_ge_0p99": float(np.mean(match >= 0.99)),
+                  "taps_match_median": float(np.median(match))},
+        "triggers_per_step": int(ntrig),
+    }
+    s.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
