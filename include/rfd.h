@@ -104,6 +104,9 @@ int64_t rfd_kernel_launches(void);
  * The context is not thread-safe: use one per host thread. */
 rfd_status rfd_ctx_create(int32_t device, rfd_ctx **out);
 void rfd_ctx_destroy(rfd_ctx *ctx);
+/* Frees the context's scratch workspaces (they are re-created on demand).  Synchronises the
+ * device. */
+void rfd_ctx_trim(rfd_ctx *ctx);
 
 /* Elements per reference row of a q_ref buffer: n + halo rounded up to a multiple of 64.
  * A q_ref buffer holds n_ref * 8 * rfd_qref_ld(n, halo) bytes in every precision. */

@@ -81,6 +81,10 @@ class Context:
         self.handle = h
         self.device = int(device)
 
+    def trim(self):
+        """Free the scratch workspaces (re-created on demand)."""
+        _lib().rfd_ctx_trim(self.handle)
+
     def close(self):
         if self.handle:
             _lib().rfd_ctx_destroy(self.handle)

@@ -54,6 +54,7 @@ SIGNATURES = {
     "rfd_kernel_launches": (_i64, []),
     "rfd_ctx_create": (_i32, [_i32, ctypes.POINTER(_vp)]),
     "rfd_ctx_destroy": (None, [_vp]),
+    "rfd_ctx_trim": (None, [_vp]),
     "rfd_qref_ld": (_i64, [_i64, _i32]),
     "rfd_gen_templates": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _i32, _vp, _vp]),
     "rfd_make_taps": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _i32, _dbl,

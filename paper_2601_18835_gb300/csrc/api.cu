@@ -177,6 +177,13 @@ void rfd_ctx_destroy(rfd_ctx *ctx) {
     delete ctx;
 }
 
+void rfd_ctx_trim(rfd_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &b : ctx->ws) release(b);
+}
+
 rfd_status rfd_gen_templates(rfd_ctx *ctx, const rfd_grid *grid, const rfd_params *params_host,
                              int32_t n_tmpl, void *h_dev, void *stream) {
     RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
