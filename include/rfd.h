@@ -215,6 +215,30 @@ rfd_status rfd_find_triggers(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *
                              rfd_trigger *trig_dev, int64_t trig_capacity,
                              int64_t *n_trig_host, void *stream);
 
+/* ------------------------------------------------------------------ find_triggers, no allocation
+ * The same merge as rfd_find_triggers, for callers that cannot allocate device memory while
+ * they run: code that must not call cudaMalloc / cudaFree once set up (both can synchronise
+ * the whole device and stall other streams, which low-latency search loops cannot afford),
+ * callers whose device memory is owned by another allocator or memory pool, and callers that
+ * hold no librfd context.  The paper has no counterpart; this is a deployment variant.
+ *
+ * It allocates nothing.  Its scratch is one fixed array of static device memory (about 4 MB,
+ * sized for RFD_NOALLOC_MAX_TEMPLATES templates and RFD_NOALLOC_MAX_CANDIDATES candidates)
+ * that every GPU loading librfd holds until the process exits.  It runs on the calling
+ * thread's current device.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * n_tmpl > RFD_NOALLOC_MAX_TEMPLATES or cand_capacity > RFD_NOALLOC_MAX_CANDIDATES is
+ * rejected with RFD_ERR_SHAPE before anything runs.  Every call on a device shares the one
+ * array: each call clears the counters it needs, but calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the caller.
+ * Arguments, outputs, synchronisation and RFD_ERR_OVERFLOW as for rfd_find_triggers. */
+#define RFD_NOALLOC_MAX_TEMPLATES 32768
+#define RFD_NOALLOC_MAX_CANDIDATES 131072
+rfd_status rfd_find_triggers_noalloc(int32_t n_tmpl, const rfd_candidate *cand_dev,
+                                     const int64_t *cand_count_dev, int64_t cand_capacity,
+                                     rfd_trigger *trig_dev, int64_t trig_capacity,
+                                     int64_t *n_trig_host, void *stream);
+
 /* ------------------------------------------------------------------ FINDCHIRP baseline
  * The standard frequency-domain matched filter of Eq. 1 for every template (Sec. II-III):
  * per template, h_j on the grid (FP64 phase), c = 4 df d conj(h_j) / S, an n-point FP32

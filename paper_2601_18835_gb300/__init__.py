@@ -20,7 +20,7 @@ from ._native import (CANDIDATE_DTYPE, PN_SO, PN_TIDAL, PREC_BF16X3, PREC_FP16X3
                       TRIGGER_DTYPE, RfdError, check)
 
 __all__ = ["Context", "Plan", "grid", "gen_templates", "make_taps", "filter_reference",
-           "find_triggers", "findchirp", "ifft_c2c", "qref_ld", "candidates_to_numpy",
+           "find_triggers", "find_triggers_noalloc", "findchirp", "ifft_c2c", "qref_ld", "candidates_to_numpy",
            "triggers_to_numpy", "CANDIDATE_DTYPE", "TRIGGER_DTYPE"]
 
 
@@ -163,6 +163,18 @@ def find_triggers(ctx, n_tmpl, cand, cand_count, trig, stream=None):
     n = ctypes.c_int64(0)
     st = _lib().rfd_find_triggers(ctx.handle, int(n_tmpl), _ptr(cand), _ptr(cand_count), int(cap),
                                   _ptr(trig), int(tcap), ctypes.byref(n), _stream(stream))
+    check(st, needed=n.value)
+    return int(n.value)
+
+
+def find_triggers_noalloc(n_tmpl, cand, cand_count, trig, stream=None):
+    """find_triggers without any device allocation (static scratch, fixed maximum sizes);
+    runs on the current CUDA device.  Returns the number of triggers."""
+    cap = cand.numel() * cand.element_size() // CANDIDATE_DTYPE.itemsize
+    tcap = trig.numel() * trig.element_size() // TRIGGER_DTYPE.itemsize
+    n = ctypes.c_int64(0)
+    st = _lib().rfd_find_triggers_noalloc(int(n_tmpl), _ptr(cand), _ptr(cand_count), int(cap), _ptr(trig),
+                                          int(tcap), ctypes.byref(n), _stream(stream))
     check(st, needed=n.value)
     return int(n.value)
 

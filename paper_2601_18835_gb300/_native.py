@@ -24,6 +24,8 @@ PN_TIDAL = 2
 PREC_FP32 = 0
 PREC_FP16X3 = 1
 PREC_BF16X3 = 2
+NOALLOC_MAX_TEMPLATES = 32768
+NOALLOC_MAX_CANDIDATES = 131072
 
 
 class Grid(ctypes.Structure):
@@ -67,6 +69,7 @@ SIGNATURES = {
     "rfd_plan_set_taps": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
     "rfd_ratio_filter_batch": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "rfd_find_triggers": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(_i64), _vp]),
+    "rfd_find_triggers_noalloc": (_i32, [_i32, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(_i64), _vp]),
     "rfd_findchirp": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _vp, _i32, _i32, _flt, _vp, _i64, _vp,
                              _vp]),
     "rfd_ifft_c2c": (_i32, [_vp, _i64, _i32, _vp, _vp, _vp]),

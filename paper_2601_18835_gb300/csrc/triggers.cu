@@ -162,3 +162,101 @@ rfd_status find_triggers_impl(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate 
 }
 
 }  // namespace rfd
+
+// ------------------------------------------------------------------ no-allocation variant
+// rfd_find_triggers_noalloc runs the same six kernels with its scratch in a fixed,
+// file-scope device array instead of context workspaces, so it never allocates.  The array
+// lives in every GPU that loads this library until the process exits.  Host code cannot use
+// the array's name as a device address, so the address is looked up once per device with
+// cudaGetSymbolAddress and cached.
+#include <mutex>
+
+namespace rfd {
+namespace {
+
+constexpr size_t kNaI32Bytes = ((3 * (size_t)RFD_NOALLOC_MAX_TEMPLATES + 1) * sizeof(int32_t) + 255) / 256 * 256;
+constexpr size_t kNaI64Bytes = (2 * ((size_t)RFD_NOALLOC_MAX_TEMPLATES + 1) * sizeof(int64_t) + 255) / 256 * 256;
+constexpr size_t kNaScratchBytes = kNaI32Bytes + kNaI64Bytes +
+                                   (size_t)RFD_NOALLOC_MAX_CANDIDATES * sizeof(rfd_candidate);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kNaMaxDevices] = {};
+
+}  // namespace
+}  // namespace rfd
+
+extern "C" rfd_status rfd_find_triggers_noalloc(int32_t n_tmpl, const rfd_candidate *cand_dev,
+                                                const int64_t *cand_count_dev, int64_t cand_capacity,
+                                                rfd_trigger *trig_dev, int64_t trig_capacity,
+                                                int64_t *n_trig_host, void *stream) {
+    using namespace rfd;
+    RFD_REQUIRE(n_tmpl >= 1 && n_tmpl <= RFD_NOALLOC_MAX_TEMPLATES, RFD_ERR_SHAPE,
+                "find_triggers_noalloc: n_tmpl=%d outside [1, %d] (the static scratch maximum)", n_tmpl,
+                RFD_NOALLOC_MAX_TEMPLATES);
+    RFD_REQUIRE(cand_capacity >= 0 && cand_capacity <= RFD_NOALLOC_MAX_CANDIDATES, RFD_ERR_SHAPE,
+                "find_triggers_noalloc: cand_capacity=%lld outside [0, %d] (the static scratch maximum)",
+                (long long)cand_capacity, RFD_NOALLOC_MAX_CANDIDATES);
+    RFD_REQUIRE(trig_capacity >= 0, RFD_ERR_SHAPE, "negative trigger capacity");
+    RFD_REQUIRE(cand_count_dev && n_trig_host && (cand_dev || cand_capacity == 0) && (trig_dev || trig_capacity == 0),
+                RFD_ERR_ARG, "NULL argument");
+    int dev = 0;
+    RFD_TRY_CUDA(cudaGetDevice(&dev));
+    RFD_REQUIRE(dev >= 0 && dev < kNaMaxDevices, RFD_ERR_UNSUPPORTED, "device index %d too large", dev);
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            RFD_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t J = (size_t)n_tmpl;
+    char *b = (char *)base;
+    int32_t *cnt = (int32_t *)b, *cur = cnt + J, *ntrig = cur + J, *bad = ntrig + J;
+    int64_t *off = (int64_t *)(b + kNaI32Bytes), *toff = off + (J + 1);
+    rfd_candidate *bucket = (rfd_candidate *)(b + kNaI32Bytes + kNaI64Bytes);
+    // the array keeps the previous call's contents: clear the counters this call accumulates into
+    const size_t i32_bytes = (3 * J + 1) * sizeof(int32_t);
+    RFD_TRY_CUDA(cudaMemsetAsync(cnt, 0, i32_bytes, s));
+    const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(4096, (cand_capacity + 255) / 256));
+    const unsigned gj = (unsigned)((J + 255) / 256);
+    k_count<<<gb, 256, 0, s>>>(cand_dev, cand_count_dev, cand_capacity, n_tmpl, cnt, bad);
+    RFD_LAUNCH_CHECK();
+    k_scan<<<1, 1024, 0, s>>>(cnt, n_tmpl, off);
+    RFD_LAUNCH_CHECK();
+    k_scatter<<<gb, 256, 0, s>>>(cand_dev, cand_count_dev, cand_capacity, n_tmpl, off, cur, bucket);
+    RFD_LAUNCH_CHECK();
+    k_merge<<<gj, 256, 0, s>>>(bucket, off, n_tmpl, ntrig);
+    RFD_LAUNCH_CHECK();
+    k_scan<<<1, 1024, 0, s>>>(ntrig, n_tmpl, toff);
+    RFD_LAUNCH_CHECK();
+    k_write<<<gj, 256, 0, s>>>(bucket, off, toff, n_tmpl, trig_capacity, trig_dev);
+    RFD_LAUNCH_CHECK();
+    int64_t host[2] = {0, 0};
+    int32_t hbad = 0;
+    RFD_TRY_CUDA(cudaMemcpyAsync(&host[0], cand_count_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RFD_TRY_CUDA(cudaMemcpyAsync(&host[1], toff + J, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RFD_TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RFD_TRY_CUDA(cudaStreamSynchronize(s));
+    RFD_REQUIRE(hbad == 0, RFD_ERR_ARG, "find_triggers_noalloc: %d candidates name a template >= n_tmpl=%d", hbad,
+                n_tmpl);
+    if (host[0] > cand_capacity) {
+        *n_trig_host = host[0];
+        set_error("find_triggers_noalloc: %lld candidates produced, capacity %lld", (long long)host[0],
+                  (long long)cand_capacity);
+        return RFD_ERR_OVERFLOW;
+    }
+    *n_trig_host = host[1];
+    if (host[1] > trig_capacity) {
+        set_error("find_triggers_noalloc: %lld triggers, capacity %lld", (long long)host[1],
+                  (long long)trig_capacity);
+        return RFD_ERR_OVERFLOW;
+    }
+    return RFD_OK;
+}
