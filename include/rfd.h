@@ -197,10 +197,18 @@ rfd_status rfd_plan_set_taps(rfd_plan *plan, const void *taps_dev, int32_t k_str
  * qref_dev / qscale_dev as written by rfd_filter_reference in the plan's precision.
  * cand_dev rfd_candidate [cand_capacity]; cand_count_dev int64 (device) is reset to 0 by this
  * call, then counts every candidate produced, including those past the capacity (which are
- * dropped; rfd_find_triggers reports RFD_ERR_OVERFLOW and the needed capacity). */
+ * dropped; rfd_find_triggers reports RFD_ERR_OVERFLOW and the needed capacity).
+ * RFD_PREC_FP32 runs an FP32 CUDA-core FIR.  RFD_PREC_FP16X3 / BF16X3 run the tcgen05 kernel:
+ * taps and q are split into hi + lo parts and the complex product is formed from three
+ * real-block-form products hi*hi + hi*lo + lo*hi accumulated in FP32 (K <= 512; the plan's halo
+ * must cover K rounded up to 16).  Its waits are bounded: a wait that gives up sets bit 62 of
+ * *cand_count_dev, which rfd_find_triggers reports as RFD_ERR_TIMEOUT. */
 rfd_status rfd_ratio_filter_batch(rfd_plan *plan, const void *qref_dev,
                                   const int32_t *qscale_dev, rfd_candidate *cand_dev,
                                   int64_t cand_capacity, int64_t *cand_count_dev, void *stream);
+
+/* Tensor-core (or FMA) flops one rfd_ratio_filter_batch call of this plan executes. */
+double rfd_plan_executed_flops(const rfd_plan *plan);
 
 /* ------------------------------------------------------------------ find_triggers
  * Merges candidates into triggers: per (j, w) the maximum key (the largest |z|^2, ties to the

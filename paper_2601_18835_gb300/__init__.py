@@ -144,6 +144,10 @@ class Plan:
         check(_lib().rfd_ratio_filter_batch(self.handle, _ptr(qref), _ptr(qscale), _ptr(cand), int(cap),
                                             _ptr(cand_count), _stream(stream)))
 
+    def executed_flops(self):
+        """Flops one ratio_filter_batch call executes (tensor-core or FMA)."""
+        return float(_lib().rfd_plan_executed_flops(self.handle))
+
     def close(self):
         if self.handle:
             _lib().rfd_plan_destroy(self.handle)

@@ -67,6 +67,7 @@ SIGNATURES = {
                                ctypes.POINTER(_vp)]),
     "rfd_plan_destroy": (None, [_vp]),
     "rfd_plan_set_taps": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
+    "rfd_plan_executed_flops": (_dbl, [_vp]),
     "rfd_ratio_filter_batch": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "rfd_find_triggers": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(_i64), _vp]),
     "rfd_find_triggers_noalloc": (_i32, [_i32, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(_i64), _vp]),

@@ -28,6 +28,78 @@ rfd_status fir32_launch(const rfd_plan *, const float2 *, rfd_candidate *, int64
                         cudaStream_t);
 rfd_status pack_taps_fp32(rfd_plan *, const float2 *, int32_t, const int32_t *, const double *,
                           cudaStream_t);
+rfd_status tc_pack(rfd_plan *, const float2 *, int32_t, const int32_t *, const double *, cudaStream_t);
+rfd_status tc_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
+                     cudaStream_t);
+int tc_rows_per_item();
+
+// Tensor-core tiles: per reference, templates in increasing K, cut so that a tile holds at
+// most 64 templates (32 once its K exceeds 256); item ranges per CTA balance the MMA work.
+static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &order, int num_sms) {
+    const int64_t n_tt = p->grid.n / tc_rows_per_item();
+    int64_t taps_off = 0;
+    int32_t kpad_max = 0;
+    uint32_t cap = 0;
+    size_t i = 0;
+    while (i < order.size()) {
+        const int32_t r = p->ref_of[order[i]];
+        TcTile t{};
+        t.ref = r;
+        t.first = (int32_t)p->perm.size();
+        while (i < order.size() && p->ref_of[order[i]] == r) {
+            const int32_t kt = std::max(t.k_tile, p->k_of[order[i]]);
+            const int32_t ntc = kt <= 256 ? 64 : 32;
+            if (t.count + 1 > ntc) break;
+            t.k_tile = kt;
+            ++t.count;
+            p->perm.push_back(order[i]);
+            ++i;
+        }
+        t.nt = t.k_tile <= 256 ? 64 : 32;
+        t.nk16 = (t.k_tile + 15) / 16;
+        t.kpad = 16 * t.nk16;
+        t.nch = (t.kpad + 63) / 64;
+        t.taps_bytes = 2 * t.nch * 2 * t.nt * 128;
+        t.taps_off = taps_off;
+        taps_off += t.taps_bytes;
+        kpad_max = std::max(kpad_max, t.kpad);
+        cap = std::max(cap, (uint32_t)t.taps_bytes);
+        p->tc_tiles.push_back(t);
+        p->executed_flops += (double)n_tt * t.nk16 * 2.0 * 128.0 * 16.0 * 12.0 * t.nt;
+    }
+    p->n_slots = (int64_t)p->perm.size();
+    p->tc_taps_cap = (cap + 1023u) / 1024u * 1024u;
+    p->tc_win = (uint32_t)(128 + kpad_max + 8);
+    RFD_REQUIRE(p->ld >= p->grid.n + kpad_max, RFD_ERR_SHAPE,
+                "tensor-core path reads %d taps past each block: halo=%d too small (need >= %d)", kpad_max,
+                p->halo, kpad_max - 1);
+    // cost-balanced contiguous item ranges, one per CTA
+    const int64_t ntiles = (int64_t)p->tc_tiles.size();
+    const int64_t total_items = ntiles * n_tt;
+    std::vector<double> cost(ntiles), prefix(ntiles + 1, 0.0);
+    for (int64_t t = 0; t < ntiles; ++t) {
+        cost[t] = (double)p->tc_tiles[t].nk16 * p->tc_tiles[t].nt + 16.0;
+        prefix[t + 1] = prefix[t] + cost[t] * n_tt;
+    }
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(num_sms, total_items));
+    std::vector<int64_t> ranges(G + 1, 0);
+    ranges[G] = total_items;
+    int64_t t = 0;
+    for (int64_t g = 1; g < G; ++g) {
+        const double target = prefix[ntiles] * (double)g / (double)G;
+        while (t + 1 < ntiles && prefix[t + 1] <= target) ++t;
+        int64_t within = (int64_t)((target - prefix[t]) / cost[t]);
+        within = std::min<int64_t>(std::max<int64_t>(within, 0), n_tt);
+        ranges[g] = std::max(ranges[g - 1], t * n_tt + within);
+    }
+    p->tc_grid = (int32_t)G;
+    RFD_TRY(ensure(p->d_ranges, (G + 1) * sizeof(int64_t)));
+    RFD_TRY_CUDA(cudaMemcpy(p->d_ranges.p, ranges.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    RFD_TRY(ensure(p->d_taps, (size_t)std::max<int64_t>(taps_off, 1024)));
+    RFD_TRY(ensure(p->d_tiles, ntiles * sizeof(TcTile)));
+    RFD_TRY_CUDA(cudaMemcpy(p->d_tiles.p, p->tc_tiles.data(), ntiles * sizeof(TcTile), cudaMemcpyHostToDevice));
+    return RFD_OK;
+}
 
 namespace {
 thread_local char g_err[1024] = {0};
@@ -262,13 +334,13 @@ rfd_status rfd_plan_create(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, in
     RFD_REQUIRE(window >= 1, RFD_ERR_ARG, "window must be >= 1");
     RFD_REQUIRE(std::isfinite(threshold) && threshold >= 0.f, RFD_ERR_ARG, "threshold must be finite, >= 0");
     RFD_REQUIRE(precision >= RFD_PREC_FP32 && precision <= RFD_PREC_BF16X3, RFD_ERR_ARG, "bad precision");
-    RFD_REQUIRE(precision == RFD_PREC_FP32, RFD_ERR_UNSUPPORTED,
-                "tensor-core precisions are not built into this library version");
     int32_t kmax = 0;
     for (int32_t j = 0; j < n_tmpl; ++j) {
         RFD_REQUIRE(ref_of_tmpl_host[j] >= 0 && ref_of_tmpl_host[j] < n_ref, RFD_ERR_ARG,
                     "ref_of_tmpl[%d] out of range", j);
         RFD_REQUIRE(k_host[j] >= 1 && k_host[j] <= 4096, RFD_ERR_SHAPE, "K[%d]=%d out of [1, 4096]", j, k_host[j]);
+        RFD_REQUIRE(precision == RFD_PREC_FP32 || k_host[j] <= 512, RFD_ERR_UNSUPPORTED,
+                    "K[%d]=%d: the tensor-core path supports K <= 512", j, k_host[j]);
         kmax = std::max(kmax, k_host[j]);
     }
     RFD_REQUIRE(halo >= kmax - 1 && halo < g.n, RFD_ERR_SHAPE, "halo=%d must be >= max K - 1 = %d and < n",
@@ -287,14 +359,41 @@ rfd_status rfd_plan_create(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, in
     p->k_max = kmax;
     p->ref_of.assign(ref_of_tmpl_host, ref_of_tmpl_host + n_tmpl);
     p->k_of.assign(k_host, k_host + n_tmpl);
-    p->tile_j = fir32_tile_templates();
-    // tiles: per reference, templates ordered by K (stable), cut into groups of tile_j
+    // tiles: per reference, templates ordered by K (stable)
     std::vector<int32_t> order(n_tmpl);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
         if (p->ref_of[a] != p->ref_of[b]) return p->ref_of[a] < p->ref_of[b];
         return p->k_of[a] < p->k_of[b];
     });
+    if (precision != RFD_PREC_FP32) {
+        rfd_status st = plan_tc_tiles(p, order, ctx->num_sms);
+        if (st == RFD_OK) {
+            do {
+                if ((st = ensure(p->d_perm, p->n_slots * sizeof(int32_t))) != RFD_OK) break;
+                if ((st = ensure(p->d_kslot, p->n_slots * sizeof(int32_t))) != RFD_OK) break;
+                if ((st = ensure(p->d_off, p->n_slots * sizeof(int32_t))) != RFD_OK) break;
+                if ((st = ensure(p->d_scale, p->n_slots * sizeof(float))) != RFD_OK) break;
+                std::vector<int32_t> kslot(p->n_slots);
+                for (int64_t s2 = 0; s2 < p->n_slots; ++s2) kslot[s2] = p->k_of[p->perm[s2]];
+                cudaError_t e1 = cudaMemcpy(p->d_perm.p, p->perm.data(), p->n_slots * sizeof(int32_t),
+                                            cudaMemcpyHostToDevice);
+                cudaError_t e2 = cudaMemcpy(p->d_kslot.p, kslot.data(), p->n_slots * sizeof(int32_t),
+                                            cudaMemcpyHostToDevice);
+                if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                    set_error("plan upload failed: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+                    st = RFD_ERR_CUDA;
+                }
+            } while (0);
+        }
+        if (st != RFD_OK) {
+            rfd_plan_destroy(p);
+            return st;
+        }
+        *out = p;
+        return RFD_OK;
+    }
+    p->tile_j = fir32_tile_templates();
     int32_t slot = 0;
     for (size_t i = 0; i < order.size();) {
         const int32_t r = p->ref_of[order[i]];
@@ -311,6 +410,7 @@ rfd_status rfd_plan_create(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, in
         }
         slot += t.count;
         p->tiles.push_back(t);
+        p->executed_flops += 8.0 * t.k_tile * (double)p->tile_j * (double)g.n;
         i = e;
     }
     p->n_slots = slot;
@@ -353,6 +453,7 @@ void rfd_plan_destroy(rfd_plan *plan) {
     release(plan->d_off);
     release(plan->d_scale);
     release(plan->d_kslot);
+    release(plan->d_ranges);
     delete plan;
 }
 
@@ -362,7 +463,10 @@ rfd_status rfd_plan_set_taps(rfd_plan *plan, const void *taps_dev, int32_t k_str
     RFD_REQUIRE(taps_dev && lag_dev && sigma_dev, RFD_ERR_ARG, "NULL argument");
     RFD_REQUIRE(k_stride >= plan->k_max, RFD_ERR_SHAPE, "k_stride=%d < max K=%d", k_stride, plan->k_max);
     RFD_TRY_CUDA(cudaSetDevice(plan->ctx->device));
-    RFD_TRY(pack_taps_fp32(plan, (const float2 *)taps_dev, k_stride, lag_dev, sigma_dev, (cudaStream_t)stream));
+    if (plan->precision == RFD_PREC_FP32)
+        RFD_TRY(pack_taps_fp32(plan, (const float2 *)taps_dev, k_stride, lag_dev, sigma_dev, (cudaStream_t)stream));
+    else
+        RFD_TRY(tc_pack(plan, (const float2 *)taps_dev, k_stride, lag_dev, sigma_dev, (cudaStream_t)stream));
     plan->taps_set = true;
     return RFD_OK;
 }
@@ -374,12 +478,16 @@ rfd_status rfd_ratio_filter_batch(rfd_plan *plan, const void *qref_dev, const in
     RFD_REQUIRE(plan->taps_set, RFD_ERR_ARG, "rfd_plan_set_taps has not been called");
     RFD_REQUIRE(qref_dev && cand_count_dev && (cand_dev || cand_capacity == 0), RFD_ERR_ARG, "NULL argument");
     RFD_REQUIRE(cand_capacity >= 0, RFD_ERR_SHAPE, "negative capacity");
-    (void)qscale_dev;
+    RFD_REQUIRE(plan->precision == RFD_PREC_FP32 || qscale_dev, RFD_ERR_ARG, "qscale_dev is NULL");
     RFD_TRY_CUDA(cudaSetDevice(plan->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     RFD_TRY_CUDA(cudaMemsetAsync(cand_count_dev, 0, sizeof(int64_t), s));
-    return fir32_launch(plan, (const float2 *)qref_dev, cand_dev, cand_capacity, cand_count_dev, s);
+    if (plan->precision == RFD_PREC_FP32)
+        return fir32_launch(plan, (const float2 *)qref_dev, cand_dev, cand_capacity, cand_count_dev, s);
+    return tc_launch(plan, qref_dev, qscale_dev, cand_dev, cand_capacity, cand_count_dev, s);
 }
+
+double rfd_plan_executed_flops(const rfd_plan *plan) { return plan ? plan->executed_flops : 0.0; }
 
 rfd_status rfd_find_triggers(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand_dev,
                              const int64_t *cand_count_dev, int64_t cand_capacity, rfd_trigger *trig_dev,

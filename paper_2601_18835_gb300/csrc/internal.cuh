@@ -127,6 +127,16 @@ struct RfdTile {
     int32_t k_tile;
 };
 
+// Tile of the tensor-core contraction (see rf_tc.cu): up to nt templates (64, or 32 when the
+// tile's K exceeds 256) of one reference; nk16 16-tap MMA steps, kpad = 16 nk16 taps, nch
+// 64-tap chunks; its pre-swizzled B-operand image is taps_bytes bytes at taps_off.
+struct TcTile {
+    int32_t ref, first, count, k_tile;
+    int32_t nt, nch, nk16, kpad;
+    int64_t taps_off;
+    int32_t taps_bytes, pad;
+};
+
 struct rfd_plan {
     rfd_ctx *ctx = nullptr;
     rfd::Grid grid{};
@@ -147,4 +157,10 @@ struct rfd_plan {
     rfd::DevBuf d_kslot;             // int32 [n_slots]: K_j
     int64_t n_slots = 0;
     bool taps_set = false;
+    // tensor-core path
+    std::vector<TcTile> tc_tiles;
+    rfd::DevBuf d_ranges;            // int64 [tc_grid + 1] item ranges per CTA
+    uint32_t tc_taps_cap = 0, tc_win = 0;
+    int32_t tc_grid = 0;
+    double executed_flops = 0.0;     // tensor (or FMA) flops one ratio_filter_batch executes
 };

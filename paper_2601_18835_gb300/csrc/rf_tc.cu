@@ -1,0 +1,452 @@
+// Tensor-core ratio filter (Eq. 3) with the fused trigger epilogue, sm_103a (tcgen05 + TMEM).
+//
+// For the templates of one tile (same reference, up to NT = 64 templates, or 32 when K > 256)
+// and one item of 128 output positions u0 .. u0+127:
+//   Y[a, u] = sum_k P[a, k] q[u + k],  P = reversed taps scaled by 2^e_a, q scaled by 2^e_r,
+// computed in the real block form with hi/lo splits of both operands (three products
+// hi*hi + hi*lo + lo*hi), FP32 accumulation in tensor memory:
+//   D[:, 0:2NT]   += Qr_h [Pr;Pi]_h^T + Qr_h [Pr;Pi]_l^T + Qr_l [Pr;Pi]_h^T   (N = 2 NT)
+//   D[:, 0:NT]    -= Qi_h Pi_h^T + Qi_h Pi_l^T + Qi_l Pi_h^T                  (N = NT, B negated)
+//   D[:, NT:2NT]  += Qi_h Pr_h^T + Qi_h Pr_l^T + Qi_l Pr_h^T                  (N = NT)
+// so D[u, a] = Re Y[a, u] and D[u, NT + a] = Im Y[a, u].
+//
+// A (the Hankel operand A[u, k] = q[u0 + u + k], M = 128 rows = TMEM lanes) is written into
+// tensor memory by four builder warps with tcgen05.st, 16 taps per stage, so the Toeplitz
+// expansion never goes through shared memory.  B (the tile's taps) stays in shared memory in
+// the K-major 128-byte swizzle layout, bulk-copied once per tile change from an image that
+// rfd_plan_set_taps pre-swizzles.  One CTA per SM walks a contiguous, cost-balanced range of
+// (tile, time block) items.  Roles: warp 0 bulk copies, warp 1 issues the MMAs (and owns the
+// TMEM allocation), warps 4-7 build A, warps 8-11 run the epilogue.  Every wait is bounded.
+#include "epilogue.cuh"
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace rfd {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kM = 128;           // output positions per item (MMA M, TMEM lanes)
+constexpr int kStages = 8;        // A stages in TMEM, 32 columns each
+constexpr int kThreads = 384;
+constexpr uint32_t kDCols = 128;  // TMEM columns per accumulator buffer
+constexpr uint32_t kACol = 256;   // first TMEM column of the A stages
+constexpr uint32_t kSpin = 1u << 22;
+
+enum {
+    kBarTapsFull = 0,
+    kBarTapsEmpty = 1,
+    kBarQFull = 2,     // 2
+    kBarQEmpty = 4,    // 2
+    kBarAFull = 6,     // kStages
+    kBarAEmpty = 14,   // kStages
+    kBarDFull = 22,    // 2
+    kBarDEmpty = 24,   // 2
+    kBarDone = 26,
+    kNumBars = 27
+};
+
+struct TcArgs {
+    const TcTile *tiles;
+    const int64_t *ranges;      // [gridDim.x + 1] item ranges
+    int64_t n_tt;               // time blocks per tile = n / 128
+    const uint8_t *taps;        // operand images
+    const uint16_t *q;          // q planes (fp16 or bf16 bits)
+    int64_t ld;
+    const int32_t *qscale;
+    const int32_t *perm;
+    const int32_t *off;
+    const float *scale;
+    int64_t n;
+    float thr;
+    uint32_t W;
+    rfd_candidate *cand;
+    int64_t cap;
+    unsigned long long *count;
+    uint32_t taps_cap;          // bytes of the taps region
+    uint32_t win;               // elements per q window plane
+};
+
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag,
+                                         unsigned long long *count) {
+    for (uint32_t i = 0; i < kSpin; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1u;
+    atomicOr(count, 1ull << 62);   // reported as RFD_ERR_TIMEOUT by find_triggers
+    return false;
+}
+
+template <int BF16>
+__global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *s_taps = sm;
+    uint16_t *s_q = (uint16_t *)(sm + A.taps_cap);
+    uint64_t *bars = (uint64_t *)(sm + A.taps_cap + 2u * 4u * A.win * 2u);
+    uint32_t *s_misc = (uint32_t *)(bars + kNumBars);
+    volatile uint32_t *abort_flag = &s_misc[1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t it0 = A.ranges[blockIdx.x], it1 = A.ranges[blockIdx.x + 1];
+    const uint32_t bar0 = smem_u32(bars);
+#define BAR(i) (bar0 + 8u * (uint32_t)(i))
+
+    if (threadIdx.x == 0) {
+        mbar_init(BAR(kBarTapsFull), 1);
+        mbar_init(BAR(kBarTapsEmpty), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(BAR(kBarQFull + b), 1);
+            mbar_init(BAR(kBarQEmpty + b), 4);
+            mbar_init(BAR(kBarDFull + b), 1);
+            mbar_init(BAR(kBarDEmpty + b), 4);
+        }
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(BAR(kBarAFull + s), 4);
+            mbar_init(BAR(kBarAEmpty + s), 1);
+        }
+        mbar_init(BAR(kBarDone), 1);
+        s_misc[1] = 0u;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(smem_u32(&s_misc[0]), 512);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_misc[0];
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer (bulk copies)
+        if (lane == 0) {
+            uint32_t tchg = 0, li = 0;
+            int64_t prev = -1;
+            for (int64_t it = it0; it < it1; ++it, ++li) {
+                const int64_t ti = it / A.n_tt, tt = it - ti * A.n_tt;
+                const TcTile T = A.tiles[ti];
+                if (ti != prev) {
+                    if (!wait_bar(BAR(kBarTapsEmpty), (tchg & 1u) ^ 1u, abort_flag, A.count)) break;
+                    mbar_arrive_expect_tx(BAR(kBarTapsFull), (uint32_t)T.taps_bytes);
+                    for (uint32_t o = 0; o < (uint32_t)T.taps_bytes; o += 32768u) {
+                        const uint32_t len = min(32768u, (uint32_t)T.taps_bytes - o);
+                        bulk_g2s(smem_u32(s_taps) + o, A.taps + T.taps_off + o, len, BAR(kBarTapsFull));
+                    }
+                    ++tchg;
+                    prev = ti;
+                }
+                const uint32_t qb = li & 1u, use = li >> 1;
+                if (!wait_bar(BAR(kBarQEmpty + qb), (use & 1u) ^ 1u, abort_flag, A.count)) break;
+                const uint32_t wbytes = (uint32_t)(kM + T.kpad) * 2u;
+                mbar_arrive_expect_tx(BAR(kBarQFull + qb), 4u * wbytes);
+                for (int p = 0; p < 4; ++p) {
+                    const uint16_t *src = A.q + (int64_t)(4 * T.ref + p) * A.ld + tt * kM;
+                    bulk_g2s(smem_u32(s_q + (qb * 4 + p) * A.win), src, wbytes, BAR(kBarQFull + qb));
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t tchg = 0, li = 0, ka = 0;
+            int64_t prev = -1;
+            const uint32_t taps_addr = smem_u32(s_taps);
+            for (int64_t it = it0; it < it1; ++it, ++li) {
+                const int64_t ti = it / A.n_tt;
+                const TcTile T = A.tiles[ti];
+                if (ti != prev) {
+                    if (!wait_bar(BAR(kBarTapsFull), tchg & 1u, abort_flag, A.count)) break;
+                    ++tchg;
+                    prev = ti;
+                }
+                const uint32_t buf = li & 1u, use = li >> 1;
+                if (!wait_bar(BAR(kBarDEmpty + buf), (use & 1u) ^ 1u, abort_flag, A.count)) break;
+                fence_after();
+                const uint32_t nt = (uint32_t)T.nt;
+                const uint32_t d = tmem + buf * kDCols;
+                const uint32_t id2 = idesc_f16(128, 2 * nt, BF16, 0);
+                const uint32_t id1 = idesc_f16(128, nt, BF16, 0);
+                const uint32_t id1n = idesc_f16(128, nt, BF16, 1);
+                const uint32_t chunk_bytes = 2u * nt * 128u;
+                bool ok = true;
+                for (int s = 0; s < T.nk16; ++s, ++ka) {
+                    const uint32_t st = ka % kStages, r = ka / kStages;
+                    if (!wait_bar(BAR(kBarAFull + st), r & 1u, abort_flag, A.count)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t c = (uint32_t)s >> 2, o = ((uint32_t)s & 3u) * 32u;
+                    const uint32_t bh = taps_addr + c * chunk_bytes + o;
+                    const uint32_t bl = taps_addr + ((uint32_t)T.nch + c) * chunk_bytes + o;
+                    const uint64_t Bh = desc_sw128(bh), Bl = desc_sw128(bl);
+                    const uint64_t Bhi = desc_sw128(bh + nt * 128u), Bli = desc_sw128(bl + nt * 128u);
+                    const uint32_t a_qr_h = tmem + kACol + st * 32u;
+                    const uint32_t a_qi_h = a_qr_h + 8u, a_qr_l = a_qr_h + 16u, a_qi_l = a_qr_h + 24u;
+                    mma_ts(d, a_qr_h, Bh, id2, s > 0 ? 1u : 0u);
+                    mma_ts(d, a_qr_h, Bl, id2, 1u);
+                    mma_ts(d, a_qr_l, Bh, id2, 1u);
+                    mma_ts(d, a_qi_h, Bhi, id1n, 1u);
+                    mma_ts(d, a_qi_h, Bli, id1n, 1u);
+                    mma_ts(d, a_qi_l, Bhi, id1n, 1u);
+                    mma_ts(d + nt, a_qi_h, Bh, id1, 1u);
+                    mma_ts(d + nt, a_qi_h, Bl, id1, 1u);
+                    mma_ts(d + nt, a_qi_l, Bh, id1, 1u);
+                    mma_commit(BAR(kBarAEmpty + st));
+                }
+                if (!ok) break;
+                mma_commit(BAR(kBarDFull + buf));
+                const bool last_of_tile = (it + 1 == it1) || ((it + 1) / A.n_tt != ti);
+                if (last_of_tile) mma_commit(BAR(kBarTapsEmpty));
+            }
+            // every MMA this thread issued has completed before TMEM is released
+            mma_commit(BAR(kBarDone));
+            for (uint32_t i = 0; i < kSpin && !mbar_try_wait(BAR(kBarDone), 0); ++i) {
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ------------------------------------------------------------ Hankel builders -> TMEM
+        const uint32_t lg = (uint32_t)warp - 4u;
+        const uint32_t row = lg * 32u + (uint32_t)lane;
+        const uint32_t tlane = (lg * 32u) << 16;
+        uint32_t li = 0, ka = 0;
+        for (int64_t it = it0; it < it1; ++it, ++li) {
+            const int64_t ti = it / A.n_tt;
+            const int nk16 = A.tiles[ti].nk16;
+            const uint32_t qb = li & 1u, use = li >> 1;
+            bool ok = wait_bar(BAR(kBarQFull + qb), use & 1u, abort_flag, A.count);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const uint32_t *W0 = (const uint32_t *)(s_q + (qb * 4 + 0) * A.win);
+            const uint32_t *W1 = (const uint32_t *)(s_q + (qb * 4 + 1) * A.win);
+            const uint32_t *W2 = (const uint32_t *)(s_q + (qb * 4 + 2) * A.win);
+            const uint32_t *W3 = (const uint32_t *)(s_q + (qb * 4 + 3) * A.win);
+            for (int s = 0; s < nk16; ++s, ++ka) {
+                const uint32_t st = ka % kStages, r = ka / kStages;
+                ok = wait_bar(BAR(kBarAEmpty + st), (r & 1u) ^ 1u, abort_flag, A.count);
+                if (!__all_sync(0xffffffffu, ok)) break;
+                const uint32_t e0 = row + (uint32_t)s * 16u, w0 = e0 >> 1, sh = (e0 & 1u) * 16u;
+                uint32_t v[32];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const uint32_t *Wp = p == 0 ? W0 : (p == 1 ? W1 : (p == 2 ? W2 : W3));
+                    uint32_t prev = Wp[w0];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const uint32_t nx = Wp[w0 + i + 1];
+                        v[p * 8 + i] = __funnelshift_r(prev, nx, sh);
+                        prev = nx;
+                    }
+                }
+                tmem_st32(tmem + tlane + kACol + st * 32u, v);
+                tmem_st_wait();
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(BAR(kBarAFull + st));
+            }
+            if (!__all_sync(0xffffffffu, ok)) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(BAR(kBarQEmpty + qb));
+        }
+    } else if (warp >= 8) {
+        // ------------------------------------------------------------ epilogue
+        const uint32_t lg = (uint32_t)warp - 8u;
+        const uint32_t row = lg * 32u + (uint32_t)lane;
+        const uint32_t tlane = (lg * 32u) << 16;
+        uint32_t li = 0;
+        for (int64_t it = it0; it < it1; ++it, ++li) {
+            const int64_t ti = it / A.n_tt, tt = it - ti * A.n_tt;
+            const TcTile T = A.tiles[ti];
+            const uint32_t buf = li & 1u, use = li >> 1;
+            const bool ok = wait_bar(BAR(kBarDFull + buf), use & 1u, abort_flag, A.count);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            fence_after();
+            const float esc = ldexpf(1.0f, -A.qscale[T.ref]);
+            const int64_t u = tt * kM + row;
+            for (int a0 = 0; a0 < T.nt; a0 += 32) {
+                uint32_t re[32], im[32];
+                tmem_ld32(tmem + tlane + buf * kDCols + (uint32_t)a0, re);
+                tmem_ld32(tmem + tlane + buf * kDCols + (uint32_t)(T.nt + a0), im);
+                tmem_ld_wait();
+                if (a0 + 32 >= T.nt) {
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(BAR(kBarDEmpty + buf));
+                }
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int a = a0 + i;
+                    const bool valid = a < T.count;
+                    int32_t j = 0, o = 0;
+                    float sc = 0.f;
+                    if (valid) {
+                        const int64_t slot = (int64_t)T.first + a;
+                        j = A.perm[slot];
+                        o = A.off[slot];
+                        sc = A.scale[slot] * esc;
+                    }
+                    const uint32_t t = (uint32_t)((u + o) & (A.n - 1));
+                    emit_window_max(valid, (uint32_t)j, t, __uint_as_float(re[i]) * sc,
+                                    __uint_as_float(im[i]) * sc, A.thr, A.W, A.cand, A.cap, A.count);
+                }
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc(tmem, 512);
+    }
+#undef BAR
+}
+
+// ------------------------------------------------------------------ taps packing
+template <typename H>
+__device__ __forceinline__ uint16_t h_bits(H x);
+template <>
+__device__ __forceinline__ uint16_t h_bits<__half>(__half x) { return __half_as_ushort(x); }
+template <>
+__device__ __forceinline__ uint16_t h_bits<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat16_as_ushort(x); }
+template <typename H>
+__device__ __forceinline__ H to_h(float x);
+template <>
+__device__ __forceinline__ __half to_h<__half>(float x) { return __float2half_rn(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_h<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ float from_h(__half x) { return __half2float(x); }
+__device__ __forceinline__ float from_h(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// One block per tile: per-template power-of-two scale (max |component| * 2^e < 2^8), then the
+// B-operand image: [hl][chunk][row][128 B], row < NT -> Re of template row, else Im of
+// template row - NT; element e of a chunk holds reversed tap k = 64 chunk + e, 16-byte units
+// XOR-swizzled by row % 8.  Also the per-slot lag offset and normalisation.
+template <typename H>
+__global__ void __launch_bounds__(256) k_pack_tc(const TcTile *__restrict__ tiles, const float2 *__restrict__ taps,
+                                                 int32_t k_stride, const int32_t *__restrict__ perm,
+                                                 const int32_t *__restrict__ kslot, const int32_t *__restrict__ lag,
+                                                 const double *__restrict__ sigma, int64_t n,
+                                                 uint8_t *__restrict__ out, int32_t *__restrict__ off,
+                                                 float *__restrict__ scale) {
+    __shared__ int s_exp[64];
+    __shared__ int s_j[64], s_k[64];
+    const TcTile T = tiles[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int a = warp; a < T.nt; a += (int)(blockDim.x >> 5)) {
+        float mx = 0.f;
+        int j = 0, K = 0;
+        if (a < T.count) {
+            j = perm[T.first + a];
+            K = kslot[T.first + a];
+            for (int k = lane; k < K; k += 32) {
+                const float2 v = taps[(int64_t)j * k_stride + k];
+                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) {
+            int e = 0;
+            if (mx > 0.f) {
+                int ex;
+                frexpf(mx, &ex);      // mx < 2^ex
+                e = 8 - ex;
+            }
+            s_exp[a] = e;
+            s_j[a] = j;
+            s_k[a] = K;
+        }
+    }
+    __syncthreads();
+    const int rows = 2 * T.nt;
+    const int64_t total = (int64_t)2 * T.nch * rows * 64;
+    uint8_t *img = out + T.taps_off;
+    for (int64_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int e = (int)(idx & 63);
+        const int64_t r1 = idx >> 6;
+        const int row = (int)(r1 % rows);
+        const int64_t r2 = r1 / rows;
+        const int c = (int)(r2 % T.nch);
+        const int hl = (int)(r2 / T.nch);
+        const int a = row % T.nt, part = row / T.nt;
+        const int k = 64 * c + e;
+        uint16_t bits = 0;
+        if (a < T.count && k < s_k[a]) {
+            const float2 v = taps[(int64_t)s_j[a] * k_stride + (s_k[a] - 1 - k)];
+            const float x = ldexpf(part ? v.y : v.x, s_exp[a]);
+            const H hi = to_h<H>(x);
+            bits = hl ? h_bits<H>(to_h<H>(x - from_h(hi))) : h_bits<H>(hi);
+        }
+        const int64_t rowbase = ((int64_t)(hl * T.nch + c) * rows + row) * 128;
+        *(uint16_t *)(img + rowbase + ((((e >> 3) ^ (row & 7)) << 4)) + (e & 7) * 2) = bits;
+    }
+    for (int a = threadIdx.x; a < T.count; a += blockDim.x) {
+        const int64_t slot = (int64_t)T.first + a;
+        const int j = s_j[a], K = s_k[a];
+        off[slot] = (int32_t)((((int64_t)lag[j] + K - 1) % n + n) % n);
+        const double sg = sigma[j];
+        scale[slot] = sg > 0.0 ? (float)(ldexp(1.0, -s_exp[a]) / sg) : 0.f;
+    }
+}
+
+}  // namespace
+
+size_t tc_smem_bytes(uint32_t taps_cap, uint32_t win) {
+    return 1024 + (size_t)taps_cap + 2u * 4u * win * 2u + kNumBars * 8 + 16;
+}
+
+rfd_status tc_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const int32_t *lag,
+                   const double *sigma, cudaStream_t s) {
+    const unsigned ntiles = (unsigned)plan->tc_tiles.size();
+    if (ntiles == 0) return RFD_OK;
+    if (plan->precision == RFD_PREC_FP16X3)
+        k_pack_tc<__half><<<ntiles, 256, 0, s>>>((const TcTile *)plan->d_tiles.p, taps, k_stride,
+                                                  (const int32_t *)plan->d_perm.p, (const int32_t *)plan->d_kslot.p,
+                                                  lag, sigma, plan->grid.n, (uint8_t *)plan->d_taps.p,
+                                                  (int32_t *)plan->d_off.p, (float *)plan->d_scale.p);
+    else
+        k_pack_tc<__nv_bfloat16><<<ntiles, 256, 0, s>>>(
+            (const TcTile *)plan->d_tiles.p, taps, k_stride, (const int32_t *)plan->d_perm.p,
+            (const int32_t *)plan->d_kslot.p, lag, sigma, plan->grid.n, (uint8_t *)plan->d_taps.p,
+            (int32_t *)plan->d_off.p, (float *)plan->d_scale.p);
+    RFD_LAUNCH_CHECK();
+    return RFD_OK;
+}
+
+rfd_status tc_launch(const rfd_plan *plan, const void *q, const int32_t *qscale, rfd_candidate *cand, int64_t cap,
+                     int64_t *count, cudaStream_t s) {
+    TcArgs a;
+    a.tiles = (const TcTile *)plan->d_tiles.p;
+    a.ranges = (const int64_t *)plan->d_ranges.p;
+    a.n_tt = plan->grid.n / kM;
+    a.taps = (const uint8_t *)plan->d_taps.p;
+    a.q = (const uint16_t *)q;
+    a.ld = plan->ld;
+    a.qscale = qscale;
+    a.perm = (const int32_t *)plan->d_perm.p;
+    a.off = (const int32_t *)plan->d_off.p;
+    a.scale = (const float *)plan->d_scale.p;
+    a.n = plan->grid.n;
+    a.thr = plan->threshold;
+    a.W = (uint32_t)plan->window;
+    a.cand = cand;
+    a.cap = cap;
+    a.count = (unsigned long long *)count;
+    a.taps_cap = plan->tc_taps_cap;
+    a.win = plan->tc_win;
+    // at least 120 KB so that exactly one CTA (and one 512-column TMEM allocation) fits per SM
+    const size_t shm = std::max<size_t>(tc_smem_bytes(a.taps_cap, a.win), 120 * 1024);
+    const unsigned grid = (unsigned)plan->tc_grid;
+    if (plan->precision == RFD_PREC_FP16X3) {
+        RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        k_rf_tc<0><<<grid, kThreads, shm, s>>>(a);
+    } else {
+        RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        k_rf_tc<1><<<grid, kThreads, shm, s>>>(a);
+    }
+    RFD_LAUNCH_CHECK();
+    return RFD_OK;
+}
+
+int tc_rows_per_item() { return kM; }
+
+}  // namespace rfd

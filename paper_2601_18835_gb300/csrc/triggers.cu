@@ -11,10 +11,14 @@ namespace rfd {
 
 namespace {
 
+// A filtering kernel whose bounded wait gave up sets bit 62 of the candidate count.
+constexpr int64_t kTimeoutBit = (int64_t)1 << 62;
+constexpr int64_t kCountMask = kTimeoutBit - 1;
+
 __global__ void k_count(const rfd_candidate *__restrict__ c, const int64_t *__restrict__ count,
                         int64_t cap, int32_t n_tmpl, int32_t *__restrict__ cnt,
                         int32_t *__restrict__ bad) {
-    const int64_t nc = min(*count, cap);
+    const int64_t nc = min(*count & kCountMask, cap);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t j = c[i].j;
@@ -50,7 +54,7 @@ __global__ void k_scan(const int32_t *__restrict__ in, int32_t n, int64_t *__res
 __global__ void k_scatter(const rfd_candidate *__restrict__ c, const int64_t *__restrict__ count,
                           int64_t cap, int32_t n_tmpl, const int64_t *__restrict__ off,
                           int32_t *__restrict__ cur, rfd_candidate *__restrict__ bucket) {
-    const int64_t nc = min(*count, cap);
+    const int64_t nc = min(*count & kCountMask, cap);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc;
          i += (int64_t)gridDim.x * blockDim.x) {
         const rfd_candidate v = c[i];
@@ -144,6 +148,8 @@ rfd_status find_triggers_impl(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate 
     RFD_TRY_CUDA(cudaMemcpyAsync(&host[1], toff + J, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     RFD_TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RFD_TRY_CUDA(cudaStreamSynchronize(s));
+    RFD_REQUIRE((host[0] & kTimeoutBit) == 0, RFD_ERR_TIMEOUT,
+                "find_triggers: the filtering kernel gave up waiting on the device (timeout)");
     RFD_REQUIRE(hbad == 0, RFD_ERR_ARG, "find_triggers: %d candidates name a template >= n_tmpl=%d",
                 hbad, n_tmpl);
     if (host[0] > cap) {
@@ -244,6 +250,8 @@ extern "C" rfd_status rfd_find_triggers_noalloc(int32_t n_tmpl, const rfd_candid
     RFD_TRY_CUDA(cudaMemcpyAsync(&host[1], toff + J, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     RFD_TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RFD_TRY_CUDA(cudaStreamSynchronize(s));
+    RFD_REQUIRE((host[0] & kTimeoutBit) == 0, RFD_ERR_TIMEOUT,
+                "find_triggers_noalloc: the filtering kernel gave up waiting on the device (timeout)");
     RFD_REQUIRE(hbad == 0, RFD_ERR_ARG, "find_triggers_noalloc: %d candidates name a template >= n_tmpl=%d", hbad,
                 n_tmpl);
     if (host[0] > cand_capacity) {

@@ -264,3 +264,107 @@ def test_c2_full_size_fp32_sampled(ctx):
             zo = ora.snr_at(j, o, g["t"].astype(np.int64))
             assert np.max(np.abs(np.sqrt(g["snr2"]) - np.abs(zo)) / np.abs(zo)) < TOL_FP32
     assert compare_triggers(trig, sets, TOL_FP32, sample, cfg.window) <= 2
+
+
+# --------------------------------------------------------------------------- tensor-core path
+TOL_TC = 1e-3
+TC_PRECISIONS = [("fp16x3", 1), ("bf16x3", 2)]
+
+
+def snr_errors(trig, sets, js):
+    """Largest relative |z| error over the GPU triggers that the oracle also has (same t)."""
+    worst = 0.0
+    for j in js:
+        o_by_t = {x["t"]: x for x in sets[j][0]}
+        for r in trig[trig["j"] == j]:
+            x = o_by_t.get(int(r["t"]))
+            if x is not None:
+                worst = max(worst, abs(math.sqrt(float(r["snr2"])) / abs(x["z"]) - 1.0))
+    return worst
+
+
+@pytest.mark.parametrize("name,prec", TC_PRECISIONS)
+def test_c1_triggers_tensor_core(c1, name, prec):
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    q, e, _ = gpu.filter_reference(halo, prec)
+    trig, ncand = gpu.ratio_filter(t, q, e, prec, halo)
+    sets = {}
+    for j in range(bank.n_tmpl):
+        o = ora.design(j, cfg.k, with_match=False)
+        sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
+    n_amb = compare_triggers(trig, sets, TOL_TC, range(bank.n_tmpl), cfg.window)
+    assert n_amb <= 4
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < (2e-5 if prec == 1 else 2e-4)
+
+
+@pytest.mark.parametrize("name,prec", TC_PRECISIONS)
+def test_ragged_bank_tensor_core(ctx, name, prec):
+    """37 templates, K from 2 to 96 (tiles padded to 16-tap steps), window 37, low threshold."""
+    cfg = workload.small_config(1, n_tmpl=37, window=37, threshold=6.0)
+    bank, data = workload.make_workload(cfg)
+    rng = np.random.default_rng(7)
+    K = (2 * rng.integers(1, 49, size=bank.n_tmpl)).astype(np.int32)
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(K, k_stride=128, match=False)
+    halo = int(((K.max() + 15) // 16) * 16) - 1
+    q, e, _ = gpu.filter_reference(halo, prec)
+    trig, ncand = gpu.ratio_filter(t, q, e, prec, halo, cand_cap=1 << 22)
+    sets = {}
+    for j in range(bank.n_tmpl):
+        o = ora.design(j, int(K[j]), with_match=False)
+        sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
+    n_or = sum(len(s[0]) for s in sets.values())
+    assert n_or > 1000
+    # at threshold 6 many windows sit within the 4 tol band; every other window must agree
+    assert compare_triggers(trig, sets, TOL_TC, range(bank.n_tmpl), cfg.window) <= 0.05 * n_or
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < (2e-5 if prec == 1 else 2e-4)
+
+
+@pytest.mark.parametrize("name,prec", TC_PRECISIONS[:1])
+def test_long_taps_tensor_core(ctx, name, prec):
+    """K = 320 and 512 (tiles of 32 templates, 20 and 32 MMA steps) next to K = 64 (64 per tile)."""
+    cfg = workload.small_config(1, n_tmpl=80, threshold=9.0)
+    bank, data = workload.make_workload(cfg)
+    K = np.where(np.arange(bank.n_tmpl) % 3 == 0, 320, np.where(np.arange(bank.n_tmpl) % 3 == 1, 512, 64))
+    K = K.astype(np.int32)
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(K, k_stride=512, match=False)
+    halo = 511
+    q, e, _ = gpu.filter_reference(halo, prec)
+    trig, ncand = gpu.ratio_filter(t, q, e, prec, halo, cand_cap=1 << 22)
+    js = list(range(0, bank.n_tmpl, 5))
+    sets = {}
+    for j in js:
+        o = ora.design(j, int(K[j]), with_match=False)
+        sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
+    n_or = sum(len(sets[j][0]) for j in js)
+    assert n_or > 100
+    assert compare_triggers(trig, sets, TOL_TC, js, cfg.window) <= 0.05 * n_or
+    assert snr_errors(trig, sets, js) < 2e-5
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,prec", TC_PRECISIONS)
+def test_c2_full_size_tensor_core_sampled(ctx, name, prec):
+    """The 4096-template, 2^19-sample bank on the tensor-core path; oracle on a stratified sample;
+    every GPU trigger of a sampled template is re-evaluated by the oracle at its sample."""
+    cfg = workload.get_config(2)
+    bank, data = workload.make_workload(cfg)
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    q, e, _ = gpu.filter_reference(halo, prec)
+    trig, ncand = gpu.ratio_filter(t, q, e, prec, halo)
+    sample = sorted({s for (_, _, _, s) in data.injections}
+                    | {int(np.nonzero(bank.ref_of_tmpl == r)[0][-1]) for r in range(0, bank.n_ref, 3)})
+    sets = {}
+    for j in sample:
+        o = ora.design(j, cfg.k, with_match=False)
+        sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
+        g = trig[trig["j"] == j]
+        if len(g):
+            zo = ora.snr_at(j, o, g["t"].astype(np.int64))
+            assert np.max(np.abs(np.sqrt(g["snr2"]) - np.abs(zo)) / np.abs(zo)) < TOL_TC
+    assert compare_triggers(trig, sets, TOL_TC, sample, cfg.window) <= 4
