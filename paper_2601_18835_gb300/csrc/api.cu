@@ -34,7 +34,11 @@ rfd_status tc_launch(const rfd_plan *, const void *, const int32_t *, rfd_candid
 int tc_rows_per_item();
 
 // Tensor-core tiles: per reference, templates in increasing K, cut so that a tile holds at
-// most 64 templates (32 once its K exceeds 256); item ranges per CTA balance the MMA work.
+// most 128 templates (64 once its K exceeds 128, 32 once it exceeds 256: the taps image,
+// 3 NT rows x K taps x hi/lo, stays within 192 KB of shared memory); NT is the tile's count
+// rounded up to 16.  Item ranges per CTA balance the MMA work.
+static int32_t tc_nt_cap(int32_t kpad) { return kpad <= 128 ? 128 : (kpad <= 256 ? 64 : 32); }
+
 static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &order, int num_sms) {
     const int64_t n_tt = p->grid.n / tc_rows_per_item();
     int64_t taps_off = 0;
@@ -48,24 +52,23 @@ static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &order, 
         t.first = (int32_t)p->perm.size();
         while (i < order.size() && p->ref_of[order[i]] == r) {
             const int32_t kt = std::max(t.k_tile, p->k_of[order[i]]);
-            const int32_t ntc = kt <= 256 ? 64 : 32;
-            if (t.count + 1 > ntc) break;
+            if (t.count + 1 > tc_nt_cap(16 * ((kt + 15) / 16))) break;
             t.k_tile = kt;
             ++t.count;
             p->perm.push_back(order[i]);
             ++i;
         }
-        t.nt = t.k_tile <= 256 ? 64 : 32;
         t.nk16 = (t.k_tile + 15) / 16;
         t.kpad = 16 * t.nk16;
+        t.nt = 16 * ((t.count + 15) / 16);
         t.nch = (t.kpad + 63) / 64;
-        t.taps_bytes = 2 * t.nch * 2 * t.nt * 128;
+        t.taps_bytes = 2 * t.nch * 3 * t.nt * 128;
         t.taps_off = taps_off;
         taps_off += t.taps_bytes;
         kpad_max = std::max(kpad_max, t.kpad);
         cap = std::max(cap, (uint32_t)t.taps_bytes);
         p->tc_tiles.push_back(t);
-        p->executed_flops += (double)n_tt * t.nk16 * 2.0 * 128.0 * 16.0 * 12.0 * t.nt;
+        p->executed_flops += (double)n_tt * t.nk16 * 6.0 * 2.0 * 128.0 * (2.0 * t.nt) * 16.0;
     }
     p->n_slots = (int64_t)p->perm.size();
     p->tc_taps_cap = (cap + 1023u) / 1024u * 1024u;
@@ -78,7 +81,7 @@ static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &order, 
     const int64_t total_items = ntiles * n_tt;
     std::vector<double> cost(ntiles), prefix(ntiles + 1, 0.0);
     for (int64_t t = 0; t < ntiles; ++t) {
-        cost[t] = (double)p->tc_tiles[t].nk16 * p->tc_tiles[t].nt + 16.0;
+        cost[t] = (double)p->tc_tiles[t].nk16 * 6.0 + 2.0;   // MMAs cost the same for any N <= 256
         prefix[t + 1] = prefix[t] + cost[t] * n_tt;
     }
     const int64_t G = std::max<int64_t>(1, std::min<int64_t>(num_sms, total_items));

@@ -1,22 +1,26 @@
 // Tensor-core ratio filter (Eq. 3) with the fused trigger epilogue, sm_103a (tcgen05 + TMEM).
 //
-// For the templates of one tile (same reference, up to NT = 64 templates, or 32 when K > 256)
-// and one item of 128 output positions u0 .. u0+127:
+// For the templates of one tile (same reference, NT of them: 128 when K <= 128, 64 when
+// K <= 256, 32 when K <= 512) and one item of 128 output positions u0 .. u0+127:
 //   Y[a, u] = sum_k P[a, k] q[u + k],  P = reversed taps scaled by 2^e_a, q scaled by 2^e_r,
-// computed in the real block form with hi/lo splits of both operands (three products
-// hi*hi + hi*lo + lo*hi), FP32 accumulation in tensor memory:
-//   D[:, 0:2NT]   += Qr_h [Pr;Pi]_h^T + Qr_h [Pr;Pi]_l^T + Qr_l [Pr;Pi]_h^T   (N = 2 NT)
-//   D[:, 0:NT]    -= Qi_h Pi_h^T + Qi_h Pi_l^T + Qi_l Pi_h^T                  (N = NT, B negated)
-//   D[:, NT:2NT]  += Qi_h Pr_h^T + Qi_h Pr_l^T + Qi_l Pr_h^T                  (N = NT)
-// so D[u, a] = Re Y[a, u] and D[u, NT + a] = Im Y[a, u].
+// with hi/lo splits of both operands (three products hi*hi + hi*lo + lo*hi) and FP32
+// accumulation in tensor memory.  The complex product uses the real block form arranged so
+// that every MMA is one instruction of N = 2 NT (a tcgen05.mma costs about the same for any
+// N <= 256, so wide N is what keeps the tensor pipe full):
+//   D = [Re Y | -Im Y] (N = 2 NT columns),
+//   D += Qr_h [Pr;-Pi]_h^T + Qr_h [Pr;-Pi]_l^T + Qr_l [Pr;-Pi]_h^T
+//      + (-Qi)_h [Pi;Pr]_h^T + (-Qi)_h [Pi;Pr]_l^T + (-Qi)_l [Pi;Pr]_h^T.
+// The taps image holds the rows [Pi; Pr; -Pi] once, so [Pi;Pr] and [Pr;-Pi] are its rows
+// 0..2NT-1 and NT..3NT-1 (two descriptors into one image).
 //
-// A (the Hankel operand A[u, k] = q[u0 + u + k], M = 128 rows = TMEM lanes) is written into
-// tensor memory by four builder warps with tcgen05.st, 16 taps per stage, so the Toeplitz
-// expansion never goes through shared memory.  B (the tile's taps) stays in shared memory in
-// the K-major 128-byte swizzle layout, bulk-copied once per tile change from an image that
-// rfd_plan_set_taps pre-swizzles.  One CTA per SM walks a contiguous, cost-balanced range of
-// (tile, time block) items.  Roles: warp 0 bulk copies, warp 1 issues the MMAs (and owns the
-// TMEM allocation), warps 4-7 build A, warps 8-11 run the epilogue.  Every wait is bounded.
+// A (the Hankel operand A[u, k] = q[u0 + u + k], M = 128 rows = TMEM lanes, planes Qr_h,
+// -Qi_h, Qr_l, -Qi_l) is written into tensor memory by four builder warps with tcgen05.st,
+// 16 taps per stage (8 stages), so the Toeplitz expansion never goes through shared memory.
+// B (the tile's taps) stays in shared memory in the K-major 128-byte swizzle layout,
+// bulk-copied once per tile change from the image rfd_plan_set_taps pre-swizzles.  One CTA
+// per SM walks a contiguous, cost-balanced range of (tile, time block) items.  Roles: warp 0
+// bulk copies, warp 1 issues the MMAs (and owns the TMEM allocation), warps 4-7 build A,
+// warps 8-15 drain the accumulator and run the epilogue.  Every wait is bounded.
 #include "epilogue.cuh"
 #include "internal.cuh"
 #include "tc_ptx.cuh"
@@ -29,9 +33,9 @@ using namespace tc;
 
 constexpr int kM = 128;           // output positions per item (MMA M, TMEM lanes)
 constexpr int kStages = 8;        // A stages in TMEM, 32 columns each
-constexpr int kThreads = 384;
-constexpr uint32_t kDCols = 128;  // TMEM columns per accumulator buffer
-constexpr uint32_t kACol = 256;   // first TMEM column of the A stages
+constexpr int kThreads = 512;
+constexpr int kEpiWarps = 8;      // two per TMEM lane group, each half of the templates
+constexpr uint32_t kACol = 256;   // first TMEM column of the A stages (D uses 0 .. 2 NT - 1)
 constexpr uint32_t kSpin = 1u << 22;
 
 enum {
@@ -41,10 +45,10 @@ enum {
     kBarQEmpty = 4,    // 2
     kBarAFull = 6,     // kStages
     kBarAEmpty = 14,   // kStages
-    kBarDFull = 22,    // 2
-    kBarDEmpty = 24,   // 2
-    kBarDone = 26,
-    kNumBars = 27
+    kBarDFull = 22,
+    kBarDEmpty = 23,
+    kBarDone = 24,
+    kNumBars = 25
 };
 
 struct TcArgs {
@@ -99,9 +103,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(BAR(kBarQFull + b), 1);
             mbar_init(BAR(kBarQEmpty + b), 4);
-            mbar_init(BAR(kBarDFull + b), 1);
-            mbar_init(BAR(kBarDEmpty + b), 4);
         }
+        mbar_init(BAR(kBarDFull), 1);
+        mbar_init(BAR(kBarDEmpty), kEpiWarps);
         for (int s = 0; s < kStages; ++s) {
             mbar_init(BAR(kBarAFull + s), 4);
             mbar_init(BAR(kBarAEmpty + s), 1);
@@ -158,15 +162,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
                     ++tchg;
                     prev = ti;
                 }
-                const uint32_t buf = li & 1u, use = li >> 1;
-                if (!wait_bar(BAR(kBarDEmpty + buf), (use & 1u) ^ 1u, abort_flag, A.count)) break;
+                if (!wait_bar(BAR(kBarDEmpty), (li & 1u) ^ 1u, abort_flag, A.count)) break;
                 fence_after();
                 const uint32_t nt = (uint32_t)T.nt;
-                const uint32_t d = tmem + buf * kDCols;
-                const uint32_t id2 = idesc_f16(128, 2 * nt, BF16, 0);
-                const uint32_t id1 = idesc_f16(128, nt, BF16, 0);
-                const uint32_t id1n = idesc_f16(128, nt, BF16, 1);
-                const uint32_t chunk_bytes = 2u * nt * 128u;
+                const uint32_t d = tmem;
+                const uint32_t idn = idesc_f16(128, 2 * nt, BF16, 0);
+                const uint32_t chunk_bytes = 3u * nt * 128u;
                 bool ok = true;
                 for (int s = 0; s < T.nk16; ++s, ++ka) {
                     const uint32_t st = ka % kStages, r = ka / kStages;
@@ -178,23 +179,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
                     const uint32_t c = (uint32_t)s >> 2, o = ((uint32_t)s & 3u) * 32u;
                     const uint32_t bh = taps_addr + c * chunk_bytes + o;
                     const uint32_t bl = taps_addr + ((uint32_t)T.nch + c) * chunk_bytes + o;
-                    const uint64_t Bh = desc_sw128(bh), Bl = desc_sw128(bl);
-                    const uint64_t Bhi = desc_sw128(bh + nt * 128u), Bli = desc_sw128(bl + nt * 128u);
+                    const uint64_t B2h = desc_sw128(bh), B2l = desc_sw128(bl);                    // [Pi; Pr]
+                    const uint64_t B1h = desc_sw128(bh + nt * 128u), B1l = desc_sw128(bl + nt * 128u);  // [Pr; -Pi]
                     const uint32_t a_qr_h = tmem + kACol + st * 32u;
                     const uint32_t a_qi_h = a_qr_h + 8u, a_qr_l = a_qr_h + 16u, a_qi_l = a_qr_h + 24u;
-                    mma_ts(d, a_qr_h, Bh, id2, s > 0 ? 1u : 0u);
-                    mma_ts(d, a_qr_h, Bl, id2, 1u);
-                    mma_ts(d, a_qr_l, Bh, id2, 1u);
-                    mma_ts(d, a_qi_h, Bhi, id1n, 1u);
-                    mma_ts(d, a_qi_h, Bli, id1n, 1u);
-                    mma_ts(d, a_qi_l, Bhi, id1n, 1u);
-                    mma_ts(d + nt, a_qi_h, Bh, id1, 1u);
-                    mma_ts(d + nt, a_qi_h, Bl, id1, 1u);
-                    mma_ts(d + nt, a_qi_l, Bh, id1, 1u);
+                    mma_ts(d, a_qr_h, B1h, idn, s > 0 ? 1u : 0u);
+                    mma_ts(d, a_qr_h, B1l, idn, 1u);
+                    mma_ts(d, a_qr_l, B1h, idn, 1u);
+                    mma_ts(d, a_qi_h, B2h, idn, 1u);
+                    mma_ts(d, a_qi_h, B2l, idn, 1u);
+                    mma_ts(d, a_qi_l, B2h, idn, 1u);
                     mma_commit(BAR(kBarAEmpty + st));
                 }
                 if (!ok) break;
-                mma_commit(BAR(kBarDFull + buf));
+                mma_commit(BAR(kBarDFull));
                 const bool last_of_tile = (it + 1 == it1) || ((it + 1) / A.n_tt != ti);
                 if (last_of_tile) mma_commit(BAR(kBarTapsEmpty));
             }
@@ -205,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
         }
     } else if (warp >= 4 && warp < 8) {
         // ------------------------------------------------------------ Hankel builders -> TMEM
-        const uint32_t lg = (uint32_t)warp - 4u;
+        const uint32_t lg = (uint32_t)warp & 3u;
         const uint32_t row = lg * 32u + (uint32_t)lane;
         const uint32_t tlane = (lg * 32u) << 16;
         uint32_t li = 0, ka = 0;
@@ -232,7 +230,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const uint32_t nx = Wp[w0 + i + 1];
-                        v[p * 8 + i] = __funnelshift_r(prev, nx, sh);
+                        // the Qi planes (1, 3) go in negated: flip both halves' sign bits
+                        v[p * 8 + i] = __funnelshift_r(prev, nx, sh) ^ ((p & 1) ? 0x80008000u : 0u);
                         prev = nx;
                     }
                 }
@@ -246,48 +245,81 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
             __syncwarp();
             if (lane == 0) mbar_arrive(BAR(kBarQEmpty + qb));
         }
-    } else if (warp >= 8) {
+    } else if (warp >= 8 && warp < 8 + kEpiWarps) {
         // ------------------------------------------------------------ epilogue
-        const uint32_t lg = (uint32_t)warp - 8u;
+        const uint32_t lg = (uint32_t)warp & 3u;
+        const int half = (warp - 8) >> 2;                 // which half of the tile's templates
         const uint32_t row = lg * 32u + (uint32_t)lane;
         const uint32_t tlane = (lg * 32u) << 16;
         uint32_t li = 0;
         for (int64_t it = it0; it < it1; ++it, ++li) {
             const int64_t ti = it / A.n_tt, tt = it - ti * A.n_tt;
             const TcTile T = A.tiles[ti];
-            const uint32_t buf = li & 1u, use = li >> 1;
-            const bool ok = wait_bar(BAR(kBarDFull + buf), use & 1u, abort_flag, A.count);
+            const bool ok = wait_bar(BAR(kBarDFull), li & 1u, abort_flag, A.count);
             if (!__all_sync(0xffffffffu, ok)) break;
             fence_after();
             const float esc = ldexpf(1.0f, -A.qscale[T.ref]);
             const int64_t u = tt * kM + row;
-            for (int a0 = 0; a0 < T.nt; a0 += 32) {
+            const int per = T.nt >> 1;                    // templates per half (multiple of 8)
+            const int a_begin = half * per, a_end = a_begin + per;
+            if (per < 32 && half == 1) {
+                // nothing to drain for this warp when the tile is narrow
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(BAR(kBarDEmpty));
+                continue;
+            }
+            const int step = per < 32 ? 2 * per : 32;     // narrow tiles: one warp takes all
+            const int lo = per < 32 ? 0 : a_begin, hi = per < 32 ? T.nt : a_end;
+            for (int a0 = lo; a0 < hi; a0 += 32) {
+                const int my_a = a0 + lane;
+                const bool my_valid = my_a < T.count && my_a < hi;
+                const int64_t my_slot = (int64_t)T.first + (my_valid ? my_a : 0);
+                const float my_sc = my_valid ? A.scale[my_slot] * esc : 0.f;
                 uint32_t re[32], im[32];
-                tmem_ld32(tmem + tlane + buf * kDCols + (uint32_t)a0, re);
-                tmem_ld32(tmem + tlane + buf * kDCols + (uint32_t)(T.nt + a0), im);
+                tmem_ld32(tmem + tlane + (uint32_t)a0, re);
+                tmem_ld32(tmem + tlane + (uint32_t)(T.nt + a0), im);
                 tmem_ld_wait();
-                if (a0 + 32 >= T.nt) {
+                if (a0 + 32 >= hi) {
                     fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(BAR(kBarDEmpty + buf));
+                    if (lane == 0) mbar_arrive(BAR(kBarDEmpty));
                 }
+                // z and |z|^2 exactly as the emitter forms them; one vote for the whole chunk
+                uint32_t hit = 0u;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    const int a = a0 + i;
-                    const bool valid = a < T.count;
-                    int32_t j = 0, o = 0;
-                    float sc = 0.f;
-                    if (valid) {
-                        const int64_t slot = (int64_t)T.first + a;
-                        j = A.perm[slot];
-                        o = A.off[slot];
-                        sc = A.scale[slot] * esc;
+                    const float sc = __shfl_sync(0xffffffffu, my_sc, i);
+                    const float zr = __fmul_rn(__uint_as_float(re[i]), sc);
+                    const float zi = -__fmul_rn(__uint_as_float(im[i]), sc);   // D holds -Im
+                    re[i] = __float_as_uint(zr);
+                    im[i] = __float_as_uint(zi);
+                    const float p = __fadd_rn(__fmul_rn(zr, zr), __fmul_rn(zi, zi));
+                    hit |= (p > A.thr ? 1u : 0u) << i;
+                }
+                if (__any_sync(0xffffffffu, hit != 0u)) {
+                    const int32_t my_j = my_valid ? A.perm[my_slot] : 0;
+                    const int32_t my_o = my_valid ? A.off[my_slot] : 0;
+                    const uint32_t any_bits = __reduce_or_sync(0xffffffffu, hit);
+#pragma unroll 1
+                    for (int i = 0; i < 32; ++i) {
+                        if (!((any_bits >> i) & 1u)) continue;          // warp-uniform
+                        const int32_t j = __shfl_sync(0xffffffffu, my_j, i);
+                        const int32_t o = __shfl_sync(0xffffffffu, my_o, i);
+                        const bool valid = a0 + i < T.count && a0 + i < hi;
+                        const uint32_t t = (uint32_t)((u + o) & (A.n - 1));
+                        float zr = 0.f, zi = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 32; ++q)
+                            if (q == i) {
+                                zr = __uint_as_float(re[q]);
+                                zi = __uint_as_float(im[q]);
+                            }
+                        emit_window_max(valid, (uint32_t)j, t, zr, zi, A.thr, A.W, A.cand, A.cap, A.count);
                     }
-                    const uint32_t t = (uint32_t)((u + o) & (A.n - 1));
-                    emit_window_max(valid, (uint32_t)j, t, __uint_as_float(re[i]) * sc,
-                                    __uint_as_float(im[i]) * sc, A.thr, A.W, A.cand, A.cap, A.count);
                 }
             }
+            (void)step;
         }
     }
 
@@ -318,9 +350,9 @@ __device__ __forceinline__ float from_h(__half x) { return __half2float(x); }
 __device__ __forceinline__ float from_h(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // One block per tile: per-template power-of-two scale (max |component| * 2^e < 2^8), then the
-// B-operand image: [hl][chunk][row][128 B], row < NT -> Re of template row, else Im of
-// template row - NT; element e of a chunk holds reversed tap k = 64 chunk + e, 16-byte units
-// XOR-swizzled by row % 8.  Also the per-slot lag offset and normalisation.
+// B-operand image: [hl][chunk][row][128 B] with rows [Pi (NT); Pr (NT); -Pi (NT)]; element e
+// of a chunk holds reversed tap k = 64 chunk + e, 16-byte units XOR-swizzled by row % 8.
+// Also the per-slot lag offset and normalisation.
 template <typename H>
 __global__ void __launch_bounds__(256) k_pack_tc(const TcTile *__restrict__ tiles, const float2 *__restrict__ taps,
                                                  int32_t k_stride, const int32_t *__restrict__ perm,
@@ -328,8 +360,8 @@ __global__ void __launch_bounds__(256) k_pack_tc(const TcTile *__restrict__ tile
                                                  const double *__restrict__ sigma, int64_t n,
                                                  uint8_t *__restrict__ out, int32_t *__restrict__ off,
                                                  float *__restrict__ scale) {
-    __shared__ int s_exp[64];
-    __shared__ int s_j[64], s_k[64];
+    __shared__ int s_exp[128];
+    __shared__ int s_j[128], s_k[128];
     const TcTile T = tiles[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int a = warp; a < T.nt; a += (int)(blockDim.x >> 5)) {
@@ -357,7 +389,7 @@ __global__ void __launch_bounds__(256) k_pack_tc(const TcTile *__restrict__ tile
         }
     }
     __syncthreads();
-    const int rows = 2 * T.nt;
+    const int rows = 3 * T.nt;
     const int64_t total = (int64_t)2 * T.nch * rows * 64;
     uint8_t *img = out + T.taps_off;
     for (int64_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -367,12 +399,13 @@ __global__ void __launch_bounds__(256) k_pack_tc(const TcTile *__restrict__ tile
         const int64_t r2 = r1 / rows;
         const int c = (int)(r2 % T.nch);
         const int hl = (int)(r2 / T.nch);
-        const int a = row % T.nt, part = row / T.nt;
+        const int a = row % T.nt, part = row / T.nt;   // 0: Pi, 1: Pr, 2: -Pi
         const int k = 64 * c + e;
         uint16_t bits = 0;
         if (a < T.count && k < s_k[a]) {
             const float2 v = taps[(int64_t)s_j[a] * k_stride + (s_k[a] - 1 - k)];
-            const float x = ldexpf(part ? v.y : v.x, s_exp[a]);
+            const float comp = part == 1 ? v.x : (part == 0 ? v.y : -v.y);
+            const float x = ldexpf(comp, s_exp[a]);
             const H hi = to_h<H>(x);
             bits = hl ? h_bits<H>(to_h<H>(x - from_h(hi))) : h_bits<H>(hi);
         }
