@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--n-tmpl", type=int, default=None, help="smaller bank (profiling cases only)")
+    ap.add_argument("--n-ref", type=int, default=None, help="fewer references (profiling cases only)")
     return ap.parse_args()
 
 
@@ -145,11 +146,13 @@ def recorded_traffic(kernel, source):
 PREC = {"fp32": 0, "fp16x3": 1, "bf16x3": 2}
 
 
-def workload_for_rank(c, rank, n_tmpl=None):
+def workload_for_rank(c, rank, n_tmpl=None, n_ref=None):
     import workload
     cfg = workload.get_config(c)
     if n_tmpl:
         cfg = dataclasses.replace(cfg, n_tmpl=n_tmpl, n_ref=min(cfg.n_ref, n_tmpl))
+    if n_ref:
+        cfg = dataclasses.replace(cfg, n_ref=min(n_ref, cfg.n_tmpl))
     if rank:
         # every rank filters its own segment: same bank, its own noise realisation
         cfg = dataclasses.replace(cfg, seeds=(cfg.seeds[0], cfg.seeds[1] + 7919 * rank, cfg.seeds[2]))
@@ -237,6 +240,9 @@ class GpuSearch:
                       cfg.k, cfg.tukey_alpha, self.taps, self.lag, self.sig, self.match)
         torch.cuda.synchronize()
         self.make_taps_s = time.perf_counter() - t0
+        # reference templates: set-up work (the references do not change between segments)
+        self.href = torch.zeros((bank.n_ref, cfg.n // 2 + 1), dtype=torch.complex64, device="cuda")
+        rfd.gen_templates(self.ctx, self.grid, bank.ref_params(), self.href)
         self.ld = rfd.qref_ld(cfg.n, self.halo)
         self.q = torch.zeros(bank.n_ref * self.ld * 8, dtype=torch.uint8, device="cuda")
         self.e = torch.zeros(bank.n_ref, dtype=torch.int32, device="cuda")
@@ -260,8 +266,7 @@ class GpuSearch:
         rfd = self.rfd
         if ev:
             ev[0].record()
-        rfd.filter_reference(self.ctx, self.grid, self.d, self.psd, self.bank.ref_params(), self.halo, self.prec,
-                             self.q, self.e)
+        rfd.filter_reference(self.ctx, self.grid, self.d, self.psd, self.href, self.halo, self.prec, self.q, self.e)
         if ev:
             ev[1].record()
         self.plan.ratio_filter_batch(self.q, self.e, self.cand, self.cnt)
@@ -285,35 +290,46 @@ class GpuSearch:
 
 
 def findchirp_rate(cfg, bank, data, device, steps=2):
-    """FINDCHIRP (Eq. 1 per template: PN template, pointwise, Stockham IFFT, same triggers)."""
+    """FINDCHIRP (Eq. 1 per template: pointwise, Stockham IFFT, same triggers) from templates
+    generated once per bank; plus the same batch of inverse FFTs through cuFFT for comparison."""
     import torch
     import paper_2601_18835_gb300 as rfd
     ctx = rfd.Context(device)
     g = rfd.grid(cfg.fs, cfg.n, cfg.f_low, cfg.pn_flags)
     psd = torch.from_numpy(data.psd).cuda()
     d = torch.from_numpy(data.dtilde.astype(np.complex64)).cuda()
+    h = torch.zeros((bank.n_tmpl, cfg.n // 2 + 1), dtype=torch.complex64, device="cuda")
+    rfd.gen_templates(ctx, g, bank.params(), h)
     cap = 1 << 22
     cand = torch.zeros(cap * 24, dtype=torch.uint8, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     trig = torch.zeros((1 << 20) * 20, dtype=torch.uint8, device="cuda")
-    params = bank.params()
 
     def one():
-        rfd.findchirp(ctx, g, d, psd, params, cfg.window, cfg.threshold, cand, cnt)
+        rfd.findchirp(ctx, g, d, psd, h, cfg.window, cfg.threshold, cand, cnt)
         return rfd.find_triggers(ctx, bank.n_tmpl, cand, cnt, trig)
-    one()
-    torch.cuda.synchronize()
-    times = []
-    for _ in range(steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        one()
-        e1.record()
+
+    def timed(fn, reps):
+        fn()
         torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return sum(ts) / len(ts)
+    t = timed(one, steps)
+    del h
+    # the inverse-FFT stage alone on a batch of 64 rows: own Stockham vs cuFFT
+    x = torch.randn((64, cfg.n), dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    t_own = timed(lambda: rfd.ifft_c2c(ctx, x, y), 5) / 64
+    t_cufft = timed(lambda: torch.fft.ifft(x, dim=-1), 5) / 64
     ctx.close()
-    t = sum(times) / len(times)
-    return bank.n_tmpl * cfg.duration / t, t
+    return bank.n_tmpl * cfg.duration / t, t, t_own, t_cufft
 
 
 def run_ours(args):
@@ -325,9 +341,9 @@ def run_ours(args):
         backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend)
     torch.cuda.set_device(local)
-    precision_name = args.precision or getattr(rfd, "DEFAULT_PRECISION_NAME", "fp32")
+    precision_name = args.precision or "fp16x3"
     prec = PREC[precision_name]
-    cfg, bank, data = workload_for_rank(args.config, rank, args.n_tmpl)
+    cfg, bank, data = workload_for_rank(args.config, rank, args.n_tmpl, args.n_ref)
     s = GpuSearch(cfg, bank, data, prec, local)
     J, dur = bank.n_tmpl, cfg.duration
 
@@ -426,21 +442,24 @@ def run_ours(args):
             comparisons["fp32_fir_step"] = {"value": J * dur / (sum(tt) / len(tt) / 1e3), "unit": UNIT,
                                             "ms_per_step": sum(tt) / len(tt)}
             s32.close()
-        fc_value, fc_t = findchirp_rate(cfg, bank, data, local)
-        comparisons["findchirp"] = {"value": fc_value, "unit": UNIT, "ms_per_step": fc_t * 1e3}
+        fc_value, fc_t, t_own, t_cufft = findchirp_rate(cfg, bank, data, local)
+        comparisons["findchirp"] = {"value": fc_value, "unit": UNIT, "ms_per_step": fc_t * 1e3,
+                                    "ifft_us_per_row_stockham": t_own * 1e6, "ifft_us_per_row_cufft": t_cufft * 1e6}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        ora, js, designs = oracle_sample(cfg, bank, data, 4)
+        ora, js, designs = oracle_sample(cfg, bank, data, 8)
         t0 = time.perf_counter()
         ora.q_ref(int(bank.ref_of_tmpl[js[0]]))
-        for j, d in zip(js, designs):
-            oracle_step(cfg, ora, j, d)
+        done = 0
+        while time.perf_counter() - t0 < 10.0:
+            oracle_step(cfg, ora, js[done % len(js)], designs[done % len(js)])
+            done += 1
         el = time.perf_counter() - t0
-        cpu = {"value": len(js) * dur / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one reference's FP64 matched filter plus %d templates through the oracle's direct "
-                         "circular FIR (K=%d, n=%d) and triggers; taps precomputed; %.1f s" % (len(js), cfg.k,
-                                                                                              cfg.n, el)}
+        cpu = {"value": done * dur / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one reference's FP64 matched filter plus %d template passes (8 distinct templates) "
+                         "through the oracle's direct circular FIR (K=%d, n=%d) and triggers, taps "
+                         "precomputed: %.1f s of one host core" % (done, cfg.k, cfg.n, el)}
 
     match = s.match.cpu().numpy()
     line = {

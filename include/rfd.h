@@ -150,23 +150,26 @@ rfd_status rfd_make_taps(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_d
 
 /* ------------------------------------------------------------------ filter_reference
  * The reference SNR series of Eq. 3, (s|h)_ref, one per reference (Eq. 1 discretised):
- *   c_r[k] = 4 df d[k] conj(h_r[k]) / S[k] for k in the reference band, 0 for all other
- *            k in [0, n);
+ *   c_r[k] = 4 df d[k] conj(h_r[k]) / S[k] for k <= n/2 (h_r is zero outside its band),
+ *            0 for k > n/2;
  *   q_r[m] = sum_k c_r[k] exp(+2 pi i k m / n)   (hand-written FP32 Stockham inverse FFT),
  * stored with a wrap halo q_r[n + i] = q_r[i], i < halo, so every FIR window
- * [u, u + K) with u < n is contiguous (halo >= K_max - 1).
- * Inputs: dtilde_dev complex64 [n/2+1]; psd_dev float64 [n/2+1]; refs_host [n_ref].
+ * [u, u + K) with u < n is contiguous (halo >= K_max - 1; the tensor-core path reads K
+ * rounded up to 16).
+ * Inputs: dtilde_dev complex64 [n/2+1]; psd_dev float64 [n/2+1]; href_dev complex64
+ * [n_ref][n/2+1], the reference templates as written by rfd_gen_templates (set-up work: the
+ * references do not change from segment to segment).
  * Output qref_dev, row length ld = rfd_qref_ld(n, halo):
  *   RFD_PREC_FP32:   complex64 q[r * ld + m];
  *   RFD_PREC_FP16X3 / BF16X3: four 2-byte planes per reference, plane p of reference r at
  *     element offset (4 r + p) ld, p = 0 re_hi, 1 im_hi, 2 re_lo, 3 im_lo, with
  *     hi = round(x 2^e_r), lo = round(x 2^e_r - hi).
  * qscale_dev int32 [n_ref] receives e_r (0 for FP32); e_r puts the rms of the scaled series
- *   near 2^10.  Deterministic: no atomics in any floating-point reduction. */
+ *   near 2^8.  Deterministic: no atomics in any floating-point reduction. */
 rfd_status rfd_filter_reference(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev,
-                                const double *psd_dev, const rfd_params *refs_host,
-                                int32_t n_ref, int32_t halo, int32_t precision,
-                                void *qref_dev, int32_t *qscale_dev, void *stream);
+                                const double *psd_dev, const void *href_dev, int32_t n_ref,
+                                int32_t halo, int32_t precision, void *qref_dev,
+                                int32_t *qscale_dev, void *stream);
 
 /* ------------------------------------------------------------------ plans
  * A plan fixes one bank's schedule: templates grouped by reference into tiles of the
@@ -249,11 +252,12 @@ rfd_status rfd_find_triggers_noalloc(int32_t n_tmpl, const rfd_candidate *cand_d
 
 /* ------------------------------------------------------------------ FINDCHIRP baseline
  * The standard frequency-domain matched filter of Eq. 1 for every template (Sec. II-III):
- * per template, h_j on the grid (FP64 phase), c = 4 df d conj(h_j) / S, an n-point FP32
- * Stockham inverse FFT, z = q / sigma(h_j), and the same threshold / window reduction into
- * candidates as rfd_ratio_filter_batch.  The comparison path for the ratio filter. */
+ * per template, c = 4 df d conj(h_j) / S, an n-point FP32 Stockham inverse FFT,
+ * z = q / sigma(h_j), and the same threshold / window reduction into candidates as
+ * rfd_ratio_filter_batch.  h_dev complex64 [n_tmpl][n/2+1] holds the templates (written by
+ * rfd_gen_templates once per bank).  The comparison path for the ratio filter. */
 rfd_status rfd_findchirp(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev,
-                         const double *psd_dev, const rfd_params *tmpl_host, int32_t n_tmpl,
+                         const double *psd_dev, const void *h_dev, int32_t n_tmpl,
                          int32_t window, float threshold, rfd_candidate *cand_dev,
                          int64_t cand_capacity, int64_t *cand_count_dev, void *stream);
 

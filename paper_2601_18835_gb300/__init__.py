@@ -114,10 +114,10 @@ def make_taps(ctx, g, psd, refs, tmpl, ref_of, k, k_stride, alpha, taps, lag, si
                                _ptr(match), _stream(stream)))
 
 
-def filter_reference(ctx, g, dtilde, psd, refs, halo, precision, qref, qscale, stream=None):
-    ra, nr = _params(refs)
-    check(_lib().rfd_filter_reference(ctx.handle, ctypes.byref(g), _ptr(dtilde), _ptr(psd), ra, nr,
-                                      int(halo), int(precision), _ptr(qref), _ptr(qscale),
+def filter_reference(ctx, g, dtilde, psd, href, halo, precision, qref, qscale, stream=None):
+    """href: complex64 [n_ref, n/2+1] reference templates (from gen_templates)."""
+    check(_lib().rfd_filter_reference(ctx.handle, ctypes.byref(g), _ptr(dtilde), _ptr(psd), _ptr(href),
+                                      int(href.shape[0]), int(halo), int(precision), _ptr(qref), _ptr(qscale),
                                       _stream(stream)))
 
 
@@ -183,11 +183,12 @@ def find_triggers_noalloc(n_tmpl, cand, cand_count, trig, stream=None):
     return int(n.value)
 
 
-def findchirp(ctx, g, dtilde, psd, tmpl, window, threshold, cand, cand_count, stream=None):
-    ta, nt = _params(tmpl)
+def findchirp(ctx, g, dtilde, psd, h, window, threshold, cand, cand_count, stream=None):
+    """h: complex64 [n_tmpl, n/2+1] templates (from gen_templates)."""
     cap = cand.numel() * cand.element_size() // CANDIDATE_DTYPE.itemsize
-    check(_lib().rfd_findchirp(ctx.handle, ctypes.byref(g), _ptr(dtilde), _ptr(psd), ta, nt, int(window),
-                               float(threshold), _ptr(cand), int(cap), _ptr(cand_count), _stream(stream)))
+    check(_lib().rfd_findchirp(ctx.handle, ctypes.byref(g), _ptr(dtilde), _ptr(psd), _ptr(h), int(h.shape[0]),
+                               int(window), float(threshold), _ptr(cand), int(cap), _ptr(cand_count),
+                               _stream(stream)))
 
 
 def ifft_c2c(ctx, x, out, stream=None):

@@ -62,7 +62,7 @@ SIGNATURES = {
     "rfd_make_taps": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _i32, _dbl,
                              _vp, _vp, _vp, _vp, _vp]),
     "rfd_filter_reference": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp,
-                                    _vp]),
+                                    _vp]),  # href_dev is a device pointer
     "rfd_plan_create": (_i32, [_vp, ctypes.POINTER(Grid), _i32, _i32, _vp, _vp, _i32, _i32, _flt, _i32,
                                ctypes.POINTER(_vp)]),
     "rfd_plan_destroy": (None, [_vp]),

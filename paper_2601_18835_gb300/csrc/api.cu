@@ -13,12 +13,10 @@ namespace rfd {
 // implemented in the kernel files
 rfd_status gen_templates_impl(rfd_ctx *, const Grid &, const std::vector<PNParams> &, float2 *,
                               cudaStream_t);
-rfd_status filter_reference_impl(rfd_ctx *, const Grid &, const float2 *, const double *,
-                                 const std::vector<PNParams> &, int32_t, int32_t, void *,
-                                 int32_t *, cudaStream_t);
-rfd_status findchirp_impl(rfd_ctx *, const Grid &, const float2 *, const double *,
-                          const std::vector<PNParams> &, int32_t, float, rfd_candidate *,
-                          int64_t, int64_t *, cudaStream_t);
+rfd_status filter_reference_impl(rfd_ctx *, const Grid &, const float2 *, const double *, const float2 *,
+                                 int64_t, int32_t, int32_t, void *, int32_t *, cudaStream_t);
+rfd_status findchirp_impl(rfd_ctx *, const Grid &, const float2 *, const double *, const float2 *, int64_t,
+                          int32_t, float, rfd_candidate *, int64_t, int64_t *, cudaStream_t);
 rfd_status make_taps_impl(rfd_ctx *, const Grid &, const double *, const std::vector<PNParams> &,
                           const std::vector<PNParams> &, const std::vector<int32_t> &,
                           const std::vector<int32_t> &, int32_t, double, float2 *, int32_t *,
@@ -306,23 +304,20 @@ rfd_status rfd_make_taps(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_d
 }
 
 rfd_status rfd_filter_reference(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev,
-                                const double *psd_dev, const rfd_params *refs_host, int32_t n_ref,
-                                int32_t halo, int32_t precision, void *qref_dev, int32_t *qscale_dev,
-                                void *stream) {
+                                const double *psd_dev, const void *href_dev, int32_t n_ref, int32_t halo,
+                                int32_t precision, void *qref_dev, int32_t *qscale_dev, void *stream) {
     RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
     Grid g;
     RFD_TRY(check_grid(grid, &g));
     RFD_REQUIRE(n_ref >= 0, RFD_ERR_SHAPE, "n_ref < 0");
     if (n_ref == 0) return RFD_OK;
-    RFD_REQUIRE(dtilde_dev && psd_dev && refs_host && qref_dev && qscale_dev, RFD_ERR_ARG, "NULL argument");
+    RFD_REQUIRE(dtilde_dev && psd_dev && href_dev && qref_dev && qscale_dev, RFD_ERR_ARG, "NULL argument");
     RFD_REQUIRE(halo >= 0 && halo < g.n, RFD_ERR_SHAPE, "halo=%d must be in [0, n)", halo);
     RFD_REQUIRE(precision >= RFD_PREC_FP32 && precision <= RFD_PREC_BF16X3, RFD_ERR_ARG, "bad precision %d",
                 precision);
     RFD_TRY_CUDA(cudaSetDevice(ctx->device));
-    std::vector<PNParams> refs;
-    RFD_TRY(make_pn_vec(g, refs_host, n_ref, &refs));
-    return filter_reference_impl(ctx, g, (const float2 *)dtilde_dev, psd_dev, refs, halo, precision, qref_dev,
-                                 qscale_dev, (cudaStream_t)stream);
+    return filter_reference_impl(ctx, g, (const float2 *)dtilde_dev, psd_dev, (const float2 *)href_dev, n_ref, halo,
+                                 precision, qref_dev, qscale_dev, (cudaStream_t)stream);
 }
 
 rfd_status rfd_plan_create(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
@@ -507,21 +502,18 @@ rfd_status rfd_find_triggers(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *
 }
 
 rfd_status rfd_findchirp(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev, const double *psd_dev,
-                         const rfd_params *tmpl_host, int32_t n_tmpl, int32_t window, float threshold,
-                         rfd_candidate *cand_dev, int64_t cand_capacity, int64_t *cand_count_dev,
-                         void *stream) {
+                         const void *h_dev, int32_t n_tmpl, int32_t window, float threshold,
+                         rfd_candidate *cand_dev, int64_t cand_capacity, int64_t *cand_count_dev, void *stream) {
     RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
     Grid g;
     RFD_TRY(check_grid(grid, &g));
     RFD_REQUIRE(n_tmpl >= 1, RFD_ERR_SHAPE, "n_tmpl must be >= 1");
-    RFD_REQUIRE(dtilde_dev && psd_dev && tmpl_host && cand_count_dev && (cand_dev || cand_capacity == 0),
-                RFD_ERR_ARG, "NULL argument");
+    RFD_REQUIRE(dtilde_dev && psd_dev && h_dev && cand_count_dev && (cand_dev || cand_capacity == 0), RFD_ERR_ARG,
+                "NULL argument");
     RFD_REQUIRE(window >= 1 && std::isfinite(threshold) && threshold >= 0.f, RFD_ERR_ARG, "bad window/threshold");
     RFD_TRY_CUDA(cudaSetDevice(ctx->device));
-    std::vector<PNParams> pn;
-    RFD_TRY(make_pn_vec(g, tmpl_host, n_tmpl, &pn));
-    return findchirp_impl(ctx, g, (const float2 *)dtilde_dev, psd_dev, pn, window, threshold, cand_dev,
-                          cand_capacity, cand_count_dev, (cudaStream_t)stream);
+    return findchirp_impl(ctx, g, (const float2 *)dtilde_dev, psd_dev, (const float2 *)h_dev, n_tmpl, window,
+                          threshold, cand_dev, cand_capacity, cand_count_dev, (cudaStream_t)stream);
 }
 
 rfd_status rfd_ifft_c2c(rfd_ctx *ctx, int64_t n, int32_t batch, const void *in_dev, void *out_dev, void *stream) {

@@ -41,34 +41,32 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
     return r;
 }
 
-// c[row][k] = 4 df d[k] conj(h_row[k]) / S[k] for k in the row's band (k_lo .. k_hi), 0 for
-// every other k in [0, n): the discretised integrand of Eq. 1.  Per block, writes the partial
-// sums of |c|^2 and of 4 df |h|^2 / S (sigma^2 of the row's template).
-__global__ void __launch_bounds__(256) k_weighted_spectrum(
-    const float2 *__restrict__ d, const double *__restrict__ psd, const PNParams *__restrict__ pn,
-    int flags, double df, int64_t n, int64_t k_lo, float2 *__restrict__ c, int64_t c_stride,
+// c[row][k] = 4 df d[k] conj(h_row[k]) / S[k] for k <= n/2 from a stored template row (zero
+// outside its band), 0 for k > n/2: the discretised integrand of Eq. 1.  Per block, partial
+// sums of |c|^2 and of 4 df |h|^2 / S (sigma^2 of the row's template), in FP64.
+__global__ void __launch_bounds__(256) k_spectrum_stored(
+    const float2 *__restrict__ d, const double *__restrict__ psd, const float2 *__restrict__ h,
+    int64_t h_stride, double df, int64_t n, float2 *__restrict__ c, int64_t c_stride,
     double *__restrict__ part_c, double *__restrict__ part_s) {
     __shared__ double sm[8];
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t row = blockIdx.y;
-    const PNParams p = pn[row];
-    double cr = 0.0, ci = 0.0, sg = 0.0;
-    if (k >= k_lo && k <= p.k_hi) {
-        const double f = (double)k * df;
-        const double psi = pn_phase(f, p, flags);
-        double s, co;
-        sincos(psi, &s, &co);
-        const double amp = pow(f, -7.0 / 6.0);
-        const double S = psd[k];
-        const double g = 4.0 * df * amp / S;
-        // conj(h) = amp (cos psi + i sin psi)
-        const double dr = (double)d[k].x, di = (double)d[k].y;
-        cr = g * (dr * co - di * s);
-        ci = g * (dr * s + di * co);
-        sg = 4.0 * df * amp * amp / S;
+    float cr = 0.f, ci = 0.f;
+    double sg = 0.0;
+    if (k <= n / 2) {
+        const float2 hv = h[row * h_stride + k];
+        if (hv.x != 0.f || hv.y != 0.f) {
+            const double w = 4.0 * df / psd[k];
+            const float wf = (float)w;
+            const float2 dv = d[k];
+            // d conj(h) = (dr hr + di hi) + i (di hr - dr hi)
+            cr = wf * (dv.x * hv.x + dv.y * hv.y);
+            ci = wf * (dv.y * hv.x - dv.x * hv.y);
+            sg = w * ((double)hv.x * hv.x + (double)hv.y * hv.y);
+        }
     }
-    if (k < n) c[row * c_stride + k] = make_float2((float)cr, (float)ci);
-    const double pc = block_sum(cr * cr + ci * ci, sm);
+    c[row * c_stride + k] = make_float2(cr, ci);
+    const double pc = block_sum((double)cr * cr + (double)ci * ci, sm);
     const double ps = block_sum(sg, sm);
     if (threadIdx.x == 0) {
         part_c[row * gridDim.x + blockIdx.x] = pc;
@@ -179,30 +177,25 @@ rfd_status gen_templates_impl(rfd_ctx *ctx, const Grid &g, const std::vector<PNP
     return RFD_OK;
 }
 
-// Workspace slots: ws[0] params, ws[1] spectrum c, ws[2] FFT output, ws[3] FFT tmp,
-// ws[4] partials, ws[5] per-row sums.
+// Workspace slots: ws[1] spectrum c, ws[2] FFT output, ws[3] FFT tmp, ws[4] partials,
+// ws[5] per-row sums.
 rfd_status filter_reference_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, const double *psd,
-                                 const std::vector<PNParams> &pn, int32_t halo, int32_t precision,
+                                 const float2 *href, int64_t R, int32_t halo, int32_t precision,
                                  void *qref, int32_t *qscale, cudaStream_t s) {
-    const int64_t R = (int64_t)pn.size();
     const int64_t n = g.n, ld = rfd_qref_ld(n, halo);
     const unsigned nblk = (unsigned)(n / 256);
-    RFD_TRY(ensure(ctx->ws[0], R * sizeof(PNParams)));
     RFD_TRY(ensure(ctx->ws[1], R * n * sizeof(float2)));
     RFD_TRY(ensure(ctx->ws[2], R * n * sizeof(float2)));
     RFD_TRY(ensure(ctx->ws[3], R * n * sizeof(float2)));
     RFD_TRY(ensure(ctx->ws[4], 2 * R * nblk * sizeof(double)));
     RFD_TRY(ensure(ctx->ws[5], 2 * R * sizeof(double)));
-    RFD_TRY_CUDA(cudaMemcpyAsync(ctx->ws[0].p, pn.data(), R * sizeof(PNParams),
-                                 cudaMemcpyHostToDevice, s));
     float2 *c = (float2 *)ctx->ws[1].p;
     double *part = (double *)ctx->ws[4].p;
     double *sums = (double *)ctx->ws[5].p;
     for (int64_t r0 = 0; r0 < R; r0 += 65535) {
         const unsigned gy = (unsigned)std::min<int64_t>(65535, R - r0);
-        k_weighted_spectrum<<<dim3(nblk, gy), 256, 0, s>>>(
-            d, psd, (const PNParams *)ctx->ws[0].p + r0, g.pn_flags, g.df, n, g.k_lo, c + r0 * n, n,
-            part + r0 * nblk, part + R * nblk + r0 * nblk);
+        k_spectrum_stored<<<dim3(nblk, gy), 256, 0, s>>>(d, psd, href + r0 * g.nf, g.nf, g.df, n, c + r0 * n, n,
+                                                         part + r0 * nblk, part + R * nblk + r0 * nblk);
         RFD_LAUNCH_CHECK();
     }
     k_sum_rows<<<(unsigned)R, 256, 0, s>>>(part, nblk, sums);
@@ -229,32 +222,28 @@ rfd_status filter_reference_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, c
     return RFD_OK;
 }
 
-// FINDCHIRP over all templates in batches; candidates as in the ratio-filter epilogue.
-rfd_status findchirp_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, const double *psd,
-                          const std::vector<PNParams> &pn, int32_t W, float thr,
-                          rfd_candidate *cand, int64_t cap, int64_t *count, cudaStream_t s) {
-    const int64_t J = (int64_t)pn.size();
+// FINDCHIRP over all templates in batches from stored templates; candidates as in the
+// ratio-filter epilogue.
+rfd_status findchirp_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, const double *psd, const float2 *h,
+                          int64_t J, int32_t W, float thr, rfd_candidate *cand, int64_t cap, int64_t *count,
+                          cudaStream_t s) {
     const int64_t n = g.n;
     const unsigned nblk = (unsigned)(n / 256);
     // batch so that three complex64 work arrays stay near 3 GB
     int64_t B = std::max<int64_t>(1, ((int64_t)1 << 30) / (n * (int64_t)sizeof(float2)));
-    B = std::min<int64_t>(B, J);
-    RFD_TRY(ensure(ctx->ws[0], J * sizeof(PNParams)));
+    B = std::min<int64_t>(std::min<int64_t>(B, J), 65535);
     RFD_TRY(ensure(ctx->ws[1], B * n * sizeof(float2)));
     RFD_TRY(ensure(ctx->ws[2], B * n * sizeof(float2)));
     RFD_TRY(ensure(ctx->ws[3], B * n * sizeof(float2)));
     RFD_TRY(ensure(ctx->ws[4], 2 * B * nblk * sizeof(double)));
     RFD_TRY(ensure(ctx->ws[5], 2 * B * sizeof(double)));
-    RFD_TRY_CUDA(cudaMemcpyAsync(ctx->ws[0].p, pn.data(), J * sizeof(PNParams),
-                                 cudaMemcpyHostToDevice, s));
     RFD_TRY_CUDA(cudaMemsetAsync(count, 0, sizeof(int64_t), s));
     float2 *c = (float2 *)ctx->ws[1].p, *q = (float2 *)ctx->ws[2].p;
     double *part = (double *)ctx->ws[4].p, *sums = (double *)ctx->ws[5].p;
     for (int64_t j0 = 0; j0 < J; j0 += B) {
         const int64_t b = std::min<int64_t>(B, J - j0);
-        k_weighted_spectrum<<<dim3(nblk, (unsigned)b), 256, 0, s>>>(
-            d, psd, (const PNParams *)ctx->ws[0].p + j0, g.pn_flags, g.df, n, g.k_lo, c, n, part,
-            part + B * nblk);
+        k_spectrum_stored<<<dim3(nblk, (unsigned)b), 256, 0, s>>>(d, psd, h + j0 * g.nf, g.nf, g.df, n, c, n, part,
+                                                                 part + B * nblk);
         RFD_LAUNCH_CHECK();
         k_sum_rows<<<(unsigned)b, 256, 0, s>>>(part + B * nblk, nblk, sums);
         RFD_LAUNCH_CHECK();

@@ -29,12 +29,18 @@ class GpuRun:
         torch.cuda.synchronize()
         return {"taps": taps, "lag": lag, "sigma": sig, "match": mat, "K": K, "k_stride": ks, "idx": idx}
 
+    def templates(self, params):
+        h = torch.zeros((len(params), self.n // 2 + 1), dtype=torch.complex64, device="cuda")
+        rfd.gen_templates(self.ctx, self.grid, params, h)
+        return h
+
     def filter_reference(self, halo, precision):
         R = self.bank.n_ref
         ld = rfd.qref_ld(self.n, halo)
         q = torch.zeros(R * ld * 8, dtype=torch.uint8, device="cuda")
         e = torch.zeros(R, dtype=torch.int32, device="cuda")
-        rfd.filter_reference(self.ctx, self.grid, self.d, self.psd, self.bank.ref_params(), halo, precision, q, e)
+        href = self.templates(self.bank.ref_params())
+        rfd.filter_reference(self.ctx, self.grid, self.d, self.psd, href, halo, precision, q, e)
         torch.cuda.synchronize()
         return q, e, ld
 

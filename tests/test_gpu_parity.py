@@ -163,7 +163,8 @@ def test_c1_findchirp_matches_oracle(c1):
     cap = 1 << 18
     cand = torch.zeros(cap * 24, dtype=torch.uint8, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-    rfd.findchirp(gpu.ctx, gpu.grid, gpu.d, gpu.psd, bank.params(), cfg.window, cfg.threshold, cand, cnt)
+    rfd.findchirp(gpu.ctx, gpu.grid, gpu.d, gpu.psd, gpu.templates(bank.params()), cfg.window, cfg.threshold,
+                  cand, cnt)
     trig = torch.zeros(cap * 20, dtype=torch.uint8, device="cuda")
     nt = rfd.find_triggers(gpu.ctx, bank.n_tmpl, cand, cnt, trig)
     tr = rfd.triggers_to_numpy(trig, nt)
@@ -182,8 +183,8 @@ def test_ratio_peak_within_one_percent_of_findchirp_gpu(c1):
     cap = 1 << 16
     cand = torch.zeros(cap * 24, dtype=torch.uint8, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-    rfd.findchirp(gpu.ctx, gpu.grid, gpu.d, gpu.psd, bank.params()[slot:slot + 1], cfg.window, cfg.threshold,
-                  cand, cnt)
+    rfd.findchirp(gpu.ctx, gpu.grid, gpu.d, gpu.psd, gpu.templates(bank.params()[slot:slot + 1]), cfg.window,
+                  cfg.threshold, cand, cnt)
     tb = torch.zeros(cap * 20, dtype=torch.uint8, device="cuda")
     nt = rfd.find_triggers(gpu.ctx, 1, cand, cnt, tb)
     pf = float(rfd.triggers_to_numpy(tb, nt)["snr2"].max())
