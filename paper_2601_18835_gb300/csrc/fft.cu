@@ -2,11 +2,13 @@
 // series of Eq. 3 and the FP64 tap design of Sec. V.
 //
 // Stockham auto-sort: each pass p with radix R reads element j + r n/R (r < R), applies the
-// twiddles exp(+-2 pi i r (j mod Ns) / (Ns R)), does a radix-R butterfly in registers and
-// writes to (j - j mod Ns) R + (j mod Ns) + r Ns, where Ns is the product of the radices of
-// the earlier passes.  No bit reversal is needed.  A radix-2 pass is used first when log2 n
-// is odd, then radix-4 passes.  Twiddles come from a table w[m] = exp(+2 pi i m / n) built
-// once per n with FP64 sincospi.
+// twiddles exp(+-2 pi i r (j mod Ns) / (Ns R)), does an R-point DFT in registers and writes
+// to (j - j mod Ns) R + (j mod Ns) + r Ns, where Ns is the product of the radices of the
+// earlier passes.  No bit reversal is needed.  Radix-16 passes, preceded by one radix-2, -4
+// or -8 pass when log2 n is not a multiple of 4 (n = 2^19: 5 passes over memory).  The
+// R-point DFT is an unrolled radix-2 decimation-in-time network over the 16th roots of
+// unity; the pass twiddles come from a table w[m] = exp(+2 pi i m / n) built once per n with
+// FP64 sincospi.
 #include "internal.cuh"
 
 namespace rfd {
@@ -21,10 +23,6 @@ template <typename T2>
 __device__ __forceinline__ T2 cmulc(T2 a, T2 b) {   // a * conj(b)
     return T2{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
-template <typename T2>
-__device__ __forceinline__ T2 cadd(T2 a, T2 b) { return T2{a.x + b.x, a.y + b.y}; }
-template <typename T2>
-__device__ __forceinline__ T2 csub(T2 a, T2 b) { return T2{a.x - b.x, a.y - b.y}; }
 
 __global__ void k_twiddle64(double2 *w, int64_t n) {
     int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -38,6 +36,60 @@ __global__ void k_twiddle32(const double2 *w64, float2 *w32, int64_t n) {
     int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (m >= n) return;
     w32[m] = make_float2((float)w64[m].x, (float)w64[m].y);
+}
+
+// cos and sin of 2 pi t / 16, t = 0 .. 15 (exact values of the 16th roots of unity)
+__device__ __constant__ double kRoot16[16][2] = {
+    {1.0, 0.0},
+    {0.92387953251128675613, 0.38268343236508977173},
+    {0.70710678118654752440, 0.70710678118654752440},
+    {0.38268343236508977173, 0.92387953251128675613},
+    {0.0, 1.0},
+    {-0.38268343236508977173, 0.92387953251128675613},
+    {-0.70710678118654752440, 0.70710678118654752440},
+    {-0.92387953251128675613, 0.38268343236508977173},
+    {-1.0, 0.0},
+    {-0.92387953251128675613, -0.38268343236508977173},
+    {-0.70710678118654752440, -0.70710678118654752440},
+    {-0.38268343236508977173, -0.92387953251128675613},
+    {0.0, -1.0},
+    {0.38268343236508977173, -0.92387953251128675613},
+    {0.70710678118654752440, -0.70710678118654752440},
+    {0.92387953251128675613, -0.38268343236508977173}};
+
+__host__ __device__ constexpr int bitrev(int x, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((x >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+// y[k] = sum_r v[r] exp(sign 2 pi i r k / R), in place, R = 2, 4, 8 or 16.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void dft_reg(typename Cplx<T>::type (&v)[R]) {
+    using T2 = typename Cplx<T>::type;
+    constexpr int L = R == 2 ? 1 : (R == 4 ? 2 : (R == 8 ? 3 : 4));
+    T2 a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[bitrev(r, L)] = v[r];
+#pragma unroll
+    for (int m = 2; m <= R; m <<= 1) {
+        const int half = m >> 1;
+#pragma unroll
+        for (int g = 0; g < R; g += m) {
+#pragma unroll
+            for (int t = 0; t < half; ++t) {
+                const int e = t * (16 / m);                       // exp(2 pi i t / m) = root16^e
+                const T wr = (T)kRoot16[e][0];
+                const T wi = INV ? (T)kRoot16[e][1] : -(T)kRoot16[e][1];
+                const T2 x = a[g + t], y = a[g + t + half];
+                const T2 yw = T2{y.x * wr - y.y * wi, y.x * wi + y.y * wr};
+                a[g + t] = T2{x.x + yw.x, x.y + yw.y};
+                a[g + t + half] = T2{x.x - yw.x, x.y - yw.y};
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = a[r];
 }
 
 template <typename T, int R, bool INV>
@@ -66,20 +118,7 @@ __global__ void __launch_bounds__(256) k_stockham(const typename Cplx<T>::type *
             v[r] = INV ? cmul(v[r], w) : cmulc(v[r], w);
         }
     }
-    if (R == 2) {
-        const T2 a = v[0], c = v[1];
-        v[0] = cadd(a, c);
-        v[1] = csub(a, c);
-    } else {
-        const T2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
-        const T2 a2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
-        // multiply d by +i (inverse) or -i (forward)
-        const T2 a3 = INV ? T2{-d.y, d.x} : T2{d.y, -d.x};
-        v[0] = cadd(a0, a2);
-        v[2] = csub(a0, a2);
-        v[1] = cadd(a1, a3);
-        v[3] = csub(a1, a3);
-    }
+    dft_reg<T, R, INV>(v);
     const int64_t idx = (j - k) * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[idx + r * ns] = v[r];
@@ -134,8 +173,8 @@ rfd_status fft_c2c(rfd_ctx *ctx, int64_t n, int64_t batch, const typename Cplx<T
     int log2n = 0;
     while ((int64_t(1) << log2n) < n) ++log2n;
     std::vector<int> radix;
-    if (log2n & 1) radix.push_back(2);
-    for (int i = 0; i < log2n / 2; ++i) radix.push_back(4);
+    if (log2n % 4) radix.push_back(1 << (log2n % 4));
+    for (int i = 0; i < log2n / 4; ++i) radix.push_back(16);
     const int P = (int)radix.size();
     int64_t ns = 1;
     const T2 *src = in;
@@ -150,17 +189,18 @@ rfd_status fft_c2c(rfd_ctx *ctx, int64_t n, int64_t batch, const typename Cplx<T
         for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
             const unsigned gy = (unsigned)std::min<int64_t>(65535, batch - b0);
             dim3 grid(gx, gy);
-            if (R == 2) {
-                if (inverse)
-                    k_stockham<T, 2, true><<<grid, 256, 0, s>>>(src, src_stride, dst, dst_stride, tw, n, ns, b0);
-                else
-                    k_stockham<T, 2, false><<<grid, 256, 0, s>>>(src, src_stride, dst, dst_stride, tw, n, ns, b0);
-            } else {
-                if (inverse)
-                    k_stockham<T, 4, true><<<grid, 256, 0, s>>>(src, src_stride, dst, dst_stride, tw, n, ns, b0);
-                else
-                    k_stockham<T, 4, false><<<grid, 256, 0, s>>>(src, src_stride, dst, dst_stride, tw, n, ns, b0);
-            }
+#define RFD_PASS(RR)                                                                                       \
+    do {                                                                                                   \
+        if (inverse)                                                                                       \
+            k_stockham<T, RR, true><<<grid, 256, 0, s>>>(src, src_stride, dst, dst_stride, tw, n, ns, b0);  \
+        else                                                                                               \
+            k_stockham<T, RR, false><<<grid, 256, 0, s>>>(src, src_stride, dst, dst_stride, tw, n, ns, b0); \
+    } while (0)
+            if (R == 2) RFD_PASS(2);
+            else if (R == 4) RFD_PASS(4);
+            else if (R == 8) RFD_PASS(8);
+            else RFD_PASS(16);
+#undef RFD_PASS
             RFD_LAUNCH_CHECK();
         }
         ns *= R;

@@ -41,36 +41,48 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
     return r;
 }
 
+// Block-wide FP32 sum in a fixed order; result valid in thread 0.
+__device__ __forceinline__ float block_sum_f(float v, float *sm) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    float r = 0.f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sm[i];
+    __syncthreads();
+    return r;
+}
+
 // c[row][k] = 4 df d[k] conj(h_row[k]) / S[k] for k <= n/2 from a stored template row (zero
-// outside its band), 0 for k > n/2: the discretised integrand of Eq. 1.  Per block, partial
-// sums of |c|^2 and of 4 df |h|^2 / S (sigma^2 of the row's template), in FP64.
+// outside its band), 0 for k > n/2: the discretised integrand of Eq. 1, in FP32.  Per block,
+// partial sums of |c|^2 and of 4 df |h|^2 / S (sigma^2 of the row's template); the partials
+// are summed in FP64 in a fixed order afterwards, so the result is deterministic.
 __global__ void __launch_bounds__(256) k_spectrum_stored(
     const float2 *__restrict__ d, const double *__restrict__ psd, const float2 *__restrict__ h,
     int64_t h_stride, double df, int64_t n, float2 *__restrict__ c, int64_t c_stride,
     double *__restrict__ part_c, double *__restrict__ part_s) {
-    __shared__ double sm[8];
+    __shared__ float sm[8];
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t row = blockIdx.y;
-    float cr = 0.f, ci = 0.f;
-    double sg = 0.0;
+    float cr = 0.f, ci = 0.f, sg = 0.f;
     if (k <= n / 2) {
         const float2 hv = h[row * h_stride + k];
         if (hv.x != 0.f || hv.y != 0.f) {
-            const double w = 4.0 * df / psd[k];
-            const float wf = (float)w;
+            const float w = (float)(4.0 * df) / (float)psd[k];
             const float2 dv = d[k];
             // d conj(h) = (dr hr + di hi) + i (di hr - dr hi)
-            cr = wf * (dv.x * hv.x + dv.y * hv.y);
-            ci = wf * (dv.y * hv.x - dv.x * hv.y);
-            sg = w * ((double)hv.x * hv.x + (double)hv.y * hv.y);
+            cr = w * (dv.x * hv.x + dv.y * hv.y);
+            ci = w * (dv.y * hv.x - dv.x * hv.y);
+            sg = w * (hv.x * hv.x + hv.y * hv.y);
         }
     }
     c[row * c_stride + k] = make_float2(cr, ci);
-    const double pc = block_sum((double)cr * cr + (double)ci * ci, sm);
-    const double ps = block_sum(sg, sm);
+    const float pc = block_sum_f(cr * cr + ci * ci, sm);
+    const float ps = block_sum_f(sg, sm);
     if (threadIdx.x == 0) {
-        part_c[row * gridDim.x + blockIdx.x] = pc;
-        part_s[row * gridDim.x + blockIdx.x] = ps;
+        part_c[row * gridDim.x + blockIdx.x] = (double)pc;
+        part_s[row * gridDim.x + blockIdx.x] = (double)ps;
     }
 }
 

@@ -63,7 +63,7 @@ def compare_triggers(gpu_trig, oracle_sets, tol, js, W):
 
 
 # --------------------------------------------------------------------------- FFT
-@pytest.mark.parametrize("n,batch", [(1024, 3), (16384, 2), (524288, 2)])
+@pytest.mark.parametrize("n,batch", [(1024, 3), (8192, 2), (16384, 2), (32768, 1), (524288, 2), (1048576, 1)])
 def test_ifft_matches_numpy(ctx, n, batch):
     rng = np.random.default_rng(n)
     x = (rng.standard_normal((batch, n)) + 1j * rng.standard_normal((batch, n))).astype(np.complex64)
