@@ -128,24 +128,32 @@ rfd_status rfd_gen_templates(rfd_ctx *ctx, const rfd_grid *grid, const rfd_param
  *            0 above the template's cutoff, and a linear magnitude / shortest-arc phase
  *            fill from G[k_hi] round the out-of-band arc to G[k_lo];
  *   g      = (1/n) IDFT_n(G)                              (hand-written FP64 Stockham FFT);
+ *   K_j    = k_host[j], or, when k_host is NULL, the smallest entry of buckets_host whose
+ *            best circular window of that many samples holds energy_frac of sum |g|^2 (the
+ *            largest bucket when none does) -- the tap count from the ratio's bandwidth;
  *   s_j    = argmax over s in [-n/2, n/2) of E[s] = sum_k w[k]^2 |g[(s+k) mod n]|^2,
- *            w = symmetric Tukey(K, tukey_alpha); values within 1e-9 relative of the maximum
- *            tie, and ties go to the s closest to -K/2, then to the smaller s;
- *   rho[k] = w[k] g[(s_j + k) mod n], k < K;
+ *            w = symmetric Tukey(K_j, tukey_alpha); values within 1e-9 relative of the
+ *            maximum tie, and ties go to the s closest to -K_j/2, then to the smaller s (found
+ *            exactly, evaluating E only where the unweighted window energy can reach it);
+ *   rho[k] = w[k] g[(s_j + k) mod n], k < K_j;
  *   sigma_eff^2 = sum_{a,b} rho[a] conj(rho[b]) C_r[b - a],
  *            C_r[l] = 4 df sum_{k in band_r} |h_r,k|^2 / S_k exp(+2 pi i k l / n);
  *   match  = |<h_j, h_eff>| / (|h_j| |h_eff|), h_eff = h_r conj(A), A = DFT of the placed taps.
  * Inputs: psd_dev float64 [n/2+1]; refs_host [n_ref]; tmpl_host [n_tmpl];
- *   ref_of_tmpl_host int32 [n_tmpl] in [0, n_ref); k_host int32 [n_tmpl], 1 <= K <= k_stride.
+ *   ref_of_tmpl_host int32 [n_tmpl] in [0, n_ref); k_host int32 [n_tmpl] with
+ *   1 <= K <= k_stride, or NULL with buckets_host int32 [n_buckets] increasing, each
+ *   <= k_stride, and energy_frac in (0, 1].
  * Outputs (device, caller-allocated): taps_dev complex64 [n_tmpl][k_stride] (entries past K
- *   are zeroed), lag_dev int32 [n_tmpl] (s_j), sigma_dev float64 [n_tmpl],
- *   match_dev float64 [n_tmpl] or NULL to skip the match (it costs one more FFT per template).
+ *   are zeroed), k_dev int32 [n_tmpl] (K_j; may be NULL when k_host is given),
+ *   lag_dev int32 [n_tmpl] (s_j), sigma_dev float64 [n_tmpl], match_dev float64 [n_tmpl] or
+ *   NULL to skip the match (it costs one more FFT per template).
  * Synchronises the stream before returning (its FP64 workspace is sized per batch). */
 rfd_status rfd_make_taps(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_dev,
                          const rfd_params *refs_host, int32_t n_ref,
                          const rfd_params *tmpl_host, const int32_t *ref_of_tmpl_host,
-                         int32_t n_tmpl, const int32_t *k_host, int32_t k_stride,
-                         double tukey_alpha, void *taps_dev, int32_t *lag_dev,
+                         int32_t n_tmpl, const int32_t *k_host, const int32_t *buckets_host,
+                         int32_t n_buckets, double energy_frac, int32_t k_stride,
+                         double tukey_alpha, void *taps_dev, int32_t *k_dev, int32_t *lag_dev,
                          double *sigma_dev, double *match_dev, void *stream);
 
 /* ------------------------------------------------------------------ filter_reference

@@ -104,14 +104,23 @@ def gen_templates(ctx, g, params, out, stream=None):
 
 
 def make_taps(ctx, g, psd, refs, tmpl, ref_of, k, k_stride, alpha, taps, lag, sigma, match=None,
-              stream=None):
+              stream=None, buckets=None, energy_frac=0.999, k_out=None):
+    """k: taps per template (array), or None to choose each K from `buckets` (the smallest
+    bucket whose best window holds `energy_frac` of the impulse response's energy); the
+    chosen K is written to k_out (device int32)."""
     ra, nr = _params(refs)
     ta, nt = _params(tmpl)
     ro, rop = _i32_host(ref_of)
-    kk, kp = _i32_host(k)
-    check(_lib().rfd_make_taps(ctx.handle, ctypes.byref(g), _ptr(psd), ra, nr, ta, rop, nt, kp,
-                               int(k_stride), float(alpha), _ptr(taps), _ptr(lag), _ptr(sigma),
-                               _ptr(match), _stream(stream)))
+    if k is None:
+        kp = None
+        bk, bkp = _i32_host(buckets)
+        nbk = len(bk)
+    else:
+        kk, kp = _i32_host(k)
+        bkp, nbk = None, 0
+    check(_lib().rfd_make_taps(ctx.handle, ctypes.byref(g), _ptr(psd), ra, nr, ta, rop, nt, kp, bkp, nbk,
+                               float(energy_frac), int(k_stride), float(alpha), _ptr(taps), _ptr(k_out),
+                               _ptr(lag), _ptr(sigma), _ptr(match), _stream(stream)))
 
 
 def filter_reference(ctx, g, dtilde, psd, href, halo, precision, qref, qscale, stream=None):

@@ -59,8 +59,8 @@ SIGNATURES = {
     "rfd_ctx_trim": (None, [_vp]),
     "rfd_qref_ld": (_i64, [_i64, _i32]),
     "rfd_gen_templates": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _i32, _vp, _vp]),
-    "rfd_make_taps": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _i32, _dbl,
-                             _vp, _vp, _vp, _vp, _vp]),
+    "rfd_make_taps": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _dbl,
+                             _i32, _dbl, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rfd_filter_reference": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp,
                                     _vp]),  # href_dev is a device pointer
     "rfd_plan_create": (_i32, [_vp, ctypes.POINTER(Grid), _i32, _i32, _vp, _vp, _i32, _i32, _flt, _i32,

@@ -5,8 +5,13 @@
 //   1. G = conj(h_j / h_r) from the FP64 phase difference in the reference band (0 above the
 //      template's cutoff), linear magnitude / shortest-arc phase fill on the out-of-band arc;
 //   2. g = IDFT_n(G) (FP64 Stockham; the 1/n is applied when the taps are cut);
-//   3. E[s] = sum_k w[k]^2 |g[(s+k) mod n]|^2 for every s, its maximum, then the tie rule
-//      (within 1e-9 of the maximum; closest to s = -K/2, then smaller s);
+//   3. K (when bucketed): the smallest bucket b whose best circular window of b samples holds
+//      `frac` of sum |g|^2 (prefix sums of |g|^2, FP64);
+//      lag: the maximiser of E[s] = sum_k w[k]^2 |g[(s+k) mod n]|^2 with the tie rule (within
+//      1e-9 of the maximum; closest to s = -K/2, then smaller s).  Since w^2 <= 1,
+//      E[s] <= U[s] = sum_k |g[(s+k) mod n]|^2, so E is evaluated exactly only where U reaches
+//      E at the argmax of U (minus a rounding allowance): the same maximiser as an exhaustive
+//      search, at O(n + candidates K) instead of O(n K);
 //   4. rho[k] = w[k] g[(s+k) mod n] / n;
 //   5. sigma_eff^2 = sum_{a,b} rho[a] conj(rho[b]) C_r[b-a] (C_r from one FP64 IDFT per
 //      reference of 4 df |h_r|^2 / S);
@@ -99,39 +104,149 @@ __global__ void __launch_bounds__(256) k_ratio_spectrum(const TapJob *__restrict
     G[(int64_t)b * n + k] = out;
 }
 
-// E[s] for s = i - n/2, i in [0, n); 256 consecutive s per block; per-template maximum.
-__global__ void __launch_bounds__(256) k_window_energy(const TapJob *__restrict__ jobs,
-                                                       const double2 *__restrict__ g, int64_t n,
-                                                       double alpha, double *__restrict__ E,
-                                                       unsigned long long *__restrict__ emax) {
-    extern __shared__ double sh[];
-    const int b = blockIdx.y;
-    const int K = jobs[b].K;
-    double *w2 = sh;                 // [K]
-    double *e = sh + K;              // [256 + K - 1]
-    const int64_t i0 = (int64_t)blockIdx.x * 256;
-    const int64_t s0 = i0 - n / 2;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const double w = tukey_w(k, K, alpha);
-        w2[k] = w * w;
-    }
+// P[b][i] = sum_{m < i} |g_b[m]|^2, i = 0 .. n, one block per template (fixed-order scan).
+__global__ void __launch_bounds__(1024) k_energy_prefix(const double2 *__restrict__ g, int64_t n,
+                                                        double *__restrict__ P) {
+    __shared__ double part[1024];
+    const int b = blockIdx.x;
     const double2 *gb = g + (int64_t)b * n;
-    for (int t = threadIdx.x; t < 256 + K - 1; t += blockDim.x) {
-        const int64_t m = ((s0 + t) % n + n) % n;
-        const double2 v = gb[m];
-        e[t] = v.x * v.x + v.y * v.y;
+    double *Pb = P + (int64_t)b * (n + 1);
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = min(n, (int64_t)threadIdx.x * per), hi = min(n, lo + per);
+    double acc = 0.0;
+    for (int64_t i = lo; i < hi; ++i) {
+        const double2 v = gb[i];
+        acc += v.x * v.x + v.y * v.y;
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double run = 0.0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            const double v = part[t];
+            part[t] = run;
+            run += v;
+        }
+        Pb[n] = run;
     }
     __syncthreads();
-    double acc = 0.0;
-    for (int k = 0; k < K; ++k) acc += w2[k] * e[threadIdx.x + k];
-    E[(int64_t)b * n + i0 + threadIdx.x] = acc;
-    // block max (E >= 0, so the bit patterns order like the values)
-    unsigned long long bits = (unsigned long long)__double_as_longlong(acc);
+    double run = part[threadIdx.x];
+    for (int64_t i = lo; i < hi; ++i) {
+        Pb[i] = run;
+        const double2 v = gb[i];
+        run += v.x * v.x + v.y * v.y;
+    }
+}
+
+// sum of |g|^2 over the circular window [m, m + L), from the prefix sums
+__device__ __forceinline__ double window_sum(const double *__restrict__ P, int64_t n, int64_t m, int64_t L) {
+    return (m + L <= n) ? P[m + L] - P[m] : (P[n] - P[m]) + P[m + L - n];
+}
+
+// per template and bucket: the best window energy over all starts (max of bit patterns)
+__global__ void __launch_bounds__(256) k_bucket_max(const double *__restrict__ P, int64_t n,
+                                                    const int32_t *__restrict__ buckets, int nb,
+                                                    unsigned long long *__restrict__ bmax) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    const double *Pb = P + (int64_t)b * (n + 1);
+    for (int i = 0; i < nb; ++i) {
+        unsigned long long bits = 0ull;
+        if (m < n) bits = (unsigned long long)__double_as_longlong(fmax(0.0, window_sum(Pb, n, m, buckets[i])));
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_down_sync(0xffffffffu, bits, o);
+            bits = other > bits ? other : bits;
+        }
+        if ((threadIdx.x & 31) == 0) atomicMax(&bmax[(int64_t)b * nb + i], bits);
+    }
+}
+
+// K_j = the smallest bucket whose best window holds frac of the energy (else the largest)
+__global__ void k_bucket_pick(TapJob *jobs, int nbt, const double *__restrict__ P, int64_t n,
+                              const int32_t *__restrict__ buckets, int nb, double frac,
+                              const unsigned long long *__restrict__ bmax, int32_t j0,
+                              int32_t *__restrict__ k_out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbt) return;
+    const double total = P[(int64_t)b * (n + 1) + n];
+    int K = buckets[nb - 1];
+    for (int i = 0; i < nb; ++i)
+        if (__longlong_as_double((long long)bmax[(int64_t)b * nb + i]) >= frac * total) {
+            K = buckets[i];
+            break;
+        }
+    jobs[b].K = K;
+    if (k_out) k_out[j0 + b] = K;
+}
+
+// U[s] = window_sum over K for every start; per-template maximum (bit patterns)
+__global__ void __launch_bounds__(256) k_umax(const TapJob *__restrict__ jobs, const double *__restrict__ P,
+                                              int64_t n, unsigned long long *__restrict__ umax) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    unsigned long long bits = 0ull;
+    if (m < n) bits = (unsigned long long)__double_as_longlong(fmax(0.0, window_sum(P + (int64_t)b * (n + 1), n, m, jobs[b].K)));
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long other = __shfl_down_sync(0xffffffffu, bits, o);
         bits = other > bits ? other : bits;
     }
-    if ((threadIdx.x & 31) == 0) atomicMax(&emax[b], bits);
+    if ((threadIdx.x & 31) == 0) atomicMax(&umax[b], bits);
+}
+
+// the smallest start m whose U equals the maximum
+__global__ void __launch_bounds__(256) k_uargmax(const TapJob *__restrict__ jobs, const double *__restrict__ P,
+                                                 int64_t n, const unsigned long long *__restrict__ umax,
+                                                 unsigned long long *__restrict__ uarg) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (m >= n) return;
+    const double u = fmax(0.0, window_sum(P + (int64_t)b * (n + 1), n, m, jobs[b].K));
+    if ((unsigned long long)__double_as_longlong(u) == umax[b]) atomicMin(&uarg[b], (unsigned long long)m);
+}
+
+__device__ __forceinline__ double exact_energy(const double2 *__restrict__ gb, int64_t n, int64_t m, int K,
+                                               double alpha) {
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double w = tukey_w(k, K, alpha);
+        int64_t idx = m + k;
+        if (idx >= n) idx -= n;
+        const double2 v = gb[idx];
+        acc += (w * w) * (v.x * v.x + v.y * v.y);
+    }
+    return acc;
+}
+
+// bound[b] = E at the argmax of U (a lower bound on the maximum of E), one thread per template
+__global__ void k_bound(const TapJob *__restrict__ jobs, const double2 *__restrict__ g, int64_t n, double alpha,
+                        int nbt, const unsigned long long *__restrict__ uarg, double *__restrict__ bound) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbt) return;
+    const int64_t m0 = uarg[b] < (unsigned long long)n ? (int64_t)uarg[b] : 0;
+    bound[b] = exact_energy(g + (int64_t)b * n, n, m0, jobs[b].K, alpha);
+}
+
+// E[i] (i = s + n/2) exactly where U[s mod n] can reach the bound, -1 elsewhere; maximum.
+__global__ void __launch_bounds__(256) k_candidates(const TapJob *__restrict__ jobs, const double2 *__restrict__ g,
+                                                    const double *__restrict__ P, int64_t n, double alpha,
+                                                    const double *__restrict__ bound,
+                                                    double *__restrict__ E,
+                                                    unsigned long long *__restrict__ emax) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (i >= n) return;
+    const int K = jobs[b].K;
+    const double *Pb = P + (int64_t)b * (n + 1);
+    const double2 *gb = g + (int64_t)b * n;
+    // allowance for the rounding of the prefix sums against the direct sums
+    const double tau = bound[b] * (1.0 - 1e-9) - 1e-6 * Pb[n];
+    const int64_t m = (i - n / 2 + n) % n;
+    double e = -1.0;
+    if (window_sum(Pb, n, m, K) >= tau) {
+        e = exact_energy(gb, n, m, K, alpha);
+        atomicMax(&emax[b], (unsigned long long)__double_as_longlong(e));
+    }
+    E[(int64_t)b * n + i] = e;
 }
 
 __global__ void __launch_bounds__(256) k_lag_select(const TapJob *__restrict__ jobs,
@@ -315,18 +430,26 @@ __global__ void k_match_final(const double *__restrict__ part, int64_t nb, int32
 rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
                           const std::vector<PNParams> &refs, const std::vector<PNParams> &tmpl,
                           const std::vector<int32_t> &ref_of, const std::vector<int32_t> &K,
-                          int32_t k_stride, double alpha, float2 *taps, int32_t *lag,
-                          double *sigma, double *match, cudaStream_t s) {
+                          const std::vector<int32_t> &buckets, double energy_frac, int32_t k_stride,
+                          double alpha, float2 *taps, int32_t *k_out, int32_t *lag, double *sigma,
+                          double *match, cudaStream_t s) {
     const int64_t n = g.n;
     const int64_t J = (int64_t)tmpl.size(), R = (int64_t)refs.size();
-    int64_t B = std::max<int64_t>(1, ((int64_t)2 << 30) / (n * 56));
+    const bool bucketed = K.empty();
+    const int nbk = (int)buckets.size();
+    int64_t B = std::max<int64_t>(1, ((int64_t)2 << 30) / (n * 64));
     B = std::min<int64_t>(std::min<int64_t>(B, J), 4096);
     const int64_t nb_match = (n / 2 + 1 + 255) / 256;
-    // C_r rows (complex, n each) live after the per-batch scalars in ws[11]
-    const size_t off_lagkey = B * sizeof(unsigned long long);
-    const size_t off_rho = 2 * off_lagkey;
     int kmax = 0;
-    for (int64_t i = 0; i < J; ++i) kmax = std::max(kmax, K[i]);
+    if (bucketed)
+        for (int b : buckets) kmax = std::max(kmax, b);
+    else
+        for (int64_t i = 0; i < J; ++i) kmax = std::max(kmax, K[i]);
+    // per-batch scalars, taps in FP64, compact C_r rows and match partials share ws[11]
+    const size_t u64b = (size_t)B * sizeof(unsigned long long);
+    const size_t off_lagkey = u64b, off_umax = 2 * u64b, off_uarg = 3 * u64b, off_bmax = 4 * u64b;
+    const size_t off_bk = off_bmax + (size_t)B * std::max(nbk, 1) * sizeof(unsigned long long);
+    const size_t off_rho = (off_bk + (size_t)std::max(nbk, 1) * sizeof(int32_t) + 15) / 16 * 16;
     const size_t off_C = off_rho + (size_t)B * k_stride * sizeof(double2);
     const size_t off_part = off_C + (size_t)R * (2 * kmax - 1) * sizeof(double2);
     const size_t ws11 = off_part + (size_t)B * 4 * nb_match * sizeof(double);
@@ -335,16 +458,24 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
     RFD_TRY(ensure(ctx->ws[8], std::max(B, R) * n * sizeof(double2)));
     RFD_TRY(ensure(ctx->ws[9], std::max(B, R) * n * sizeof(double2)));
     RFD_TRY(ensure(ctx->ws[10], B * n * sizeof(double)));
+    RFD_TRY(ensure(ctx->ws[15], B * (n + 1) * sizeof(double)));
     RFD_TRY(ensure(ctx->ws[11], ws11));
     RFD_TRY(ensure(ctx->ws[0], R * sizeof(PNParams)));
     char *base11 = (char *)ctx->ws[11].p;
     unsigned long long *emax = (unsigned long long *)base11;
     unsigned long long *lagkey = (unsigned long long *)(base11 + off_lagkey);
+    unsigned long long *umax = (unsigned long long *)(base11 + off_umax);
+    unsigned long long *uarg = (unsigned long long *)(base11 + off_uarg);
+    unsigned long long *bmax = (unsigned long long *)(base11 + off_bmax);
+    int32_t *d_buckets = (int32_t *)(base11 + off_bk);
     double2 *rho64 = (double2 *)(base11 + off_rho);
     double2 *C = (double2 *)(base11 + off_C);
     double *part = (double *)(base11 + off_part);
     double2 *Gb = (double2 *)ctx->ws[7].p, *gb = (double2 *)ctx->ws[8].p, *tmp = (double2 *)ctx->ws[9].p;
     double *E = (double *)ctx->ws[10].p;
+    double *Pbuf = (double *)ctx->ws[15].p;
+    if (bucketed)
+        RFD_TRY_CUDA(cudaMemcpyAsync(d_buckets, buckets.data(), nbk * sizeof(int32_t), cudaMemcpyHostToDevice, s));
 
     // C_r[l] = sum_k 4 df |h_r|^2/S exp(+2 pi i k l / n): one inverse FFT per reference
     RFD_TRY_CUDA(cudaMemcpyAsync(ctx->ws[0].p, refs.data(), R * sizeof(PNParams),
@@ -359,15 +490,13 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
     std::vector<TapJob> jobs(B);
     for (int64_t j0 = 0; j0 < J; j0 += B) {
         const int64_t nbt = std::min<int64_t>(B, J - j0);
-        int kb = 0;
         for (int64_t b = 0; b < nbt; ++b) {
             TapJob &jb = jobs[b];
             jb = TapJob{};
             jb.tj = tmpl[j0 + b];
             jb.ref = ref_of[j0 + b];
             jb.tr = refs[jb.ref];
-            jb.K = K[j0 + b];
-            kb = std::max(kb, jb.K);
+            jb.K = bucketed ? kmax : K[j0 + b];      // bucketed: chosen on the device below
         }
         TapJob *dj = (TapJob *)ctx->ws[6].p;
         RFD_TRY_CUDA(cudaMemcpyAsync(dj, jobs.data(), nbt * sizeof(TapJob), cudaMemcpyHostToDevice, s));
@@ -377,10 +506,31 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
                                                                                n, g.k_lo, Gb);
         RFD_LAUNCH_CHECK();
         RFD_TRY(fft_c2c<double>(ctx, n, nbt, Gb, n, gb, n, tmp, true, s));
+        // energy prefix sums, optional K bucket, pruned exact lag search
+        k_energy_prefix<<<(unsigned)nbt, 1024, 0, s>>>(gb, n, Pbuf);
+        RFD_LAUNCH_CHECK();
+        if (bucketed) {
+            RFD_TRY_CUDA(cudaMemsetAsync(bmax, 0, nbt * nbk * sizeof(unsigned long long), s));
+            k_bucket_max<<<dim3((unsigned)(n / 256), (unsigned)nbt), 256, 0, s>>>(Pbuf, n, d_buckets, nbk, bmax);
+            RFD_LAUNCH_CHECK();
+            k_bucket_pick<<<(unsigned)((nbt + 127) / 128), 128, 0, s>>>(dj, (int)nbt, Pbuf, n, d_buckets, nbk,
+                                                                        energy_frac, bmax, (int32_t)j0, k_out);
+            RFD_LAUNCH_CHECK();
+        } else if (k_out) {
+            RFD_TRY_CUDA(cudaMemcpyAsync(k_out + j0, K.data() + j0, nbt * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        }
         RFD_TRY_CUDA(cudaMemsetAsync(emax, 0, nbt * sizeof(unsigned long long), s));
         RFD_TRY_CUDA(cudaMemsetAsync(lagkey, 0xff, nbt * sizeof(unsigned long long), s));
-        const size_t shm = (size_t)(kb + 256 + kb) * sizeof(double);
-        k_window_energy<<<dim3((unsigned)(n / 256), (unsigned)nbt), 256, shm, s>>>(dj, gb, n, alpha, E, emax);
+        RFD_TRY_CUDA(cudaMemsetAsync(umax, 0, nbt * sizeof(unsigned long long), s));
+        RFD_TRY_CUDA(cudaMemsetAsync(uarg, 0xff, nbt * sizeof(unsigned long long), s));
+        k_umax<<<dim3((unsigned)(n / 256), (unsigned)nbt), 256, 0, s>>>(dj, Pbuf, n, umax);
+        RFD_LAUNCH_CHECK();
+        k_uargmax<<<dim3((unsigned)(n / 256), (unsigned)nbt), 256, 0, s>>>(dj, Pbuf, n, umax, uarg);
+        RFD_LAUNCH_CHECK();
+        k_bound<<<(unsigned)((nbt + 127) / 128), 128, 0, s>>>(dj, gb, n, alpha, (int)nbt, uarg, (double *)umax);
+        RFD_LAUNCH_CHECK();
+        k_candidates<<<dim3((unsigned)(n / 256), (unsigned)nbt), 256, 0, s>>>(dj, gb, Pbuf, n, alpha,
+                                                                             (const double *)umax, E, emax);
         RFD_LAUNCH_CHECK();
         k_lag_select<<<dim3((unsigned)(n / 256), (unsigned)nbt), 256, 0, s>>>(dj, E, n, emax, lagkey);
         RFD_LAUNCH_CHECK();
@@ -388,7 +538,7 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
         k_place<<<(unsigned)nbt, 256, 0, s>>>(dj, gb, n, alpha, lagkey, (int32_t)j0, k_stride, rho64,
                                               taps, lag, match ? Gb : nullptr);
         RFD_LAUNCH_CHECK();
-        k_sigma_eff<<<(unsigned)nbt, 256, (size_t)kb * sizeof(double2), s>>>(dj, rho64, k_stride, C,
+        k_sigma_eff<<<(unsigned)nbt, 256, (size_t)kmax * sizeof(double2), s>>>(dj, rho64, k_stride, C,
                                                                            kmax, (int32_t)j0, sigma);
         RFD_LAUNCH_CHECK();
         if (match) {
