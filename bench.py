@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--n-tmpl", type=int, default=None, help="smaller bank (profiling cases only)")
     ap.add_argument("--n-ref", type=int, default=None, help="fewer references (profiling cases only)")
+    ap.add_argument("--no-graph", action="store_true", help="separate launches instead of one CUDA graph")
     return ap.parse_args()
 
 
@@ -215,12 +216,23 @@ def run_reference(args):
 
 # ------------------------------------------------------------------------------- GPU arm
 class GpuSearch:
-    def __init__(self, cfg, bank, data, precision, device):
+    """Set-up (templates, taps, autotuned plan) and the per-segment search as one CUDA graph."""
+
+    def __init__(self, cfg, bank, data, precision, device, use_graph=True, autotune_cache=None):
         import torch
         import paper_2601_18835_gb300 as rfd
+        from paper_2601_18835_gb300 import autotune
         self.torch, self.rfd = torch, rfd
         self.cfg, self.bank = cfg, bank
         self.prec = precision
+        self.stream = torch.cuda.Stream()
+        self.use_graph = use_graph
+        with torch.cuda.stream(self.stream):
+            self._setup(cfg, bank, data, precision, device, autotune, autotune_cache)
+        torch.cuda.synchronize()
+
+    def _setup(self, cfg, bank, data, precision, device, autotune, autotune_cache):
+        torch, rfd = self.torch, self.rfd
         self.ctx = rfd.Context(device)
         self.grid = rfd.grid(cfg.fs, cfg.n, cfg.f_low, cfg.pn_flags)
         self.psd = torch.from_numpy(data.psd).cuda()
@@ -228,27 +240,40 @@ class GpuSearch:
         self.d_host = torch.from_numpy(d64).pin_memory()
         self.d = self.d_host.cuda()
         J = bank.n_tmpl
-        self.K = np.full(J, cfg.k, dtype=np.int32)
-        self.halo = cfg.k - 1
-        self.taps = torch.zeros((J, cfg.k), dtype=torch.complex64, device="cuda")
+        bucketed = cfg.k == 0
+        k_stride = max(cfg.k_buckets) if bucketed else cfg.k
+        self.taps = torch.zeros((J, k_stride), dtype=torch.complex64, device="cuda")
         self.lag = torch.zeros(J, dtype=torch.int32, device="cuda")
         self.sig = torch.zeros(J, dtype=torch.float64, device="cuda")
         self.match = torch.zeros(J, dtype=torch.float64, device="cuda")
+        kout = torch.zeros(J, dtype=torch.int32, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rfd.make_taps(self.ctx, self.grid, self.psd, bank.ref_params(), bank.params(), bank.ref_of_tmpl, self.K,
-                      cfg.k, cfg.tukey_alpha, self.taps, self.lag, self.sig, self.match)
+        rfd.make_taps(self.ctx, self.grid, self.psd, bank.ref_params(), bank.params(), bank.ref_of_tmpl,
+                      None if bucketed else np.full(J, cfg.k, dtype=np.int32), k_stride, cfg.tukey_alpha,
+                      self.taps, self.lag, self.sig, self.match, stream=self.stream,
+                      buckets=list(cfg.k_buckets) if bucketed else None, k_out=kout)
         torch.cuda.synchronize()
         self.make_taps_s = time.perf_counter() - t0
+        self.K = kout.cpu().numpy().astype(np.int32)
+        kmax = int(self.K.max())
+        self.halo = 16 * ((kmax + 15) // 16) - 1
         # reference templates: set-up work (the references do not change between segments)
         self.href = torch.zeros((bank.n_ref, cfg.n // 2 + 1), dtype=torch.complex64, device="cuda")
-        rfd.gen_templates(self.ctx, self.grid, bank.ref_params(), self.href)
+        rfd.gen_templates(self.ctx, self.grid, bank.ref_params(), self.href, stream=self.stream)
         self.ld = rfd.qref_ld(cfg.n, self.halo)
         self.q = torch.zeros(bank.n_ref * self.ld * 8, dtype=torch.uint8, device="cuda")
         self.e = torch.zeros(bank.n_ref, dtype=torch.int32, device="cuda")
+        rfd.filter_reference(self.ctx, self.grid, self.d, self.psd, self.href, self.halo, precision, self.q,
+                             self.e, stream=self.stream)
+        self.options, self.tuning = {}, None
+        if precision != 0:
+            self.options, self.tuning = autotune.autotune(
+                self.ctx, self.grid, bank.n_ref, bank.ref_of_tmpl, self.K, precision, cfg.window, cfg.threshold,
+                self.halo, self.taps, k_stride, self.lag, self.sig, self.q, self.e, cache_path=autotune_cache)
         self.plan = rfd.Plan(self.ctx, self.grid, bank.n_ref, bank.ref_of_tmpl, self.K, precision, cfg.window,
-                             cfg.threshold, self.halo)
-        self.plan.set_taps(self.taps, cfg.k, self.lag, self.sig)
+                             cfg.threshold, self.halo, options=self.options)
+        self.plan.set_taps(self.taps, k_stride, self.lag, self.sig, stream=self.stream)
         self.ctx.trim()          # drop the FP64 tap-design workspaces
         self.cand_cap = 1 << 22
         self.cand = torch.zeros(self.cand_cap * 24, dtype=torch.uint8, device="cuda")
@@ -257,34 +282,57 @@ class GpuSearch:
         self.trig = torch.zeros(self.trig_cap * 20, dtype=torch.uint8, device="cuda")
         self.trig_host = torch.zeros(self.trig_cap * 20, dtype=torch.uint8).pin_memory()
         self.flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        self.stream = torch.cuda.current_stream()
+        self.search = None
+        if self.use_graph:
+            self.search = rfd.Search(self.plan, self.d, self.psd, self.href, self.q, self.e, self.cand, self.cnt,
+                                     self.trig, self.stream)
+
+    def alg_flops(self):
+        return 8.0 * float(self.K.astype(np.float64).sum()) * self.cfg.n
 
     def flush_l2(self):
-        self.flush_buf.random_(0, 255)
+        with self.torch.cuda.stream(self.stream):
+            self.flush_buf.random_(0, 255)
 
     def step(self, ev=None):
-        rfd = self.rfd
-        if ev:
-            ev[0].record()
-        rfd.filter_reference(self.ctx, self.grid, self.d, self.psd, self.href, self.halo, self.prec, self.q, self.e)
-        if ev:
-            ev[1].record()
-        self.plan.ratio_filter_batch(self.q, self.e, self.cand, self.cnt)
-        if ev:
-            ev[2].record()
-        nt = rfd.find_triggers(self.ctx, self.bank.n_tmpl, self.cand, self.cnt, self.trig)
-        if ev:
-            ev[3].record()
-        return nt
+        """One segment; ev = (start, end) events recorded on the search stream around it.
+        Returns (triggers, ratio-filter kernel ms)."""
+        torch, rfd = self.torch, self.rfd
+        with torch.cuda.stream(self.stream):
+            if ev:
+                ev[0].record(self.stream)
+            if self.search is not None:
+                nt = self.search.run()
+                kms = self.search.filter_ms()
+                self.last_step_ms = self.search.step_ms()
+            else:
+                rfd.filter_reference(self.ctx, self.grid, self.d, self.psd, self.href, self.halo, self.prec, self.q,
+                                     self.e, stream=self.stream)
+                k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                k0.record(self.stream)
+                self.plan.ratio_filter_batch(self.q, self.e, self.cand, self.cnt, stream=self.stream)
+                k1.record(self.stream)
+                nt = rfd.find_triggers(self.ctx, self.bank.n_tmpl, self.cand, self.cnt, self.trig, stream=self.stream)
+                kms = k0.elapsed_time(k1)
+            if ev:
+                ev[1].record(self.stream)
+                if self.search is None:
+                    ev[1].synchronize()
+                    self.last_step_ms = ev[0].elapsed_time(ev[1])
+        return nt, kms
 
     def step_e2e(self):
         """Through host buffers: H2D of the data spectrum, the step, D2H of the triggers."""
-        self.d.copy_(self.d_host, non_blocking=True)
-        nt = self.step()
-        self.trig_host[: nt * 20].copy_(self.trig[: nt * 20], non_blocking=False)
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            self.d.copy_(self.d_host, non_blocking=True)
+            nt, _ = self.step()
+            self.trig_host[: nt * 20].copy_(self.trig[: nt * 20], non_blocking=False)
         return nt
 
     def close(self):
+        if self.search is not None:
+            self.search.close()
         self.plan.close()
         self.ctx.close()
 
@@ -344,7 +392,8 @@ def run_ours(args):
     precision_name = args.precision or "fp16x3"
     prec = PREC[precision_name]
     cfg, bank, data = workload_for_rank(args.config, rank, args.n_tmpl, args.n_ref)
-    s = GpuSearch(cfg, bank, data, prec, local)
+    tune_cache = os.path.join(ROOT, "paper_2601_18835_gb300", "_build", "autotune.json")
+    s = GpuSearch(cfg, bank, data, prec, local, use_graph=not args.no_graph, autotune_cache=tune_cache)
     J, dur = bank.n_tmpl, cfg.duration
 
     def barrier():
@@ -355,7 +404,8 @@ def run_ours(args):
         s.flush_l2()
         s.step()
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    kernel_ms = []
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.5)
@@ -365,18 +415,18 @@ def run_ours(args):
     torch.cuda.profiler.start()      # ncu --profile-from-start off sees only the timed steps
     w0 = time.perf_counter()
     ntrig = 0
+    step_ms = []
     for i in range(args.steps):
         s.flush_l2()
-        ntrig = s.step(evs[i])
+        ntrig, kms = s.step(evs[i])
+        kernel_ms.append(kms)
+        step_ms.append(s.last_step_ms)      # device time of the step (graph's first to last node)
     torch.cuda.synchronize()
     w1 = time.perf_counter()
     torch.cuda.profiler.stop()
     barrier()
     launches = rfd.kernel_launches() - l0
     clk = clocks.stop(w0, w1)
-    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
-    filt_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    ref_ms = [e[0].elapsed_time(e[1]) for e in evs]
     ms = sum(step_ms) / len(step_ms)
     t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if ws > 1:
@@ -403,8 +453,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel: the ratio-filter contraction
     peaks, peak_kind = measured_peaks()
-    filt_s = sum(filt_ms) / len(filt_ms) / 1e3
-    alg_flops = 8.0 * cfg.k * J * cfg.n
+    filt_s = sum(kernel_ms) / len(kernel_ms) / 1e3
+    alg_flops = s.alg_flops()
     if prec == 0:
         kernel, src = "k_fir32", "fir32.cu"
         # FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
@@ -414,7 +464,7 @@ def run_ours(args):
     else:
         kernel, src = "k_rf_tc", "rf_tc.cu"
         peak_tf = peaks["bf16_tflops_sustained"]
-        exec_flops = getattr(rfd, "executed_flops", lambda c: 3 * alg_flops)(cfg)
+        exec_flops = s.plan.executed_flops()
         roof = {"bound": "tensor", "achieved": alg_flops / filt_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
                 "peak_source": "%s bf16 dense sustained (fp16 has the same dense rate)" % peak_kind,
                 "executed_tflops": exec_flops / filt_s / 1e12,
@@ -428,17 +478,17 @@ def run_ours(args):
     comparisons = {}
     if not args.no_compare and rank == 0:
         if prec != 0:
-            s32 = GpuSearch(cfg, bank, data, 0, local)
+            s32 = GpuSearch(cfg, bank, data, 0, local, use_graph=True)
             for _ in range(2):
                 s32.step()
             torch.cuda.synchronize()
             tt = []
             for _ in range(3):
                 s32.flush_l2()
-                e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
                 s32.step(e)
                 torch.cuda.synchronize()
-                tt.append(e[0].elapsed_time(e[3]))
+                tt.append(s32.last_step_ms)
             comparisons["fp32_fir_step"] = {"value": J * dur / (sum(tt) / len(tt) / 1e3), "unit": UNIT,
                                             "ms_per_step": sum(tt) / len(tt)}
             s32.close()
@@ -466,7 +516,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": precision_name, "data": "synthetic",
-        "config": {"workload": cfg.name, "n_tmpl": J, "n_ref": bank.n_ref, "k": cfg.k, "n": cfg.n, "fs": cfg.fs,
+        "config": {"workload": cfg.name, "n_tmpl": J, "n_ref": bank.n_ref,
+                   "k": cfg.k if cfg.k else {"buckets": list(cfg.k_buckets),
+                                             "histogram": {int(b): int((s.K == b).sum()) for b in cfg.k_buckets}},
+                   "n": cfg.n, "fs": cfg.fs,
                    "segment_s": dur, "window": cfg.window, "threshold": cfg.threshold,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if ws > 1 else "single"},
         "clocks": clk,
@@ -476,8 +529,10 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "comparisons": comparisons,
-        "breakdown_ms": {"filter_reference": sum(ref_ms) / len(ref_ms), "ratio_filter_batch": filt_s * 1e3,
-                         "find_triggers": ms - sum(ref_ms) / len(ref_ms) - filt_s * 1e3},
+        "breakdown_ms": {"ratio_filter_batch": filt_s * 1e3, "rest_of_step": ms - filt_s * 1e3},
+        "graph": {"used": s.search is not None,
+                  "kernels_per_step": s.search.kernels_per_run if s.search is not None else None},
+        "autotune": {"options": s.options, "candidates_ms": [c["ms"] for c in (s.tuning or {}).get("candidates", [])]},
         "setup": {"make_taps_s": s.make_taps_s, "taps_match_ge_0p99": float(np.mean(match >= 0.99)),
                   "taps_match_median": float(np.median(match))},
         "triggers_per_step": int(ntrig),

@@ -192,6 +192,24 @@ rfd_status rfd_plan_create(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, in
                            rfd_plan **out);
 void rfd_plan_destroy(rfd_plan *plan);
 
+/* Tile choices of the tensor-core path (what the autotuner varies). */
+typedef struct {
+    int32_t tile_nt[3];   /* templates per tile (multiple of 16) for K rounded to 16 in (0,128],
+                             (128,256], (256,512]: at most 128, 64, 32 (the taps image of a tile,
+                             3 x templates x K x hi/lo, stays within 192 KB of shared memory) */
+    int32_t mix_k;        /* 1: a tile may hold templates whose K differ (padded to the largest);
+                             0: tiles also split where the number of 16-tap steps changes */
+    int32_t grid_ctas;    /* persistent CTAs of the tensor-core kernel, 0 = one per SM */
+    int32_t reserved[3];  /* must be 0 */
+} rfd_plan_options;
+/* Fills the defaults: tile_nt = {128, 64, 32}, mix_k = 1, grid_ctas = 0. */
+void rfd_plan_options_default(rfd_plan_options *options);
+/* rfd_plan_create with explicit tile choices (NULL = defaults). */
+rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
+                              const int32_t *ref_of_tmpl_host, const int32_t *k_host,
+                              int32_t precision, int32_t window, float threshold, int32_t halo,
+                              const rfd_plan_options *options, rfd_plan **out);
+
 /* Packs the taps from rfd_make_taps into the plan's own layout (reversed, scaled, split
  * into hi/lo parts for the tensor-core path) and stores 1/sigma_eff and the lags.
  * taps_dev complex64 [n_tmpl][k_stride]; lag_dev int32 [n_tmpl]; sigma_dev float64 [n_tmpl].
@@ -233,6 +251,32 @@ rfd_status rfd_find_triggers(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *
                              const int64_t *cand_count_dev, int64_t cand_capacity,
                              rfd_trigger *trig_dev, int64_t trig_capacity,
                              int64_t *n_trig_host, void *stream);
+
+/* ------------------------------------------------------------------ whole segment as one graph
+ * One data segment through filter_reference, ratio_filter_batch and the trigger merge,
+ * captured once into a CUDA graph and replayed per segment (the per-segment loop of Table II
+ * with one launch).  All buffers (as described for the three calls) are bound at creation;
+ * to search the next segment, write its spectrum into dtilde_dev and run again.
+ * rfd_search_create runs the step once outside the capture (sizing every workspace), then
+ * captures it on `stream`, which must be a created stream (not the legacy default stream),
+ * and synchronises.  rfd_search_run launches the graph on `stream`, waits for it, and returns
+ * the trigger count in *n_trig_host with the status rules of rfd_find_triggers.  The plan and
+ * the buffers must outlive the search; runs of one search must not overlap. */
+typedef struct rfd_search rfd_search;
+rfd_status rfd_search_create(rfd_plan *plan, const void *dtilde_dev, const double *psd_dev,
+                             const void *href_dev, void *qref_dev, int32_t *qscale_dev,
+                             rfd_candidate *cand_dev, int64_t cand_capacity,
+                             int64_t *cand_count_dev, rfd_trigger *trig_dev,
+                             int64_t trig_capacity, void *stream, rfd_search **out);
+rfd_status rfd_search_run(rfd_search *search, void *stream, int64_t *n_trig_host);
+/* Kernels one run launches (they are counted in rfd_kernel_launches as they are replayed). */
+int64_t rfd_search_kernels_per_run(const rfd_search *search);
+/* Device time (ms) of the ratio-filter kernel in the last completed run (CUDA events recorded
+ * inside the graph around it), or -1. */
+double rfd_search_filter_ms(const rfd_search *search);
+/* Device time (ms) of the whole last completed run, first to last node of the graph, or -1. */
+double rfd_search_step_ms(const rfd_search *search);
+void rfd_search_destroy(rfd_search *search);
 
 /* ------------------------------------------------------------------ find_triggers, no allocation
  * The same merge as rfd_find_triggers, for callers that cannot allocate device memory while

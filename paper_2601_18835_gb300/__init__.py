@@ -19,7 +19,7 @@ from . import _native
 from ._native import (CANDIDATE_DTYPE, PN_SO, PN_TIDAL, PREC_BF16X3, PREC_FP16X3, PREC_FP32,  # noqa: F401
                       TRIGGER_DTYPE, RfdError, check)
 
-__all__ = ["Context", "Plan", "grid", "gen_templates", "make_taps", "filter_reference",
+__all__ = ["Context", "Plan", "Search", "grid", "gen_templates", "make_taps", "filter_reference",
            "find_triggers", "find_triggers_noalloc", "findchirp", "ifft_c2c", "qref_ld", "candidates_to_numpy",
            "triggers_to_numpy", "CANDIDATE_DTYPE", "TRIGGER_DTYPE"]
 
@@ -133,13 +133,26 @@ def filter_reference(ctx, g, dtilde, psd, href, halo, precision, qref, qscale, s
 class Plan:
     """One bank's ratio-filter schedule (templates tiled per reference) and packed taps."""
 
-    def __init__(self, ctx, g, n_ref, ref_of, k, precision, window, threshold, halo):
+    def __init__(self, ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, options=None):
+        """options: dict with any of tile_nt (3 ints), mix_k (0/1), grid_ctas (int)."""
         ro, rop = _i32_host(ref_of)
         kk, kp = _i32_host(k)
         h = ctypes.c_void_p()
-        check(_lib().rfd_plan_create(ctx.handle, ctypes.byref(g), int(n_ref), len(ro), rop, kp,
-                                     int(precision), int(window), float(threshold), int(halo),
-                                     ctypes.byref(h)))
+        opt = None
+        if options:
+            opt = _native.PlanOptions()
+            _lib().rfd_plan_options_default(ctypes.byref(opt))
+            if "tile_nt" in options:
+                for i, v in enumerate(options["tile_nt"]):
+                    opt.tile_nt[i] = int(v)
+            if "mix_k" in options:
+                opt.mix_k = int(options["mix_k"])
+            if "grid_ctas" in options:
+                opt.grid_ctas = int(options["grid_ctas"])
+        check(_lib().rfd_plan_create_ex(ctx.handle, ctypes.byref(g), int(n_ref), len(ro), rop, kp,
+                                        int(precision), int(window), float(threshold), int(halo),
+                                        ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))
+        self.options = dict(options or {})
         self.handle = h
         self.ctx = ctx
         self.n_tmpl = len(ro)
@@ -160,6 +173,52 @@ class Plan:
     def close(self):
         if self.handle:
             _lib().rfd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Search:
+    """One segment through filter_reference, ratio_filter_batch and the trigger merge, captured
+    once into a CUDA graph (rfd_search_*); buffers are bound at creation.  `stream` must be a
+    torch.cuda.Stream other than the default stream."""
+
+    def __init__(self, plan, dtilde, psd, href, qref, qscale, cand, cand_count, trig, stream):
+        cap = cand.numel() * cand.element_size() // CANDIDATE_DTYPE.itemsize
+        tcap = trig.numel() * trig.element_size() // TRIGGER_DTYPE.itemsize
+        h = ctypes.c_void_p()
+        self.stream = stream
+        check(_lib().rfd_search_create(plan.handle, _ptr(dtilde), _ptr(psd), _ptr(href), _ptr(qref), _ptr(qscale),
+                                       _ptr(cand), int(cap), _ptr(cand_count), _ptr(trig), int(tcap),
+                                       _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self.plan = plan
+
+    @property
+    def kernels_per_run(self):
+        return int(_lib().rfd_search_kernels_per_run(self.handle))
+
+    def step_ms(self):
+        """Device time of the whole last run (events at the graph's first and last node)."""
+        return float(_lib().rfd_search_step_ms(self.handle))
+
+    def filter_ms(self):
+        """Device time of the ratio-filter kernel in the last run (events inside the graph)."""
+        return float(_lib().rfd_search_filter_ms(self.handle))
+
+    def run(self):
+        """Replays the graph, waits, returns the number of triggers."""
+        n = ctypes.c_int64(0)
+        check(_lib().rfd_search_run(self.handle, _stream(self.stream), ctypes.byref(n)), needed=n.value)
+        return int(n.value)
+
+    def close(self):
+        if self.handle:
+            _lib().rfd_search_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -33,6 +33,11 @@ class Grid(ctypes.Structure):
                 ("pn_flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("tile_nt", ctypes.c_int32 * 3), ("mix_k", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
 class Params(ctypes.Structure):
     _fields_ = [("m1", ctypes.c_double), ("m2", ctypes.c_double), ("chi1", ctypes.c_double),
                 ("chi2", ctypes.c_double), ("lambda_tilde", ctypes.c_double)]
@@ -68,6 +73,16 @@ SIGNATURES = {
     "rfd_plan_destroy": (None, [_vp]),
     "rfd_plan_set_taps": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
     "rfd_plan_executed_flops": (_dbl, [_vp]),
+    "rfd_plan_options_default": (None, [_vp]),
+    "rfd_plan_create_ex": (_i32, [_vp, ctypes.POINTER(Grid), _i32, _i32, _vp, _vp, _i32, _i32, _flt, _i32, _vp,
+                                  ctypes.POINTER(_vp)]),
+    "rfd_search_create": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _i64, _vp,
+                                 ctypes.POINTER(_vp)]),
+    "rfd_search_run": (_i32, [_vp, _vp, ctypes.POINTER(_i64)]),
+    "rfd_search_kernels_per_run": (_i64, [_vp]),
+    "rfd_search_filter_ms": (_dbl, [_vp]),
+    "rfd_search_step_ms": (_dbl, [_vp]),
+    "rfd_search_destroy": (None, [_vp]),
     "rfd_ratio_filter_batch": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "rfd_find_triggers": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(_i64), _vp]),
     "rfd_find_triggers_noalloc": (_i32, [_i32, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(_i64), _vp]),

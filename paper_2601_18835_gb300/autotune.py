@@ -1,0 +1,82 @@
+"""Autotuner for the tensor-core ratio filter: picks the plan's tile choices by timing them.
+
+The choices (rfd_plan_options): templates per tile for each K class, whether a tile may mix
+templates of different K (padding the short ones) or must split where K changes, and the
+number of persistent CTAs.  Each candidate plan is built through the C ABI, given the bank's
+taps, and timed on the q_ref buffer with CUDA events; the fastest wins.  Results are cached
+in a JSON file keyed by the workload's signature (grid, precision, the (reference, K)
+histogram, the device), so a bank is tuned once.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import torch
+
+from . import Plan, CANDIDATE_DTYPE
+
+DEFAULT_CANDIDATES = [
+    {"mix_k": 1},
+    {"mix_k": 0},
+    {"mix_k": 1, "tile_nt": [64, 64, 32]},
+    {"mix_k": 0, "tile_nt": [64, 64, 32]},
+    {"mix_k": 1, "grid_ctas": 0},
+]
+
+
+def signature(g, precision, ref_of, k):
+    ref_of = np.asarray(ref_of, dtype=np.int64)
+    k = np.asarray(k, dtype=np.int64)
+    pairs, counts = np.unique(np.stack([ref_of, (k + 15) // 16]), axis=1, return_counts=True)
+    h = hashlib.sha256()
+    h.update(repr((float(g.fs), int(g.n), float(g.f_low), int(g.pn_flags), int(precision))).encode())
+    h.update(pairs.tobytes())
+    h.update(counts.tobytes())
+    h.update(torch.cuda.get_device_name().encode())
+    return h.hexdigest()[:24]
+
+
+def _time_plan(plan, qref, qscale, cand, cnt, reps):
+    for _ in range(2):
+        plan.ratio_filter_batch(qref, qscale, cand, cnt)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.ratio_filter_batch(qref, qscale, cand, cnt)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def autotune(ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, taps, k_stride, lag, sigma,
+             qref, qscale, cache_path=None, candidates=None, reps=3):
+    """Returns (options, report): the fastest candidate's options and every candidate's time (ms)."""
+    sig = signature(g, precision, ref_of, k)
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as fh:
+            cache = json.load(fh)
+        if sig in cache:
+            return cache[sig]["options"], cache[sig]
+    cand = torch.zeros((1 << 22) * CANDIDATE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    report = []
+    for opts in (candidates or DEFAULT_CANDIDATES):
+        plan = Plan(ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, options=opts)
+        plan.set_taps(taps, k_stride, lag, sigma)
+        ms = _time_plan(plan, qref, qscale, cand, cnt, reps)
+        report.append({"options": opts, "ms": ms, "executed_tflop": plan.executed_flops() / 1e12})
+        plan.close()
+    best = min(report, key=lambda r: r["ms"])
+    entry = {"options": best["options"], "ms": best["ms"], "candidates": report}
+    if cache_path:
+        cache[sig] = entry
+        d = os.path.dirname(os.path.abspath(cache_path))
+        os.makedirs(d, exist_ok=True)
+        with open(cache_path, "w") as fh:
+            json.dump(cache, fh, indent=1)
+    return best["options"], entry

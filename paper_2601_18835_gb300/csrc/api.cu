@@ -35,9 +35,12 @@ int tc_rows_per_item();
 // most 128 templates (64 once its K exceeds 128, 32 once it exceeds 256: the taps image,
 // 3 NT rows x K taps x hi/lo, stays within 192 KB of shared memory); NT is the tile's count
 // rounded up to 16.  Item ranges per CTA balance the MMA work.
-static int32_t tc_nt_cap(int32_t kpad) { return kpad <= 128 ? 128 : (kpad <= 256 ? 64 : 32); }
+static int32_t tc_nt_cap(const rfd_plan_options &o, int32_t kpad) {
+    return kpad <= 128 ? o.tile_nt[0] : (kpad <= 256 ? o.tile_nt[1] : o.tile_nt[2]);
+}
 
-static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &order, int num_sms) {
+static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &order, int num_sms,
+                                const rfd_plan_options &opt) {
     const int64_t n_tt = p->grid.n / tc_rows_per_item();
     int64_t taps_off = 0;
     int32_t kpad_max = 0;
@@ -50,7 +53,9 @@ static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &order, 
         t.first = (int32_t)p->perm.size();
         while (i < order.size() && p->ref_of[order[i]] == r) {
             const int32_t kt = std::max(t.k_tile, p->k_of[order[i]]);
-            if (t.count + 1 > tc_nt_cap(16 * ((kt + 15) / 16))) break;
+            if (t.count + 1 > tc_nt_cap(opt, 16 * ((kt + 15) / 16))) break;
+            // without mixing, a tile ends where the 16-tap step count changes
+            if (!opt.mix_k && t.count > 0 && (kt + 15) / 16 != (t.k_tile + 15) / 16) break;
             t.k_tile = kt;
             ++t.count;
             p->perm.push_back(order[i]);
@@ -82,7 +87,8 @@ static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &order, 
         cost[t] = (double)p->tc_tiles[t].nk16 * 6.0 + 2.0;   // MMAs cost the same for any N <= 256
         prefix[t + 1] = prefix[t] + cost[t] * n_tt;
     }
-    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(num_sms, total_items));
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(opt.grid_ctas > 0 ? opt.grid_ctas : num_sms,
+                                                           total_items));
     std::vector<int64_t> ranges(G + 1, 0);
     ranges[G] = total_items;
     int64_t t = 0;
@@ -108,6 +114,8 @@ std::atomic<int64_t> g_launches{0};
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -336,6 +344,34 @@ rfd_status rfd_filter_reference(rfd_ctx *ctx, const rfd_grid *grid, const void *
 rfd_status rfd_plan_create(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
                            const int32_t *ref_of_tmpl_host, const int32_t *k_host, int32_t precision,
                            int32_t window, float threshold, int32_t halo, rfd_plan **out) {
+    return rfd_plan_create_ex(ctx, grid, n_ref, n_tmpl, ref_of_tmpl_host, k_host, precision, window, threshold,
+                              halo, nullptr, out);
+}
+
+void rfd_plan_options_default(rfd_plan_options *o) {
+    if (!o) return;
+    *o = rfd_plan_options{};
+    o->tile_nt[0] = 128;
+    o->tile_nt[1] = 64;
+    o->tile_nt[2] = 32;
+    o->mix_k = 1;
+    o->grid_ctas = 0;
+}
+
+rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
+                              const int32_t *ref_of_tmpl_host, const int32_t *k_host, int32_t precision,
+                              int32_t window, float threshold, int32_t halo, const rfd_plan_options *options,
+                              rfd_plan **out) {
+    rfd_plan_options opt;
+    rfd_plan_options_default(&opt);
+    if (options) opt = *options;
+    {
+        static const int32_t cap[3] = {128, 64, 32};
+        for (int c = 0; c < 3; ++c)
+            RFD_REQUIRE(opt.tile_nt[c] >= 16 && opt.tile_nt[c] <= cap[c] && opt.tile_nt[c] % 16 == 0, RFD_ERR_ARG,
+                        "tile_nt[%d]=%d must be a multiple of 16 in [16, %d]", c, opt.tile_nt[c], cap[c]);
+        RFD_REQUIRE(opt.grid_ctas >= 0, RFD_ERR_ARG, "grid_ctas must be >= 0");
+    }
     RFD_REQUIRE(ctx && out, RFD_ERR_ARG, "NULL ctx or out");
     *out = nullptr;
     Grid g;
@@ -378,7 +414,7 @@ rfd_status rfd_plan_create(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, in
         return p->k_of[a] < p->k_of[b];
     });
     if (precision != RFD_PREC_FP32) {
-        rfd_status st = plan_tc_tiles(p, order, ctx->num_sms);
+        rfd_status st = plan_tc_tiles(p, order, ctx->num_sms, opt);
         if (st == RFD_OK) {
             do {
                 if ((st = ensure(p->d_perm, p->n_slots * sizeof(int32_t))) != RFD_OK) break;

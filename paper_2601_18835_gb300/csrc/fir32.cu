@@ -85,7 +85,12 @@ rfd_status fir32_launch(const rfd_plan *plan, const float2 *q, rfd_candidate *ca
                         int64_t *count, cudaStream_t s) {
     const int64_t n = plan->grid.n;
     const size_t shm = (size_t)(kTT + plan->k_max - 1 + kJT * plan->k_max) * sizeof(float2);
-    RFD_TRY_CUDA(cudaFuncSetAttribute(k_fir32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    static size_t smem_set[64] = {};
+    const int dev = plan->ctx->device < 64 ? plan->ctx->device : 63;
+    if (shm > smem_set[dev]) {
+        RFD_TRY_CUDA(cudaFuncSetAttribute(k_fir32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        smem_set[dev] = shm;
+    }
     const unsigned ntiles = (unsigned)plan->tiles.size();
     for (unsigned t0 = 0; t0 < ntiles; t0 += 65535) {
         dim3 grid((unsigned)(n / kTT), std::min(65535u, ntiles - t0));

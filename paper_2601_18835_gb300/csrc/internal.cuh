@@ -22,6 +22,7 @@ void set_error(const char *fmt, ...);
     do {                                                                                     \
         cudaError_t e_ = (expr);                                                             \
         if (e_ != cudaSuccess) {                                                             \
+            (void)cudaGetLastError(); /* a failed call leaves no error for the next check */ \
             ::rfd::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
                              __LINE__);                                                      \
             return RFD_ERR_CUDA;                                                             \
@@ -104,6 +105,17 @@ rfd_status fft_c2c(rfd_ctx *ctx, int64_t n, int64_t batch, const typename Cplx<T
                    typename Cplx<T>::type *tmp, bool inverse, cudaStream_t s);
 
 // ------------------------------------------------------------------ triggers (triggers.cu)
+struct TrigReadback {
+    int64_t count;    // candidates produced (bit 62: a filtering kernel timed out)
+    int64_t total;    // triggers
+    int32_t bad;      // candidates naming a template out of range
+    int32_t pad;
+};
+rfd_status find_triggers_enqueue(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand,
+                                 const int64_t *cand_count, int64_t cap, rfd_trigger *trig,
+                                 int64_t trig_cap, TrigReadback *host, cudaStream_t s);
+rfd_status find_triggers_check(const TrigReadback &h, int32_t n_tmpl, int64_t cap, int64_t trig_cap,
+                               int64_t *n_trig_host);
 rfd_status find_triggers_impl(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand,
                               const int64_t *cand_count, int64_t cap, rfd_trigger *trig,
                               int64_t trig_cap, int64_t *n_trig_host, cudaStream_t s);

@@ -469,13 +469,22 @@ rfd_status tc_launch(const rfd_plan *plan, const void *q, const int32_t *qscale,
     // at least 120 KB so that exactly one CTA (and one 512-column TMEM allocation) fits per SM
     const size_t shm = std::max<size_t>(tc_smem_bytes(a.taps_cap, a.win), 120 * 1024);
     const unsigned grid = (unsigned)plan->tc_grid;
-    if (plan->precision == RFD_PREC_FP16X3) {
-        RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        k_rf_tc<0><<<grid, kThreads, shm, s>>>(a);
-    } else {
-        RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-        k_rf_tc<1><<<grid, kThreads, shm, s>>>(a);
+    // the attribute is set once per device and size, so that launches inside a stream capture
+    // make no other runtime calls
+    static size_t smem_set[64][2] = {};
+    const int dev = plan->ctx->device < 64 ? plan->ctx->device : 63;
+    const int bf = plan->precision == RFD_PREC_FP16X3 ? 0 : 1;
+    if (shm > smem_set[dev][bf]) {
+        if (bf == 0)
+            RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        else
+            RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        smem_set[dev][bf] = shm;
     }
+    if (bf == 0)
+        k_rf_tc<0><<<grid, kThreads, shm, s>>>(a);
+    else
+        k_rf_tc<1><<<grid, kThreads, shm, s>>>(a);
     RFD_LAUNCH_CHECK();
     return RFD_OK;
 }

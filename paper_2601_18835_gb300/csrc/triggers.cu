@@ -114,9 +114,11 @@ __global__ void k_write(const rfd_candidate *__restrict__ bucket, const int64_t 
 }  // namespace
 
 // Scratch: ctx->ws[12] holds the int32 / int64 arrays, ctx->ws[13] the bucketed candidates.
-rfd_status find_triggers_impl(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand,
-                              const int64_t *cand_count, int64_t cap, rfd_trigger *trig,
-                              int64_t trig_cap, int64_t *n_trig_host, cudaStream_t s) {
+// Enqueues the six kernels and the read-back of (candidate count, trigger total, bad count)
+// into `host` (pinned memory when the stream is being captured into a graph).
+rfd_status find_triggers_enqueue(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand,
+                                 const int64_t *cand_count, int64_t cap, rfd_trigger *trig,
+                                 int64_t trig_cap, TrigReadback *host, cudaStream_t s) {
     const size_t J = (size_t)n_tmpl;
     // layout: cnt[J] cur[J] ntrig[J] bad[1] (int32, padded) | off[J+1] toff[J+1] (int64)
     const size_t i32_bytes = ((3 * J + 1) * sizeof(int32_t) + 15) / 16 * 16;
@@ -142,29 +144,39 @@ rfd_status find_triggers_impl(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate 
     RFD_LAUNCH_CHECK();
     k_write<<<gj, 256, 0, s>>>(bucket, off, toff, n_tmpl, trig_cap, trig);
     RFD_LAUNCH_CHECK();
-    int64_t host[3] = {0, 0, 0};
-    int32_t hbad = 0;
-    RFD_TRY_CUDA(cudaMemcpyAsync(&host[0], cand_count, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    RFD_TRY_CUDA(cudaMemcpyAsync(&host[1], toff + J, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    RFD_TRY_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    RFD_TRY_CUDA(cudaStreamSynchronize(s));
-    RFD_REQUIRE((host[0] & kTimeoutBit) == 0, RFD_ERR_TIMEOUT,
+    RFD_TRY_CUDA(cudaMemcpyAsync(&host->count, cand_count, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RFD_TRY_CUDA(cudaMemcpyAsync(&host->total, toff + J, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RFD_TRY_CUDA(cudaMemcpyAsync(&host->bad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    return RFD_OK;
+}
+
+// Interprets a completed read-back.
+rfd_status find_triggers_check(const TrigReadback &h, int32_t n_tmpl, int64_t cap, int64_t trig_cap,
+                               int64_t *n_trig_host) {
+    RFD_REQUIRE((h.count & kTimeoutBit) == 0, RFD_ERR_TIMEOUT,
                 "find_triggers: the filtering kernel gave up waiting on the device (timeout)");
-    RFD_REQUIRE(hbad == 0, RFD_ERR_ARG, "find_triggers: %d candidates name a template >= n_tmpl=%d",
-                hbad, n_tmpl);
-    if (host[0] > cap) {
-        *n_trig_host = host[0];
-        ::rfd::set_error("find_triggers: %lld candidates produced, capacity %lld", (long long)host[0],
+    RFD_REQUIRE(h.bad == 0, RFD_ERR_ARG, "find_triggers: %d candidates name a template >= n_tmpl=%d", h.bad, n_tmpl);
+    if (h.count > cap) {
+        *n_trig_host = h.count;
+        ::rfd::set_error("find_triggers: %lld candidates produced, capacity %lld", (long long)h.count,
                          (long long)cap);
         return RFD_ERR_OVERFLOW;
     }
-    *n_trig_host = host[1];
-    if (host[1] > trig_cap) {
-        ::rfd::set_error("find_triggers: %lld triggers, capacity %lld", (long long)host[1],
-                         (long long)trig_cap);
+    *n_trig_host = h.total;
+    if (h.total > trig_cap) {
+        ::rfd::set_error("find_triggers: %lld triggers, capacity %lld", (long long)h.total, (long long)trig_cap);
         return RFD_ERR_OVERFLOW;
     }
     return RFD_OK;
+}
+
+rfd_status find_triggers_impl(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand,
+                              const int64_t *cand_count, int64_t cap, rfd_trigger *trig,
+                              int64_t trig_cap, int64_t *n_trig_host, cudaStream_t s) {
+    TrigReadback h{};
+    RFD_TRY(find_triggers_enqueue(ctx, n_tmpl, cand, cand_count, cap, trig, trig_cap, &h, s));
+    RFD_TRY_CUDA(cudaStreamSynchronize(s));
+    return find_triggers_check(h, n_tmpl, cap, trig_cap, n_trig_host);
 }
 
 }  // namespace rfd

@@ -412,3 +412,117 @@ def test_bucketed_taps_and_uneven_k_tensor_core(ctx):
     # those windows are ambiguous by the rule; every other window must agree exactly
     assert compare_triggers(trig, sets, TOL_TC, range(J), cfg.window) <= 0.5 * n_or
     assert snr_errors(trig, sets, range(J)) < 2e-5
+
+
+# --------------------------------------------------------------------------- graph and autotuner
+def test_search_graph_matches_separate_calls(c1):
+    """The whole segment as one CUDA graph (rfd_search_*) equals the three separate calls, on two
+    segments in a row (the second written into the bound spectrum buffer)."""
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    href = gpu.templates(bank.ref_params())
+    ld = rfd.qref_ld(cfg.n, halo)
+    q = torch.zeros(bank.n_ref * ld * 8, dtype=torch.uint8, device="cuda")
+    e = torch.zeros(bank.n_ref, dtype=torch.int32, device="cuda")
+    plan = rfd.Plan(gpu.ctx, gpu.grid, bank.n_ref, bank.ref_of_tmpl, t["K"], rfd.PREC_FP16X3, cfg.window,
+                    cfg.threshold, halo)
+    plan.set_taps(t["taps"], t["k_stride"], t["lag"], t["sigma"])
+    cap, tcap = 1 << 18, 1 << 16
+    cand = torch.zeros(cap * 24, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    trig = torch.zeros(tcap * 20, dtype=torch.uint8, device="cuda")
+    d = gpu.d.clone()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        search = rfd.Search(plan, d, gpu.psd, href, q, e, cand, cnt, trig, stream)
+    assert search.kernels_per_run >= 8
+    rng = np.random.default_rng(3)
+    for seg in range(2):
+        if seg:
+            noise = (rng.standard_normal(d.numel()) + 1j * rng.standard_normal(d.numel())).astype(np.complex64)
+            d.copy_(torch.from_numpy(noise * np.abs(data.dtilde.astype(np.complex64))))
+        torch.cuda.synchronize()
+        nt_graph = search.run()
+        got = rfd.triggers_to_numpy(trig, nt_graph).copy()
+        # the same segment through the separate calls
+        rfd.filter_reference(gpu.ctx, gpu.grid, d, gpu.psd, href, halo, rfd.PREC_FP16X3, q, e)
+        plan.ratio_filter_batch(q, e, cand, cnt)
+        trig2 = torch.zeros_like(trig)
+        nt2 = rfd.find_triggers(gpu.ctx, bank.n_tmpl, cand, cnt, trig2)
+        assert nt_graph == nt2
+        assert np.array_equal(got.view(np.uint8), rfd.triggers_to_numpy(trig2, nt2).view(np.uint8))
+    search.close()
+    plan.close()
+
+
+def test_autotuner_choices_give_identical_triggers(ctx, tmp_path):
+    """Every tile choice the autotuner tries gives bit-identical triggers (tiles only change
+    which templates share an MMA and how many zero taps pad them); the tuner caches its pick."""
+    from paper_2601_18835_gb300 import autotune
+    cfg = workload.small_config(3, n=65536, n_tmpl=96, n_ref=3, threshold=9.0)
+    bank, data = workload.make_workload(cfg)
+    gpu = GpuRun(cfg, bank, data, ctx=ctx)
+    J = bank.n_tmpl
+    taps = torch.zeros((J, 512), dtype=torch.complex64, device="cuda")
+    lag = torch.zeros(J, dtype=torch.int32, device="cuda")
+    sig = torch.zeros(J, dtype=torch.float64, device="cuda")
+    kout = torch.zeros(J, dtype=torch.int32, device="cuda")
+    rfd.make_taps(ctx, gpu.grid, gpu.psd, bank.ref_params(), bank.params(), bank.ref_of_tmpl, None, 512,
+                  cfg.tukey_alpha, taps, lag, sig, buckets=list(cfg.k_buckets), k_out=kout)
+    K = kout.cpu().numpy().astype(np.int32)
+    q, e, _ = gpu.filter_reference(511, rfd.PREC_FP16X3)
+    cache = str(tmp_path / "tune.json")
+    opts, rep = autotune.autotune(ctx, gpu.grid, bank.n_ref, bank.ref_of_tmpl, K, rfd.PREC_FP16X3, cfg.window,
+                                  cfg.threshold, 511, taps, 512, lag, sig, q, e, cache_path=cache)
+    assert opts in [c["options"] for c in rep["candidates"]]
+    opts2, rep2 = autotune.autotune(ctx, gpu.grid, bank.n_ref, bank.ref_of_tmpl, K, rfd.PREC_FP16X3, cfg.window,
+                                    cfg.threshold, 511, taps, 512, lag, sig, q, e, cache_path=cache)
+    assert opts2 == opts
+    results = []
+    for c in rep["candidates"]:
+        plan = rfd.Plan(ctx, gpu.grid, bank.n_ref, bank.ref_of_tmpl, K, rfd.PREC_FP16X3, cfg.window, cfg.threshold,
+                        511, options=c["options"])
+        plan.set_taps(taps, 512, lag, sig)
+        cand = torch.zeros((1 << 22) * 24, dtype=torch.uint8, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        plan.ratio_filter_batch(q, e, cand, cnt)
+        tb = torch.zeros((1 << 18) * 20, dtype=torch.uint8, device="cuda")
+        nt = rfd.find_triggers(ctx, J, cand, cnt, tb)
+        results.append(rfd.triggers_to_numpy(tb, nt).view(np.uint8).copy())
+        plan.close()
+    assert len(results[0]) > 0
+    for r in results[1:]:
+        assert np.array_equal(r, results[0])
+
+
+def test_search_graph_times_each_run(c1):
+    """The events inside the graph are re-recorded on every replay: after two runs, two
+    different, positive step times, each longer than the ratio-filter kernel inside it."""
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    href = gpu.templates(bank.ref_params())
+    ld = rfd.qref_ld(cfg.n, halo)
+    q = torch.zeros(bank.n_ref * ld * 8, dtype=torch.uint8, device="cuda")
+    e = torch.zeros(bank.n_ref, dtype=torch.int32, device="cuda")
+    plan = rfd.Plan(gpu.ctx, gpu.grid, bank.n_ref, bank.ref_of_tmpl, t["K"], rfd.PREC_FP16X3, cfg.window,
+                    cfg.threshold, halo)
+    plan.set_taps(t["taps"], t["k_stride"], t["lag"], t["sigma"])
+    cand = torch.zeros((1 << 16) * 24, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    trig = torch.zeros((1 << 14) * 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        search = rfd.Search(plan, gpu.d, gpu.psd, href, q, e, cand, cnt, trig, stream)
+    times = []
+    for _ in range(3):
+        search.run()
+        step, kern = search.step_ms(), search.filter_ms()
+        assert 0 < kern < step
+        times.append(step)
+    assert len(set(times)) > 1
+    # nothing left behind for the next call's error check
+    rfd.filter_reference(gpu.ctx, gpu.grid, gpu.d, gpu.psd, href, halo, rfd.PREC_FP16X3, q, e)
+    search.close()
+    plan.close()
