@@ -121,13 +121,17 @@ def choose_lag(E, K):
     return int(best.min())
 
 
+def taps_at_lag(g, K, alpha, s):
+    """Windowed taps placed at a given lag: rho[k] = w[k] g[(s+k) mod N]."""
+    n = len(g)
+    return tukey(K, alpha) * g[(s + np.arange(K)) % n]
+
+
 def place_taps(g, K, alpha):
     """(s_j, rho_j): lag and windowed taps rho[k] = w[k] g[(s+k) mod N]."""
     w = tukey(K, alpha)
     s = choose_lag(window_energy(g, w), K)
-    n = len(g)
-    rho = w * g[(s + np.arange(K)) % n]
-    return s, rho
+    return s, taps_at_lag(g, K, alpha, s)
 
 
 # ---------------------------------------------------------------- the FIR of Eq. 3
