@@ -156,6 +156,18 @@ rfd_status rfd_make_taps(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_d
                          double tukey_alpha, void *taps_dev, int32_t *k_dev, int32_t *lag_dev,
                          double *sigma_dev, double *match_dev, void *stream);
 
+/* Taps at a given lag: as rfd_make_taps with fixed K, except that the placement s_j is
+ * lag_host[j] (in [-n/2, n/2)) instead of the window-energy maximiser, so
+ * rho_j[k] = w[k] g_j[(s_j + k) mod n].  These are the targets the learned-tap networks are
+ * trained on (each network's taps sit at one lag per reference).  sigma_dev / match_dev as
+ * for rfd_make_taps (match_dev may be NULL).  Synchronises the stream before returning. */
+rfd_status rfd_make_taps_at_lag(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_dev,
+                                const rfd_params *refs_host, int32_t n_ref,
+                                const rfd_params *tmpl_host, const int32_t *ref_of_tmpl_host,
+                                int32_t n_tmpl, const int32_t *k_host, const int32_t *lag_host,
+                                int32_t k_stride, double tukey_alpha, void *taps_dev,
+                                double *sigma_dev, double *match_dev, void *stream);
+
 /* ------------------------------------------------------------------ filter_reference
  * The reference SNR series of Eq. 3, (s|h)_ref, one per reference (Eq. 1 discretised):
  *   c_r[k] = 4 df d[k] conj(h_r[k]) / S[k] for k <= n/2 (h_r is zero outside its band),
@@ -317,6 +329,100 @@ rfd_status rfd_findchirp(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_
  * with the library's Stockham kernels: in_dev and out_dev may not overlap. */
 rfd_status rfd_ifft_c2c(rfd_ctx *ctx, int64_t n, int32_t batch, const void *in_dev,
                         void *out_dev, void *stream);
+
+/* ------------------------------------------------------------------ learned taps
+ * A surrogate for make_taps: one network per reference maps a template to 128 complex taps
+ * at the network's fixed lag.  Inputs (20): the features
+ *   x = (Mc, eta, chi_eff, Lambda~),  Mc = M eta^(3/5), chi_eff = (m1 chi1 + m2 chi2) / M,
+ * standardised per network, xh = (x - mu) / sd, then cos p_m and sin p_m of the ratio's phase
+ * (Eq. 2) p_m = Dpsi(f_m) - Dpsi(f_4), Dpsi = Psi_j - Psi_r in FP64, at the eight frequencies
+ * f_m (m = 0..8, m != 4) log-spaced from 3 f_low to 0.45 fs.  Layers
+ *   h1 = gelu(W1 in + b1), h2 = gelu(W2 h1 + b2), h3 = gelu(W3 h2 + b3), y = W4 h3 + b4
+ * (widths 20 -> 256 -> 256 -> 256 -> 256; gelu(u) = u/2 (1 + tanh(sqrt(2/pi)(u + 0.044715 u^3))))
+ * give rho[k] = out_scale (y[k] + i y[128 + k]).
+ * Training minimises the PSD-weighted chi^2 of Eq. 4 (Sec. V.A) between the response of rho
+ * and that of the exact taps a* at the same lag, written in the tap domain through Parseval
+ * (Eqs. 5-6) and minimised over a constant phase of a* (which only rotates z):
+ *   L = (rho^H M rho + a*^H M a* - 2 |a*^H M rho|) / (a*^H M a*),  M[b, a] = C_r[b - a],
+ * averaged over the batch.  FP16 operands on the tensor cores, FP32 master weights, Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8), dynamic loss scaling on the device.
+ * Weights (host float32), per network in this order: W1 [256][20], b1 [256], W2 [256][256],
+ * b2, W3 [256][256], b3, W4 [256][256], b4: rfd_mlp_param_count() floats per network. */
+#define RFD_MLP_TAPS 128
+#define RFD_MLP_INPUTS 20
+#define RFD_MLP_FEATURES_LD 64     /* halfs per row of an input buffer (20 used, zero padded) */
+typedef struct rfd_mlp rfd_mlp;
+int64_t rfd_mlp_param_count(void);
+/* One network per reference; computes the references' autocorrelations C_r[l], |l| < 128
+ * (Eq. 6 on the sample grid, FP64).  Weights start at zero: call rfd_mlp_set_weights. */
+rfd_status rfd_mlp_create(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_dev,
+                          const rfd_params *refs_host, int32_t n_ref, rfd_mlp **out);
+void rfd_mlp_destroy(rfd_mlp *mlp);
+/* Sets the FP32 master weights of every network (host [n_ref][param_count]) and resets the
+ * optimiser (step 0, loss scale 2^16).  Synchronous.  get_weights copies them back. */
+rfd_status rfd_mlp_set_weights(rfd_mlp *mlp, const float *weights_host);
+rfd_status rfd_mlp_get_weights(const rfd_mlp *mlp, float *weights_host);
+/* Per network: feature mean and spread (host double [n_ref][4] each, spread > 0), output
+ * scale (double [n_ref], > 0) and lag s_r (int32 [n_ref], in [-n/2, n/2)).  Synchronous. */
+rfd_status rfd_mlp_set_norm(rfd_mlp *mlp, const double *mu_host, const double *sd_host,
+                            const double *out_scale_host, const int32_t *lag_host);
+/* C_r rows as complex128 [n_ref][255], lag l at index l + 127.  Synchronous. */
+rfd_status rfd_mlp_get_autocorr(const rfd_mlp *mlp, double *autocorr_host);
+/* FP16 network inputs of n templates (row j uses network net_of_host[j]) into feat_dev
+ * half [n][64].  Synchronises the stream. */
+rfd_status rfd_mlp_features(rfd_mlp *mlp, const rfd_params *params_host,
+                            const int32_t *net_of_host, int32_t n, void *feat_dev, void *stream);
+/* One optimiser step of every network on a batch: network g uses the rows
+ * idx_dev[g][b] (int32 [n_ref][batch], each < n_train) of feat_dev (half
+ * [n_ref][n_train][64]) and target_dev (complex64 [n_ref][n_train][128], the exact taps).
+ * batch: multiple of 128 in [128, 8192].  Stream-ordered, no host synchronisation; a step
+ * whose gradients are not finite is skipped on the device. */
+rfd_status rfd_mlp_train_step(rfd_mlp *mlp, const void *feat_dev, const void *target_dev,
+                              int32_t n_train, const int32_t *idx_dev, int32_t batch, float lr,
+                              void *stream);
+/* Forward and backward only: unscaled gradients into grads_dev (float [n_ref][param_count],
+ * the weight layout) and the batch-mean loss per network into loss_dev (float [n_ref]).
+ * Synchronises the stream. */
+rfd_status rfd_mlp_grads(rfd_mlp *mlp, const void *feat_dev, const void *target_dev,
+                         int32_t n_train, const int32_t *idx_dev, int32_t batch,
+                         float *grads_dev, float *loss_dev, void *stream);
+/* After the last step: batch-mean loss per network (host float [n_ref], may be NULL), steps
+ * taken and the current loss scale.  Synchronises the stream; RFD_ERR_TIMEOUT if a kernel
+ * gave up a bounded wait. */
+rfd_status rfd_mlp_state(rfd_mlp *mlp, float *loss_host, int32_t *step_host,
+                         float *loss_scale_host, void *stream);
+/* Surrogate taps of n templates: taps_dev complex64 [n][k_stride] (k_stride >= 128, taps
+ * 128.. zero), lag_dev int32 [n] (the network's lag), sigma_dev float64 [n] (sigma_eff of
+ * the stored taps, Eqs. 5-6).  The outputs are what rfd_plan_set_taps takes.  Synchronises
+ * the stream. */
+rfd_status rfd_mlp_infer(rfd_mlp *mlp, const rfd_params *params_host,
+                         const int32_t *net_of_host, int32_t n, int32_t k_stride,
+                         void *taps_dev, int32_t *lag_dev, double *sigma_dev, void *stream);
+/* Match between the responses of tap rows rho1[i] and rho2[i] (complex64, row strides ld1,
+ * ld2 >= 128, first 128 taps, same lag) under reference net_of_host[i]'s C_r:
+ * |rho2^H M rho1| / sqrt(rho1^H M rho1 rho2^H M rho2) into match_dev float64 [n].
+ * Synchronises the stream. */
+rfd_status rfd_mlp_cross_match(rfd_mlp *mlp, const int32_t *net_of_host, int32_t n,
+                               const void *rho1_dev, int64_t ld1, const void *rho2_dev,
+                               int64_t ld2, double *match_dev, void *stream);
+/* Taps for a bank with the surrogate and exact extraction as the fallback.  Every template
+ * gets surrogate taps; per reference, templates are ordered by chirp mass and every
+ * spot_stride-th one (and the last) is spot-checked: its exact taps at the network's lag
+ * (rfd_make_taps_at_lag) are compared with its surrogate taps by the match above.  A
+ * template keeps its surrogate taps when the spot checks on both sides of it in that order
+ * (or its own, for a spot-checked one) reach min_match (0.999 is the intended bar); the rest
+ * get exact taps from rfd_make_taps (their own lag, K = 128).
+ * Outputs: taps_dev complex64 [n_tmpl][k_stride], lag_dev, sigma_dev as for rfd_make_taps;
+ * surrogate_match_dev float64 [n_tmpl] (may be NULL): the measured match of spot-checked
+ * templates, NaN elsewhere; source_dev int32 [n_tmpl]: 0 surrogate, 1 exact fallback,
+ * 2 surrogate and spot-checked; stats_host int64 [4] (may be NULL): templates on surrogate
+ * taps, on exact taps, spot-checked, spot checks below min_match.  Synchronous. */
+rfd_status rfd_learned_taps(rfd_mlp *mlp, const double *psd_dev, const rfd_params *tmpl_host,
+                            const int32_t *ref_of_tmpl_host, int32_t n_tmpl, int32_t spot_stride,
+                            double min_match, int32_t k_stride, double tukey_alpha,
+                            void *taps_dev, int32_t *lag_dev, double *sigma_dev,
+                            double *surrogate_match_dev, int32_t *source_dev,
+                            int64_t *stats_host, void *stream);
 
 #ifdef __cplusplus
 }

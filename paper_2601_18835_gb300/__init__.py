@@ -9,6 +9,8 @@ step of the method runs in the library's CUDA kernels.  Names follow include/rfd
   Plan.ratio_filter_batch   FIR of every template on q_ref + fused triggers    Eq. 3, Table II
   find_triggers      per-window maxima above threshold                         Table II
   findchirp          the FINDCHIRP comparison path                             Eq. 1
+  make_taps_at_lag   taps at a given lag (the learned-tap targets)             Sec. V
+  Mlp                learned taps: per-reference networks, training, inference Eq. 4 through Eqs. 5-6
 """
 import ctypes
 
@@ -19,7 +21,8 @@ from . import _native
 from ._native import (CANDIDATE_DTYPE, PN_SO, PN_TIDAL, PREC_BF16X3, PREC_FP16X3, PREC_FP32,  # noqa: F401
                       TRIGGER_DTYPE, RfdError, check)
 
-__all__ = ["Context", "Plan", "Search", "grid", "gen_templates", "make_taps", "filter_reference",
+__all__ = ["Context", "Plan", "Search", "Mlp", "grid", "gen_templates", "make_taps", "make_taps_at_lag",
+           "filter_reference",
            "find_triggers", "find_triggers_noalloc", "findchirp", "ifft_c2c", "qref_ld", "candidates_to_numpy",
            "triggers_to_numpy", "CANDIDATE_DTYPE", "TRIGGER_DTYPE"]
 
@@ -121,6 +124,19 @@ def make_taps(ctx, g, psd, refs, tmpl, ref_of, k, k_stride, alpha, taps, lag, si
     check(_lib().rfd_make_taps(ctx.handle, ctypes.byref(g), _ptr(psd), ra, nr, ta, rop, nt, kp, bkp, nbk,
                                float(energy_frac), int(k_stride), float(alpha), _ptr(taps), _ptr(k_out),
                                _ptr(lag), _ptr(sigma), _ptr(match), _stream(stream)))
+
+
+def make_taps_at_lag(ctx, g, psd, refs, tmpl, ref_of, k, lag, k_stride, alpha, taps, sigma, match=None,
+                     stream=None):
+    """Taps placed at the given lags (int32 per template, in [-n/2, n/2))."""
+    ra, nr = _params(refs)
+    ta, nt = _params(tmpl)
+    ro, rop = _i32_host(ref_of)
+    kk, kp = _i32_host(k)
+    ll, lp = _i32_host(lag)
+    check(_lib().rfd_make_taps_at_lag(ctx.handle, ctypes.byref(g), _ptr(psd), ra, nr, ta, rop, nt, kp, lp,
+                                      int(k_stride), float(alpha), _ptr(taps), _ptr(sigma), _ptr(match),
+                                      _stream(stream)))
 
 
 def filter_reference(ctx, g, dtilde, psd, href, halo, precision, qref, qscale, stream=None):
@@ -274,3 +290,112 @@ def candidates_to_numpy(buf, count):
 def triggers_to_numpy(buf, count):
     raw = buf[: count * TRIGGER_DTYPE.itemsize].cpu().numpy().view(np.uint8)
     return raw.view(TRIGGER_DTYPE)
+
+
+class Mlp:
+    """Learned taps: one network per reference (include/rfd.h, "learned taps")."""
+
+    TAPS = _native.MLP_TAPS
+    FEATURES_LD = _native.MLP_FEATURES_LD
+
+    def __init__(self, ctx, g, psd, refs):
+        ra, nr = _params(refs)
+        h = ctypes.c_void_p()
+        check(_lib().rfd_mlp_create(ctx.handle, ctypes.byref(g), _ptr(psd), ra, nr, ctypes.byref(h)))
+        self.handle = h
+        self.n_ref = nr
+        self.ctx = ctx
+
+    @staticmethod
+    def param_count():
+        return int(_lib().rfd_mlp_param_count())
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float32).reshape(self.n_ref, self.param_count()))
+        check(_lib().rfd_mlp_set_weights(self.handle, w.ctypes.data_as(ctypes.c_void_p)))
+
+    def get_weights(self):
+        w = np.empty((self.n_ref, self.param_count()), dtype=np.float32)
+        check(_lib().rfd_mlp_get_weights(self.handle, w.ctypes.data_as(ctypes.c_void_p)))
+        return w
+
+    def set_norm(self, mu, sd, out_scale, lag):
+        mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float64).reshape(self.n_ref, 4))
+        sd = np.ascontiguousarray(np.asarray(sd, dtype=np.float64).reshape(self.n_ref, 4))
+        sc = np.ascontiguousarray(np.asarray(out_scale, dtype=np.float64).reshape(self.n_ref))
+        lg, lp = _i32_host(np.asarray(lag).reshape(self.n_ref))
+        check(_lib().rfd_mlp_set_norm(self.handle, mu.ctypes.data_as(ctypes.c_void_p),
+                                      sd.ctypes.data_as(ctypes.c_void_p), sc.ctypes.data_as(ctypes.c_void_p), lp))
+
+    def autocorr(self):
+        c = np.empty((self.n_ref, 2 * self.TAPS - 1, 2), dtype=np.float64)
+        check(_lib().rfd_mlp_get_autocorr(self.handle, c.ctypes.data_as(ctypes.c_void_p)))
+        return c[..., 0] + 1j * c[..., 1]
+
+    def features(self, params, net_of, out=None, stream=None):
+        pa, n = _params(params)
+        no, nop = _i32_host(net_of)
+        if out is None:
+            out = torch.empty((n, self.FEATURES_LD), dtype=torch.float16, device="cuda")
+        check(_lib().rfd_mlp_features(self.handle, pa, nop, n, _ptr(out), _stream(stream)))
+        return out
+
+    def train_step(self, feat, target, n_train, idx, batch, lr, stream=None):
+        check(_lib().rfd_mlp_train_step(self.handle, _ptr(feat), _ptr(target), int(n_train), _ptr(idx), int(batch),
+                                        float(lr), _stream(stream)))
+
+    def grads(self, feat, target, n_train, idx, batch, stream=None):
+        g = torch.empty((self.n_ref, self.param_count()), dtype=torch.float32, device="cuda")
+        loss = torch.empty(self.n_ref, dtype=torch.float32, device="cuda")
+        check(_lib().rfd_mlp_grads(self.handle, _ptr(feat), _ptr(target), int(n_train), _ptr(idx), int(batch),
+                                   _ptr(g), _ptr(loss), _stream(stream)))
+        return g, loss
+
+    def state(self, stream=None):
+        """(per-network batch loss, steps taken, loss scale) after the last step."""
+        loss = np.empty(self.n_ref, dtype=np.float32)
+        step = ctypes.c_int32()
+        scale = ctypes.c_float()
+        check(_lib().rfd_mlp_state(self.handle, loss.ctypes.data_as(ctypes.c_void_p), ctypes.byref(step),
+                                   ctypes.byref(scale), _stream(stream)))
+        return loss, int(step.value), float(scale.value)
+
+    def infer(self, params, net_of, taps, lag, sigma, k_stride=None, stream=None):
+        pa, n = _params(params)
+        no, nop = _i32_host(net_of)
+        ks = int(taps.shape[-1]) if k_stride is None else int(k_stride)
+        check(_lib().rfd_mlp_infer(self.handle, pa, nop, n, ks, _ptr(taps), _ptr(lag), _ptr(sigma),
+                                   _stream(stream)))
+
+    def cross_match(self, net_of, rho1, rho2, stream=None):
+        no, nop = _i32_host(net_of)
+        out = torch.empty(len(no), dtype=torch.float64, device="cuda")
+        check(_lib().rfd_mlp_cross_match(self.handle, nop, len(no), _ptr(rho1), int(rho1.shape[-1]), _ptr(rho2),
+                                         int(rho2.shape[-1]), _ptr(out), _stream(stream)))
+        return out
+
+    def learned_taps(self, psd, tmpl, ref_of, taps, lag, sigma, spot_stride=8, min_match=0.999, alpha=0.1,
+                     stream=None):
+        """Surrogate taps with spot checks and exact fallback; returns (source, surrogate match, stats)."""
+        ta, nt = _params(tmpl)
+        ro, rop = _i32_host(ref_of)
+        source = torch.empty(nt, dtype=torch.int32, device="cuda")
+        smatch = torch.empty(nt, dtype=torch.float64, device="cuda")
+        stats = np.zeros(4, dtype=np.int64)
+        check(_lib().rfd_learned_taps(self.handle, _ptr(psd), ta, rop, nt, int(spot_stride), float(min_match),
+                                      int(taps.shape[-1]), float(alpha), _ptr(taps), _ptr(lag), _ptr(sigma),
+                                      _ptr(smatch), _ptr(source), stats.ctypes.data_as(ctypes.c_void_p),
+                                      _stream(stream)))
+        return source, smatch, {"surrogate": int(stats[0]), "exact": int(stats[1]), "spot_checked": int(stats[2]),
+                                "spot_failed": int(stats[3])}
+
+    def close(self):
+        if self.handle:
+            _lib().rfd_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

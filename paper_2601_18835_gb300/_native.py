@@ -89,7 +89,26 @@ SIGNATURES = {
     "rfd_findchirp": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _vp, _i32, _i32, _flt, _vp, _i64, _vp,
                              _vp]),
     "rfd_ifft_c2c": (_i32, [_vp, _i64, _i32, _vp, _vp, _vp]),
+    "rfd_make_taps_at_lag": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _i32,
+                                    _dbl, _vp, _vp, _vp, _vp]),
+    "rfd_mlp_param_count": (_i64, []),
+    "rfd_mlp_create": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, ctypes.POINTER(_vp)]),
+    "rfd_mlp_destroy": (None, [_vp]),
+    "rfd_mlp_set_weights": (_i32, [_vp, _vp]),
+    "rfd_mlp_get_weights": (_i32, [_vp, _vp]),
+    "rfd_mlp_set_norm": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "rfd_mlp_get_autocorr": (_i32, [_vp, _vp]),
+    "rfd_mlp_features": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    "rfd_mlp_train_step": (_i32, [_vp, _vp, _vp, _i32, _vp, _i32, _flt, _vp]),
+    "rfd_mlp_grads": (_i32, [_vp, _vp, _vp, _i32, _vp, _i32, _vp, _vp, _vp]),
+    "rfd_mlp_state": (_i32, [_vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_flt), _vp]),
+    "rfd_mlp_infer": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp]),
+    "rfd_mlp_cross_match": (_i32, [_vp, _vp, _i32, _vp, _i64, _vp, _i64, _vp, _vp]),
+    "rfd_learned_taps": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _dbl, _i32, _dbl, _vp, _vp, _vp, _vp, _vp, _vp,
+                                _vp]),
 }
+MLP_TAPS = 128
+MLP_FEATURES_LD = 64
 
 _lib = None
 

@@ -17,10 +17,6 @@ rfd_status filter_reference_impl(rfd_ctx *, const Grid &, const float2 *, const 
                                  int64_t, int32_t, int32_t, void *, int32_t *, cudaStream_t);
 rfd_status findchirp_impl(rfd_ctx *, const Grid &, const float2 *, const double *, const float2 *, int64_t,
                           int32_t, float, rfd_candidate *, int64_t, int64_t *, cudaStream_t);
-rfd_status make_taps_impl(rfd_ctx *, const Grid &, const double *, const std::vector<PNParams> &,
-                          const std::vector<PNParams> &, const std::vector<int32_t> &,
-                          const std::vector<int32_t> &, const std::vector<int32_t> &, double, int32_t, double,
-                          float2 *, int32_t *, int32_t *, double *, double *, cudaStream_t);
 int fir32_tile_templates();
 rfd_status fir32_launch(const rfd_plan *, const float2 *, rfd_candidate *, int64_t, int64_t *,
                         cudaStream_t);
@@ -195,7 +191,7 @@ rfd_status make_pn(const Grid &g, const rfd_params *p, PNParams *out) {
     return RFD_OK;
 }
 
-static rfd_status make_pn_vec(const Grid &g, const rfd_params *p, int32_t count,
+rfd_status make_pn_vec(const Grid &g, const rfd_params *p, int32_t count,
                               std::vector<PNParams> *out) {
     out->resize(count);
     for (int32_t i = 0; i < count; ++i) RFD_TRY(make_pn(g, &p[i], &(*out)[i]));
@@ -320,8 +316,43 @@ rfd_status rfd_make_taps(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_d
     RFD_TRY(make_pn_vec(g, tmpl_host, n_tmpl, &tmpl));
     for (int32_t r = 0; r < n_ref; ++r)
         RFD_REQUIRE(refs[r].k_hi >= g.k_lo, RFD_ERR_ARG, "reference %d has an empty band (ISCO below f_low)", r);
-    return make_taps_impl(ctx, g, psd_dev, refs, tmpl, ref_of, K, buckets, energy_frac, k_stride, tukey_alpha,
+    return make_taps_impl(ctx, g, psd_dev, refs, tmpl, ref_of, K, buckets, {}, energy_frac, k_stride, tukey_alpha,
                           (float2 *)taps_dev, k_dev, lag_dev, sigma_dev, match_dev, (cudaStream_t)stream);
+}
+
+rfd_status rfd_make_taps_at_lag(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_dev,
+                                const rfd_params *refs_host, int32_t n_ref, const rfd_params *tmpl_host,
+                                const int32_t *ref_of_tmpl_host, int32_t n_tmpl, const int32_t *k_host,
+                                const int32_t *lag_host, int32_t k_stride, double tukey_alpha, void *taps_dev,
+                                double *sigma_dev, double *match_dev, void *stream) {
+    RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
+    Grid g;
+    RFD_TRY(check_grid(grid, &g));
+    RFD_REQUIRE(n_ref >= 1 && n_tmpl >= 0, RFD_ERR_SHAPE, "need n_ref >= 1 and n_tmpl >= 0");
+    if (n_tmpl == 0) return RFD_OK;
+    RFD_REQUIRE(psd_dev && refs_host && tmpl_host && ref_of_tmpl_host && k_host && lag_host && taps_dev && sigma_dev,
+                RFD_ERR_ARG, "NULL argument");
+    RFD_REQUIRE(k_stride >= 1 && k_stride <= 4096 && k_stride <= g.n, RFD_ERR_SHAPE,
+                "k_stride=%d out of [1, min(4096, n)]", k_stride);
+    RFD_REQUIRE(std::isfinite(tukey_alpha) && tukey_alpha >= 0.0, RFD_ERR_ARG, "tukey_alpha must be >= 0");
+    std::vector<int32_t> ref_of(ref_of_tmpl_host, ref_of_tmpl_host + n_tmpl), K(k_host, k_host + n_tmpl),
+        lag(lag_host, lag_host + n_tmpl);
+    for (int32_t j = 0; j < n_tmpl; ++j) {
+        RFD_REQUIRE(ref_of[j] >= 0 && ref_of[j] < n_ref, RFD_ERR_ARG, "ref_of_tmpl[%d]=%d out of range", j, ref_of[j]);
+        RFD_REQUIRE(K[j] >= 1 && K[j] <= k_stride, RFD_ERR_SHAPE, "K[%d]=%d not in [1, k_stride]", j, K[j]);
+        RFD_REQUIRE(lag[j] >= -(g.n / 2) && lag[j] < g.n / 2, RFD_ERR_ARG, "lag[%d]=%d not in [-n/2, n/2)", j, lag[j]);
+    }
+    RFD_TRY_CUDA(cudaSetDevice(ctx->device));
+    std::vector<PNParams> refs, tmpl;
+    RFD_TRY(make_pn_vec(g, refs_host, n_ref, &refs));
+    RFD_TRY(make_pn_vec(g, tmpl_host, n_tmpl, &tmpl));
+    for (int32_t r = 0; r < n_ref; ++r)
+        RFD_REQUIRE(refs[r].k_hi >= g.k_lo, RFD_ERR_ARG, "reference %d has an empty band (ISCO below f_low)", r);
+    // the placed lag is written back; it equals lag_host
+    RFD_TRY(ensure(ctx->ws[12], (size_t)n_tmpl * sizeof(int32_t)));
+    int32_t *lag_dev = (int32_t *)ctx->ws[12].p;
+    return make_taps_impl(ctx, g, psd_dev, refs, tmpl, ref_of, K, {}, lag, 1.0, k_stride, tukey_alpha,
+                          (float2 *)taps_dev, nullptr, lag_dev, sigma_dev, match_dev, (cudaStream_t)stream);
 }
 
 rfd_status rfd_filter_reference(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev,

@@ -427,12 +427,31 @@ __global__ void k_match_final(const double *__restrict__ part, int64_t nb, int32
 
 // Workspace slots: ws[6] jobs, ws[7] G / placed taps, ws[8] g / A, ws[9] FFT tmp, ws[10] E,
 // ws[11] per-template scalars (emax, lagkey) + rho64 + C_r rows + match partials.
+// C_r[l] = sum_k 4 df |h_r|^2/S exp(+2 pi i k l / n) for |l| < kmax, one inverse FFT per
+// reference (Eq. 6 on the sample grid): C[r][l + kmax - 1], complex128.  refs_dev: PNParams[R].
+// Scratch: ws[7], ws[8], ws[9] (R n complex128 each).
+rfd_status ref_autocorr_impl(rfd_ctx *ctx, const Grid &g, const double *psd, const PNParams *refs_dev, int64_t R,
+                             int32_t kmax, double2 *C, cudaStream_t s) {
+    const int64_t n = g.n;
+    RFD_TRY(ensure(ctx->ws[7], R * n * sizeof(double2)));
+    RFD_TRY(ensure(ctx->ws[8], R * n * sizeof(double2)));
+    RFD_TRY(ensure(ctx->ws[9], R * n * sizeof(double2)));
+    double2 *Gb = (double2 *)ctx->ws[7].p, *gb = (double2 *)ctx->ws[8].p, *tmp = (double2 *)ctx->ws[9].p;
+    k_ref_weight<<<dim3((unsigned)((n + 255) / 256), (unsigned)R), 256, 0, s>>>(refs_dev, psd, g.df, n, g.k_lo, gb);
+    RFD_LAUNCH_CHECK();
+    RFD_TRY(fft_c2c<double>(ctx, n, R, gb, n, Gb, n, tmp, true, s));
+    k_compact_C<<<(unsigned)R, 256, 0, s>>>(Gb, n, kmax, C);
+    RFD_LAUNCH_CHECK();
+    return RFD_OK;
+}
+
 rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
                           const std::vector<PNParams> &refs, const std::vector<PNParams> &tmpl,
                           const std::vector<int32_t> &ref_of, const std::vector<int32_t> &K,
-                          const std::vector<int32_t> &buckets, double energy_frac, int32_t k_stride,
-                          double alpha, float2 *taps, int32_t *k_out, int32_t *lag, double *sigma,
-                          double *match, cudaStream_t s) {
+                          const std::vector<int32_t> &buckets, const std::vector<int32_t> &lag_in,
+                          double energy_frac, int32_t k_stride, double alpha, float2 *taps, int32_t *k_out,
+                          int32_t *lag, double *sigma, double *match, cudaStream_t s) {
+    const bool fixed_lag = !lag_in.empty();
     const int64_t n = g.n;
     const int64_t J = (int64_t)tmpl.size(), R = (int64_t)refs.size();
     const bool bucketed = K.empty();
@@ -471,7 +490,6 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
     double2 *rho64 = (double2 *)(base11 + off_rho);
     double2 *C = (double2 *)(base11 + off_C);
     double *part = (double *)(base11 + off_part);
-    double2 *Gb = (double2 *)ctx->ws[7].p, *gb = (double2 *)ctx->ws[8].p, *tmp = (double2 *)ctx->ws[9].p;
     double *E = (double *)ctx->ws[10].p;
     double *Pbuf = (double *)ctx->ws[15].p;
     if (bucketed)
@@ -480,12 +498,9 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
     // C_r[l] = sum_k 4 df |h_r|^2/S exp(+2 pi i k l / n): one inverse FFT per reference
     RFD_TRY_CUDA(cudaMemcpyAsync(ctx->ws[0].p, refs.data(), R * sizeof(PNParams),
                                  cudaMemcpyHostToDevice, s));
-    k_ref_weight<<<dim3((unsigned)((n + 255) / 256), (unsigned)R), 256, 0, s>>>(
-        (const PNParams *)ctx->ws[0].p, psd, g.df, n, g.k_lo, gb);
-    RFD_LAUNCH_CHECK();
-    RFD_TRY(fft_c2c<double>(ctx, n, R, gb, n, Gb, n, tmp, true, s));
-    k_compact_C<<<(unsigned)R, 256, 0, s>>>(Gb, n, kmax, C);
-    RFD_LAUNCH_CHECK();
+    RFD_TRY(ref_autocorr_impl(ctx, g, psd, (const PNParams *)ctx->ws[0].p, R, kmax, C, s));
+    double2 *Gb = (double2 *)ctx->ws[7].p, *gb = (double2 *)ctx->ws[8].p, *tmp = (double2 *)ctx->ws[9].p;
+    std::vector<unsigned long long> lk;
 
     std::vector<TapJob> jobs(B);
     for (int64_t j0 = 0; j0 < J; j0 += B) {
@@ -506,6 +521,16 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
                                                                                n, g.k_lo, Gb);
         RFD_LAUNCH_CHECK();
         RFD_TRY(fft_c2c<double>(ctx, n, nbt, Gb, n, gb, n, tmp, true, s));
+        if (fixed_lag) {
+            // lags given by the caller: the placement key holds s + n/2 in its low bits
+            lk.resize(nbt);
+            for (int64_t b = 0; b < nbt; ++b) lk[b] = (unsigned long long)((int64_t)lag_in[j0 + b] + n / 2);
+            RFD_TRY_CUDA(cudaMemcpyAsync(lagkey, lk.data(), nbt * sizeof(unsigned long long),
+                                         cudaMemcpyHostToDevice, s));
+            if (k_out)
+                RFD_TRY_CUDA(cudaMemcpyAsync(k_out + j0, K.data() + j0, nbt * sizeof(int32_t),
+                                             cudaMemcpyHostToDevice, s));
+        } else {
         // energy prefix sums, optional K bucket, pruned exact lag search
         k_energy_prefix<<<(unsigned)nbt, 1024, 0, s>>>(gb, n, Pbuf);
         RFD_LAUNCH_CHECK();
@@ -534,6 +559,7 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
         RFD_LAUNCH_CHECK();
         k_lag_select<<<dim3((unsigned)(n / 256), (unsigned)nbt), 256, 0, s>>>(dj, E, n, emax, lagkey);
         RFD_LAUNCH_CHECK();
+        }
         if (match) RFD_TRY_CUDA(cudaMemsetAsync(Gb, 0, nbt * n * sizeof(double2), s));
         k_place<<<(unsigned)nbt, 256, 0, s>>>(dj, gb, n, alpha, lagkey, (int32_t)j0, k_stride, rho64,
                                               taps, lag, match ? Gb : nullptr);

@@ -14,5 +14,5 @@ with their own code, which is what the injection-recovery tests compare against.
 from .configs import CONFIGS, Config, get_config, small_config  # noqa: F401
 from .generate import (  # noqa: F401
     Bank, Data, T_SUN, chirp_mass, make_bank, make_data, make_workload, psd_analytic,
-    band_low_index,
+    band_low_index, make_training_bank, dense_bank,
 )

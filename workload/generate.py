@@ -127,6 +127,52 @@ def make_bank(cfg: Config, n_tmpl: int = None) -> Bank:
                 chi2[ref_idx].copy(), lam[ref_idx].copy(), ref_of, ref_idx)
 
 
+def make_training_bank(cfg: Config, bank: Bank, n_train: int) -> Bank:
+    """Templates from cfg's parameter distribution with the training seed 5000 + c, assigned to
+    `bank`'s references by nearest chirp mass (the learned-tap networks' training set)."""
+    rng = np.random.default_rng(5000 + cfg.index)
+    m = rng.uniform(cfg.m_range[0], cfg.m_range[1], size=(n_train, 2))
+    m1 = np.maximum(m[:, 0], m[:, 1])
+    m2 = np.minimum(m[:, 0], m[:, 1])
+    z = np.zeros(n_train)
+    chi1, chi2, lam = z.copy(), z.copy(), z.copy()
+    if cfg.chi_range is not None:
+        chi = rng.uniform(cfg.chi_range[0], cfg.chi_range[1], size=(n_train, 2))
+        chi1, chi2 = chi[:, 0].copy(), chi[:, 1].copy()
+    if cfg.lambda_range is not None:
+        lam = rng.uniform(cfg.lambda_range[0], cfg.lambda_range[1], size=n_train)
+    ref_mc = chirp_mass(bank.ref_m1, bank.ref_m2)
+    d = np.abs(chirp_mass(m1, m2)[:, None] - ref_mc[None, :])
+    ref_of = np.argmin(d, axis=1).astype(np.int32)
+    return Bank(m1, m2, chi1, chi2, lam, bank.ref_m1, bank.ref_m2, bank.ref_chi1, bank.ref_chi2, bank.ref_lam,
+                ref_of, bank.ref_tmpl_index)
+
+
+def dense_bank(ref_params, n_per_ref: int, delta_mc: float, seed: int, q_range=(0.8, 1.0),
+               chi_range=(-0.05, 0.05), lam_range=(0.0, 2000.0)) -> Bank:
+    """The dense-reference regime of the paper (references about 1 % of the bank, each
+    template close to its reference): for each reference, n_per_ref templates with chirp mass
+    uniform within a relative +-delta_mc of the reference's, mass ratio q = m2/m1 uniform in
+    q_range, spins and Lambda~ uniform.  Templates are grouped by reference."""
+    ref = np.asarray(ref_params, dtype=np.float64).reshape(-1, 5)
+    rng = np.random.default_rng(seed)
+    out, ref_of = [], []
+    for r, p in enumerate(ref):
+        mc0 = float(chirp_mass(p[0], p[1]))
+        mc = mc0 * (1.0 + delta_mc * rng.uniform(-1.0, 1.0, n_per_ref))
+        q = rng.uniform(q_range[0], q_range[1], n_per_ref)
+        m1 = mc * (1.0 + q) ** 0.2 / q ** 0.6
+        m2 = q * m1
+        c = rng.uniform(chi_range[0], chi_range[1], (n_per_ref, 2))
+        lam = rng.uniform(lam_range[0], lam_range[1], n_per_ref)
+        out.append(np.stack([m1, m2, c[:, 0], c[:, 1], lam], axis=1))
+        ref_of.append(np.full(n_per_ref, r, dtype=np.int32))
+    P = np.concatenate(out)
+    return Bank(P[:, 0].copy(), P[:, 1].copy(), P[:, 2].copy(), P[:, 3].copy(), P[:, 4].copy(),
+                ref[:, 0].copy(), ref[:, 1].copy(), ref[:, 2].copy(), ref[:, 3].copy(), ref[:, 4].copy(),
+                np.concatenate(ref_of), np.full(len(ref), -1, dtype=np.int32))
+
+
 def _inject(f, m1, m2, chi1, chi2, lam, pn_flags, f_low):
     """Frequency-domain TaylorF2 chirp for the injected signal (data synthesis only):
     amplitude f^(-7/6) between f_low and the Schwarzschild ISCO, stationary-phase phase
