@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--n-tmpl", type=int, default=None, help="smaller bank (profiling cases only)")
     ap.add_argument("--n-ref", type=int, default=None, help="fewer references (profiling cases only)")
     ap.add_argument("--no-graph", action="store_true", help="separate launches instead of one CUDA graph")
+    ap.add_argument("--n-train", type=int, default=200000, help="learned taps: training tap sets (config 4)")
+    ap.add_argument("--epochs", type=int, default=400, help="learned taps: training epochs (config 4)")
+    ap.add_argument("--spot-stride", type=int, default=8, help="learned taps: one spot check per this many templates")
+    ap.add_argument("--dense-refs", type=int, default=0,
+                    help="learned taps: this many references with templates clustered within +-0.2%% of their "
+                         "chirp mass (the dense-reference regime) instead of the config's bank")
     return ap.parse_args()
 
 
@@ -215,10 +221,136 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------- GPU arm
+def learned_taps(cfg, bank, ctx, grid, psd, stream, n_train, epochs, spot_stride=8, dense_train=None, seed=4):
+    """Learned-tap set-up for a bank: per-reference networks trained on the GPU on exact taps
+    at each reference's lag, then surrogate taps with spot checks and exact fallback for the
+    bank.  Returns (taps, lag, sigma, report)."""
+    import torch
+    import paper_2601_18835_gb300 as rfd
+    import workload
+    K, R = 128, bank.n_ref
+    rep = {}
+    train = dense_train if dense_train is not None else workload.make_training_bank(cfg, bank, n_train)
+    rng = np.random.default_rng(seed)
+    n_per = max(256, len(train.m1) // R)
+    groups = []
+    for r in range(R):
+        g = np.nonzero(train.ref_of_tmpl == r)[0]
+        if len(g) == 0:
+            g = np.nonzero(bank.ref_of_tmpl == r)[0]
+            src = bank
+        else:
+            src = train
+        pick = rng.choice(g, n_per, replace=len(g) < n_per)
+        groups.append(src.params()[pick])
+    P = np.concatenate(groups)
+    ro = np.repeat(np.arange(R, dtype=np.int32), n_per)
+    # each network's lag: the median of its templates' own lags (sample of 128)
+    samp = np.concatenate([np.arange(r * n_per, r * n_per + min(128, n_per)) for r in range(R)])
+    ts = torch.zeros((len(samp), K), dtype=torch.complex64, device="cuda")
+    ls = torch.zeros(len(samp), dtype=torch.int32, device="cuda")
+    ss = torch.zeros(len(samp), dtype=torch.float64, device="cuda")
+    rfd.make_taps(ctx, grid, psd, bank.ref_params(), P[samp], ro[samp], np.full(len(samp), K), K, cfg.tukey_alpha,
+                  ts, ls, ss, stream=stream)
+    lown = ls.cpu().numpy()
+    lag = np.array([int(np.median(lown[ro[samp] == r])) for r in range(R)], dtype=np.int32)
+    # training targets: exact taps at the network's lag
+    T = torch.zeros((len(P), K), dtype=torch.complex64, device="cuda")
+    sT = torch.zeros(len(P), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rfd.make_taps_at_lag(ctx, grid, psd, bank.ref_params(), P, ro, np.full(len(P), K), lag[ro], K, cfg.tukey_alpha,
+                         T, sT, stream=stream)
+    torch.cuda.synchronize()
+    rep["targets_s"] = time.perf_counter() - t0
+    rep["n_train"] = int(len(P))
+    # standardisation of the physical inputs: mean and spread of (Mc, eta, chi_eff, Lambda~) per network
+    M = P[:, 0] + P[:, 1]
+    eta = P[:, 0] * P[:, 1] / M ** 2
+    feats = np.stack([M * eta ** 0.6, eta, (P[:, 0] * P[:, 2] + P[:, 1] * P[:, 3]) / M, P[:, 4]], axis=1)
+    mu = np.stack([feats[ro == r].mean(axis=0) for r in range(R)])
+    sd = np.stack([np.where(feats[ro == r].std(axis=0) > 0, feats[ro == r].std(axis=0), 1.0) for r in range(R)])
+    Tn = T.cpu().numpy()
+    scale = np.array([float(np.sqrt(np.mean(np.abs(Tn[ro == r]) ** 2))) for r in range(R)])
+    net = rfd.Mlp(ctx, grid, psd, bank.ref_params())
+    net.set_norm(mu, sd, scale, lag)
+    w = []
+    wr = np.random.default_rng(seed + 1)
+    for _ in range(R):
+        parts = []
+        for (o, i) in [(256, 20), (256, 256), (256, 256), (256, 256)]:
+            lim = 1.0 / np.sqrt(i)
+            parts += [wr.uniform(-lim, lim, o * i), wr.uniform(-lim, lim, o)]
+        w.append(np.concatenate(parts))
+    net.set_weights(np.stack(w).astype(np.float32))
+    feat = net.features(P, ro, stream=stream)
+    B = 256
+    spe = n_per // B
+    lr0 = 3e-3
+    idx = torch.empty((spe, R, B), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for ep in range(epochs):
+        perm = np.stack([rng.permutation(n_per)[: spe * B].reshape(spe, B) for _ in range(R)], axis=1)
+        idx.copy_(torch.from_numpy(perm.astype(np.int32)))
+        lr = max(1e-6, lr0 * 0.5 * (1 + np.cos(np.pi * ep / epochs)))
+        for s_ in range(spe):
+            net.train_step(feat, T, n_per, idx[s_], B, lr, stream=stream)
+    loss, steps, lscale = net.state(stream=stream)
+    rep["train_s"] = time.perf_counter() - t0
+    rep["train_steps"] = steps
+    rep["final_loss_median"] = float(np.median(loss))
+    rep["epochs"] = epochs
+    rep["spot_stride"] = spot_stride
+    # the bank: surrogate quality on every template (evaluation), then taps with spot checks
+    J = bank.n_tmpl
+    Pb, rb = bank.params(), bank.ref_of_tmpl
+    ex = torch.zeros((J, K), dtype=torch.complex64, device="cuda")
+    sx = torch.zeros(J, dtype=torch.float64, device="cuda")
+    rfd.make_taps_at_lag(ctx, grid, psd, bank.ref_params(), Pb, rb, np.full(J, K), lag[rb], K, cfg.tukey_alpha,
+                         ex, sx, stream=stream)
+    sur = torch.zeros((J, K), dtype=torch.complex64, device="cuda")
+    lsu = torch.zeros(J, dtype=torch.int32, device="cuda")
+    ssu = torch.zeros(J, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net.infer(Pb, rb, sur, lsu, ssu, stream=stream)
+    torch.cuda.synchronize()
+    rep["infer_s"] = time.perf_counter() - t0
+    m = net.cross_match(rb, sur, ex, stream=stream).cpu().numpy()
+    rep["surrogate_match"] = {"median": float(np.median(m)), "p10": float(np.percentile(m, 10)),
+                              "frac_ge_0p999": float(np.mean(m >= 0.999)), "frac_ge_0p99": float(np.mean(m >= 0.99))}
+    taps = torch.zeros((J, K), dtype=torch.complex64, device="cuda")
+    lagt = torch.zeros(J, dtype=torch.int32, device="cuda")
+    sig = torch.zeros(J, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    source, _, stats = net.learned_taps(psd, Pb, rb, taps, lagt, sig, spot_stride=spot_stride, min_match=0.999,
+                                        alpha=cfg.tukey_alpha, stream=stream)
+    torch.cuda.synchronize()
+    rep["learned_taps_s"] = time.perf_counter() - t0
+    rep["learned_taps_stats"] = stats
+    # the method without the network: exact taps for every template
+    t1 = torch.zeros((J, K), dtype=torch.complex64, device="cuda")
+    l1 = torch.zeros(J, dtype=torch.int32, device="cuda")
+    s1 = torch.zeros(J, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rfd.make_taps(ctx, grid, psd, bank.ref_params(), Pb, rb, np.full(J, K), K, cfg.tukey_alpha, t1, l1, s1,
+                  stream=stream)
+    torch.cuda.synchronize()
+    rep["make_taps_s"] = time.perf_counter() - t0
+    rep["tap_prep_speedup"] = rep["make_taps_s"] / rep["learned_taps_s"]
+    net.close()
+    del t1, l1, s1, ex, sx, sur, lsu, ssu, T, sT, feat
+    return taps, lagt, sig, rep
+
+
 class GpuSearch:
     """Set-up (templates, taps, autotuned plan) and the per-segment search as one CUDA graph."""
 
-    def __init__(self, cfg, bank, data, precision, device, use_graph=True, autotune_cache=None):
+    def __init__(self, cfg, bank, data, precision, device, use_graph=True, autotune_cache=None, learned=None):
+        self.learned = learned
         import torch
         import paper_2601_18835_gb300 as rfd
         from paper_2601_18835_gb300 import autotune
@@ -249,10 +381,17 @@ class GpuSearch:
         kout = torch.zeros(J, dtype=torch.int32, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rfd.make_taps(self.ctx, self.grid, self.psd, bank.ref_params(), bank.params(), bank.ref_of_tmpl,
-                      None if bucketed else np.full(J, cfg.k, dtype=np.int32), k_stride, cfg.tukey_alpha,
-                      self.taps, self.lag, self.sig, self.match, stream=self.stream,
-                      buckets=list(cfg.k_buckets) if bucketed else None, k_out=kout)
+        self.learned_report = None
+        if self.learned is not None:
+            self.taps, self.lag, self.sig, self.learned_report = learned_taps(
+                cfg, bank, self.ctx, self.grid, self.psd, self.stream, **self.learned)
+            self.match = None
+            kout.fill_(k_stride)
+        else:
+            rfd.make_taps(self.ctx, self.grid, self.psd, bank.ref_params(), bank.params(), bank.ref_of_tmpl,
+                          None if bucketed else np.full(J, cfg.k, dtype=np.int32), k_stride, cfg.tukey_alpha,
+                          self.taps, self.lag, self.sig, self.match, stream=self.stream,
+                          buckets=list(cfg.k_buckets) if bucketed else None, k_out=kout)
         torch.cuda.synchronize()
         self.make_taps_s = time.perf_counter() - t0
         self.K = kout.cpu().numpy().astype(np.int32)
@@ -392,8 +531,24 @@ def run_ours(args):
     precision_name = args.precision or "fp16x3"
     prec = PREC[precision_name]
     cfg, bank, data = workload_for_rank(args.config, rank, args.n_tmpl, args.n_ref)
+    learned = None
+    if cfg.lambda_range is not None:          # the learned-tap workload
+        import workload
+        dense_train = None
+        if args.dense_refs:
+            refs = workload.make_bank(dataclasses.replace(cfg, n_ref=args.dense_refs), n_tmpl=max(
+                args.dense_refs * 64, 20000)).ref_params()
+            bank = workload.dense_bank(refs, max(1, bank.n_tmpl // args.dense_refs), 0.002, seed=cfg.seeds[0])
+            dense_train = workload.dense_bank(refs, max(256, args.n_train // args.dense_refs), 0.002,
+                                              seed=5000 + cfg.index)
+            cfg = dataclasses.replace(cfg, name=cfg.name + "_dense%d" % args.dense_refs, n_tmpl=bank.n_tmpl,
+                                      n_ref=bank.n_ref)
+            data = workload.make_data(cfg, bank)
+        learned = {"n_train": args.n_train, "epochs": args.epochs, "dense_train": dense_train,
+                   "spot_stride": args.spot_stride}
     tune_cache = os.path.join(ROOT, "paper_2601_18835_gb300", "_build", "autotune.json")
-    s = GpuSearch(cfg, bank, data, prec, local, use_graph=not args.no_graph, autotune_cache=tune_cache)
+    s = GpuSearch(cfg, bank, data, prec, local, use_graph=not args.no_graph, autotune_cache=tune_cache,
+                  learned=learned)
     J, dur = bank.n_tmpl, cfg.duration
 
     def barrier():
@@ -511,7 +666,7 @@ def run_ours(args):
                          "through the oracle's direct circular FIR (K=%d, n=%d) and triggers, taps "
                          "precomputed: %.1f s of one host core" % (done, cfg.k, cfg.n, el)}
 
-    match = s.match.cpu().numpy()
+    match = s.match.cpu().numpy() if s.match is not None else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -533,10 +688,13 @@ def run_ours(args):
         "graph": {"used": s.search is not None,
                   "kernels_per_step": s.search.kernels_per_run if s.search is not None else None},
         "autotune": {"options": s.options, "candidates_ms": [c["ms"] for c in (s.tuning or {}).get("candidates", [])]},
-        "setup": {"make_taps_s": s.make_taps_s, "taps_match_ge_0p99": float(np.mean(match >= 0.99)),
-                  "taps_match_median": float(np.median(match))},
+        "setup": {"make_taps_s": s.make_taps_s,
+                  "taps_match_ge_0p99": float(np.mean(match >= 0.99)) if match is not None else None,
+                  "taps_match_median": float(np.median(match)) if match is not None else None},
         "triggers_per_step": int(ntrig),
     }
+    if s.learned_report is not None:
+        line["learned_taps"] = s.learned_report
     s.close()
     if rank == 0:
         print(json.dumps(line))
