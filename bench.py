@@ -65,6 +65,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device="cuda"):
+    """The largest of every rank's value (the whole job is as slow as its slowest replica)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, n_tmpl, duration_s, step_s):
+    """Whole-job template-seconds per second: every rank filters its own segment with the
+    full bank (replicas, weak scaling), so the job does ws x n_tmpl x duration per step."""
+    return ws * n_tmpl * duration_s / step_s
+
+
 # ------------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
@@ -583,11 +598,8 @@ def run_ours(args):
     launches = rfd.kernel_launches() - l0
     clk = clocks.stop(w0, w1)
     ms = sum(step_ms) / len(step_ms)
-    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = ws * J * dur / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, ws)
+    value = job_rate(ws, J, dur, ms_max / 1e3)
 
     # end to end through host buffers
     for _ in range(2):
@@ -601,10 +613,7 @@ def run_ours(args):
         nt = s.step_e2e()
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = torch.tensor([sum(e2e_t) / len(e2e_t)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(e2e_s, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = ws * J * dur / float(e2e_s.item())
+    e2e_value = job_rate(ws, J, dur, max_over_ranks(sum(e2e_t) / len(e2e_t), ws))
 
     # roofline of the dominant kernel: the ratio-filter contraction
     peaks, peak_kind = measured_peaks()
