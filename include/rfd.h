@@ -212,9 +212,13 @@ typedef struct {
     int32_t mix_k;        /* 1: a tile may hold templates whose K differ (padded to the largest);
                              0: tiles also split where the number of 16-tap steps changes */
     int32_t grid_ctas;    /* persistent CTAs of the tensor-core kernel, 0 = one per SM */
-    int32_t reserved[3];  /* must be 0 */
+    int32_t long_k;       /* templates with K > long_k go to the long-tap kernel (64 templates
+                             on the MMA's M side, 256 output positions on its N side, taps
+                             streamed, so every MMA is full width for any K <= 512): 0 = every
+                             template, 512 = none (tile_nt[1], tile_nt[2] then apply) */
+    int32_t reserved[2];  /* must be 0 */
 } rfd_plan_options;
-/* Fills the defaults: tile_nt = {128, 64, 32}, mix_k = 1, grid_ctas = 0. */
+/* Fills the defaults: tile_nt = {128, 64, 32}, mix_k = 1, grid_ctas = 0, long_k = 128. */
 void rfd_plan_options_default(rfd_plan_options *options);
 /* rfd_plan_create with explicit tile choices (NULL = defaults). */
 rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,

@@ -150,7 +150,7 @@ class Plan:
     """One bank's ratio-filter schedule (templates tiled per reference) and packed taps."""
 
     def __init__(self, ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, options=None):
-        """options: dict with any of tile_nt (3 ints), mix_k (0/1), grid_ctas (int)."""
+        """options: dict with any of tile_nt (3 ints), mix_k (0/1), grid_ctas (int), long_k (int)."""
         ro, rop = _i32_host(ref_of)
         kk, kp = _i32_host(k)
         h = ctypes.c_void_p()
@@ -165,6 +165,8 @@ class Plan:
                 opt.mix_k = int(options["mix_k"])
             if "grid_ctas" in options:
                 opt.grid_ctas = int(options["grid_ctas"])
+            if "long_k" in options:
+                opt.long_k = int(options["long_k"])
         check(_lib().rfd_plan_create_ex(ctx.handle, ctypes.byref(g), int(n_ref), len(ro), rop, kp,
                                         int(precision), int(window), float(threshold), int(halo),
                                         ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))

@@ -35,7 +35,7 @@ class Grid(ctypes.Structure):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("tile_nt", ctypes.c_int32 * 3), ("mix_k", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("long_k", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Params(ctypes.Structure):

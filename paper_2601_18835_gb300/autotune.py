@@ -1,8 +1,9 @@
 """Autotuner for the tensor-core ratio filter: picks the plan's tile choices by timing them.
 
 The choices (rfd_plan_options): templates per tile for each K class, whether a tile may mix
-templates of different K (padding the short ones) or must split where K changes, and the
-number of persistent CTAs.  Each candidate plan is built through the C ABI, given the bank's
+templates of different K (padding the short ones) or must split where K changes, the number
+of persistent CTAs, and above which K templates go to the long-tap kernel (templates on the
+MMA's M side, time on its N side).  Each candidate plan is built through the C ABI, given the bank's
 taps, and timed on the q_ref buffer with CUDA events; the fastest wins.  Results are cached
 in a JSON file keyed by the workload's signature (grid, precision, the (reference, K)
 histogram, the device), so a bank is tuned once.
@@ -21,7 +22,9 @@ DEFAULT_CANDIDATES = [
     {"mix_k": 0},
     {"mix_k": 1, "tile_nt": [64, 64, 32]},
     {"mix_k": 0, "tile_nt": [64, 64, 32]},
-    {"mix_k": 1, "grid_ctas": 0},
+    {"mix_k": 1, "long_k": 512},
+    {"mix_k": 1, "long_k": 64},
+    {"mix_k": 1, "long_k": 0},
 ]
 
 

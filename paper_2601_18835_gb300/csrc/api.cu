@@ -23,6 +23,12 @@ rfd_status fir32_launch(const rfd_plan *, const float2 *, rfd_candidate *, int64
 rfd_status pack_taps_fp32(rfd_plan *, const float2 *, int32_t, const int32_t *, const double *,
                           cudaStream_t);
 rfd_status tc_pack(rfd_plan *, const float2 *, int32_t, const int32_t *, const double *, cudaStream_t);
+rfd_status tl_pack(rfd_plan *, const float2 *, int32_t, const int32_t *, const double *, cudaStream_t);
+rfd_status tl_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
+                     cudaStream_t);
+uint32_t tl_ystride(int32_t kpad_max);
+int tl_rows_per_item();
+int tl_tile_templates();
 rfd_status tc_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
                      cudaStream_t);
 int tc_rows_per_item();
@@ -35,12 +41,89 @@ static int32_t tc_nt_cap(const rfd_plan_options &o, int32_t kpad) {
     return kpad <= 128 ? o.tile_nt[0] : (kpad <= 256 ? o.tile_nt[1] : o.tile_nt[2]);
 }
 
-static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &order, int num_sms,
+// Cost-balanced contiguous item ranges (one per CTA) over tiles of n_it items each, an item of
+// tile t costing cost[t].
+static std::vector<int64_t> balanced_ranges(const std::vector<double> &cost, int64_t n_it, int64_t G) {
+    const int64_t ntiles = (int64_t)cost.size();
+    const int64_t total_items = ntiles * n_it;
+    std::vector<double> prefix(ntiles + 1, 0.0);
+    for (int64_t t = 0; t < ntiles; ++t) prefix[t + 1] = prefix[t] + cost[t] * n_it;
+    std::vector<int64_t> ranges(G + 1, 0);
+    ranges[G] = total_items;
+    int64_t t = 0;
+    for (int64_t g = 1; g < G; ++g) {
+        const double target = prefix[ntiles] * (double)g / (double)G;
+        while (t + 1 < ntiles && prefix[t + 1] <= target) ++t;
+        int64_t within = (int64_t)((target - prefix[t]) / cost[t]);
+        within = std::min<int64_t>(std::max<int64_t>(within, 0), n_it);
+        ranges[g] = std::max(ranges[g - 1], t * n_it + within);
+    }
+    return ranges;
+}
+
+// Long-tap tiles: per reference, up to 64 templates with K > long_k (mix_k as for the other
+// kernel); appended to the plan's slot order.
+static rfd_status plan_tl_tiles(rfd_plan *p, const std::vector<int32_t> &order, int num_sms,
+                                const rfd_plan_options &opt) {
+    const int64_t n_tb = p->grid.n / tl_rows_per_item();
+    const int32_t nt = tl_tile_templates();
+    int64_t taps_off = 0;
+    int32_t kpad_max = 0;
+    size_t i = 0;
+    while (i < order.size()) {
+        const int32_t r = p->ref_of[order[i]];
+        TcTile t{};
+        t.ref = r;
+        t.first = (int32_t)p->perm.size();
+        while (i < order.size() && p->ref_of[order[i]] == r && t.count < nt) {
+            const int32_t kt = std::max(t.k_tile, p->k_of[order[i]]);
+            if (!opt.mix_k && t.count > 0 && (kt + 15) / 16 != (t.k_tile + 15) / 16) break;
+            t.k_tile = kt;
+            ++t.count;
+            p->perm.push_back(order[i]);
+            ++i;
+        }
+        t.nk16 = (t.k_tile + 15) / 16;
+        t.kpad = 16 * t.nk16;
+        t.nt = nt;
+        t.nch = (t.kpad + 63) / 64;
+        t.taps_bytes = t.nch * 2 * 3 * nt * 128;
+        t.taps_off = taps_off;
+        taps_off += t.taps_bytes;
+        kpad_max = std::max(kpad_max, t.kpad);
+        p->tl_tiles.push_back(t);
+        p->executed_flops += (double)n_tb * t.nk16 * 6.0 * 2.0 * 128.0 * (double)tl_rows_per_item() * 16.0;
+    }
+    const int64_t ntiles = (int64_t)p->tl_tiles.size();
+    if (ntiles == 0) return RFD_OK;
+    RFD_REQUIRE(p->ld >= p->grid.n + kpad_max, RFD_ERR_SHAPE,
+                "tensor-core path reads %d taps past each block: halo=%d too small (need >= %d)", kpad_max,
+                p->halo, kpad_max - 1);
+    p->tl_ystride = tl_ystride(kpad_max);
+    std::vector<double> cost(ntiles);
+    for (int64_t t = 0; t < ntiles; ++t) cost[t] = (double)p->tl_tiles[t].nk16 * 6.0 + 2.0;
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(opt.grid_ctas > 0 ? opt.grid_ctas : num_sms,
+                                                           ntiles * n_tb));
+    const std::vector<int64_t> ranges = balanced_ranges(cost, n_tb, G);
+    p->tl_grid = (int32_t)G;
+    RFD_TRY(ensure(p->d_tl_ranges, (G + 1) * sizeof(int64_t)));
+    RFD_TRY_CUDA(cudaMemcpy(p->d_tl_ranges.p, ranges.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    RFD_TRY(ensure(p->d_tl_taps, (size_t)taps_off));
+    RFD_TRY(ensure(p->d_tl_tiles, ntiles * sizeof(TcTile)));
+    RFD_TRY_CUDA(
+        cudaMemcpy(p->d_tl_tiles.p, p->tl_tiles.data(), ntiles * sizeof(TcTile), cudaMemcpyHostToDevice));
+    return RFD_OK;
+}
+
+static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &all, int num_sms,
                                 const rfd_plan_options &opt) {
     const int64_t n_tt = p->grid.n / tc_rows_per_item();
     int64_t taps_off = 0;
     int32_t kpad_max = 0;
     uint32_t cap = 0;
+    const int32_t long_k = opt.long_k;
+    std::vector<int32_t> order, order_long;
+    for (int32_t j : all) (p->k_of[j] > long_k ? order_long : order).push_back(j);
     size_t i = 0;
     while (i < order.size()) {
         const int32_t r = p->ref_of[order[i]];
@@ -69,32 +152,21 @@ static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &order, 
         p->tc_tiles.push_back(t);
         p->executed_flops += (double)n_tt * t.nk16 * 6.0 * 2.0 * 128.0 * (2.0 * t.nt) * 16.0;
     }
-    p->n_slots = (int64_t)p->perm.size();
     p->tc_taps_cap = (cap + 1023u) / 1024u * 1024u;
     p->tc_win = (uint32_t)(128 + kpad_max + 8);
     RFD_REQUIRE(p->ld >= p->grid.n + kpad_max, RFD_ERR_SHAPE,
                 "tensor-core path reads %d taps past each block: halo=%d too small (need >= %d)", kpad_max,
                 p->halo, kpad_max - 1);
-    // cost-balanced contiguous item ranges, one per CTA
+    RFD_TRY(plan_tl_tiles(p, order_long, num_sms, opt));
+    p->n_slots = (int64_t)p->perm.size();
     const int64_t ntiles = (int64_t)p->tc_tiles.size();
-    const int64_t total_items = ntiles * n_tt;
-    std::vector<double> cost(ntiles), prefix(ntiles + 1, 0.0);
-    for (int64_t t = 0; t < ntiles; ++t) {
-        cost[t] = (double)p->tc_tiles[t].nk16 * 6.0 + 2.0;   // MMAs cost the same for any N <= 256
-        prefix[t + 1] = prefix[t] + cost[t] * n_tt;
-    }
+    if (ntiles == 0) return RFD_OK;
+    // cost-balanced contiguous item ranges, one per CTA (MMAs cost the same for any N <= 256)
+    std::vector<double> cost(ntiles);
+    for (int64_t t = 0; t < ntiles; ++t) cost[t] = (double)p->tc_tiles[t].nk16 * 6.0 + 2.0;
     const int64_t G = std::max<int64_t>(1, std::min<int64_t>(opt.grid_ctas > 0 ? opt.grid_ctas : num_sms,
-                                                           total_items));
-    std::vector<int64_t> ranges(G + 1, 0);
-    ranges[G] = total_items;
-    int64_t t = 0;
-    for (int64_t g = 1; g < G; ++g) {
-        const double target = prefix[ntiles] * (double)g / (double)G;
-        while (t + 1 < ntiles && prefix[t + 1] <= target) ++t;
-        int64_t within = (int64_t)((target - prefix[t]) / cost[t]);
-        within = std::min<int64_t>(std::max<int64_t>(within, 0), n_tt);
-        ranges[g] = std::max(ranges[g - 1], t * n_tt + within);
-    }
+                                                           ntiles * n_tt));
+    const std::vector<int64_t> ranges = balanced_ranges(cost, n_tt, G);
     p->tc_grid = (int32_t)G;
     RFD_TRY(ensure(p->d_ranges, (G + 1) * sizeof(int64_t)));
     RFD_TRY_CUDA(cudaMemcpy(p->d_ranges.p, ranges.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
@@ -387,6 +459,7 @@ void rfd_plan_options_default(rfd_plan_options *o) {
     o->tile_nt[2] = 32;
     o->mix_k = 1;
     o->grid_ctas = 0;
+    o->long_k = 128;
 }
 
 rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
@@ -402,6 +475,8 @@ rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref,
             RFD_REQUIRE(opt.tile_nt[c] >= 16 && opt.tile_nt[c] <= cap[c] && opt.tile_nt[c] % 16 == 0, RFD_ERR_ARG,
                         "tile_nt[%d]=%d must be a multiple of 16 in [16, %d]", c, opt.tile_nt[c], cap[c]);
         RFD_REQUIRE(opt.grid_ctas >= 0, RFD_ERR_ARG, "grid_ctas must be >= 0");
+        RFD_REQUIRE(opt.long_k >= 0 && opt.long_k <= 512, RFD_ERR_ARG, "long_k must be in [0, 512]");
+        RFD_REQUIRE(opt.reserved[0] == 0 && opt.reserved[1] == 0, RFD_ERR_ARG, "reserved options must be 0");
     }
     RFD_REQUIRE(ctx && out, RFD_ERR_ARG, "NULL ctx or out");
     *out = nullptr;
@@ -532,6 +607,9 @@ void rfd_plan_destroy(rfd_plan *plan) {
     release(plan->d_scale);
     release(plan->d_kslot);
     release(plan->d_ranges);
+    release(plan->d_tl_tiles);
+    release(plan->d_tl_ranges);
+    release(plan->d_tl_taps);
     delete plan;
 }
 
@@ -543,8 +621,10 @@ rfd_status rfd_plan_set_taps(rfd_plan *plan, const void *taps_dev, int32_t k_str
     RFD_TRY_CUDA(cudaSetDevice(plan->ctx->device));
     if (plan->precision == RFD_PREC_FP32)
         RFD_TRY(pack_taps_fp32(plan, (const float2 *)taps_dev, k_stride, lag_dev, sigma_dev, (cudaStream_t)stream));
-    else
+    else {
         RFD_TRY(tc_pack(plan, (const float2 *)taps_dev, k_stride, lag_dev, sigma_dev, (cudaStream_t)stream));
+        RFD_TRY(tl_pack(plan, (const float2 *)taps_dev, k_stride, lag_dev, sigma_dev, (cudaStream_t)stream));
+    }
     plan->taps_set = true;
     return RFD_OK;
 }
@@ -562,7 +642,8 @@ rfd_status rfd_ratio_filter_batch(rfd_plan *plan, const void *qref_dev, const in
     RFD_TRY_CUDA(cudaMemsetAsync(cand_count_dev, 0, sizeof(int64_t), s));
     if (plan->precision == RFD_PREC_FP32)
         return fir32_launch(plan, (const float2 *)qref_dev, cand_dev, cand_capacity, cand_count_dev, s);
-    return tc_launch(plan, qref_dev, qscale_dev, cand_dev, cand_capacity, cand_count_dev, s);
+    RFD_TRY(tc_launch(plan, qref_dev, qscale_dev, cand_dev, cand_capacity, cand_count_dev, s));
+    return tl_launch(plan, qref_dev, qscale_dev, cand_dev, cand_capacity, cand_count_dev, s);
 }
 
 double rfd_plan_executed_flops(const rfd_plan *plan) { return plan ? plan->executed_flops : 0.0; }

@@ -183,6 +183,11 @@ struct rfd_plan {
     bool taps_set = false;
     // tensor-core path
     std::vector<TcTile> tc_tiles;
+    // long-tap kernel (rf_tc_long.cu): tiles of 64 templates, items of 256 outputs
+    std::vector<TcTile> tl_tiles;
+    rfd::DevBuf d_tl_tiles, d_tl_ranges, d_tl_taps;
+    int32_t tl_grid = 0;
+    uint32_t tl_ystride = 0;
     rfd::DevBuf d_ranges;            // int64 [tc_grid + 1] item ranges per CTA
     uint32_t tc_taps_cap = 0, tc_win = 0;
     int32_t tc_grid = 0;

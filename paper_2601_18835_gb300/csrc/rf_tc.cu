@@ -447,6 +447,7 @@ rfd_status tc_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const i
 
 rfd_status tc_launch(const rfd_plan *plan, const void *q, const int32_t *qscale, rfd_candidate *cand, int64_t cap,
                      int64_t *count, cudaStream_t s) {
+    if (plan->tc_tiles.empty()) return RFD_OK;
     TcArgs a;
     a.tiles = (const TcTile *)plan->d_tiles.p;
     a.ranges = (const int64_t *)plan->d_ranges.p;

@@ -1,0 +1,500 @@
+// Tensor-core ratio filter for long taps (K > 128), sm_103a: templates on the MMA's M side,
+// time on its N side.
+//
+// For a tile of 64 templates of one reference and one item of 256 output positions
+// u0 .. u0+255:
+//   D[row, u] = sum_k A[row, k] q[u0 + u + k]      (Eq. 3 with P = reversed, scaled taps)
+// with rows 0..63 the real parts and rows 64..127 the imaginary parts of the 64 templates:
+//   D = [Pr; Pi] Qr^T + [-Pi; Pr] Qi^T,
+// each as three products hi*hi + hi*lo + lo*hi of the FP16 (BF16) splits, FP32 accumulation in
+// tensor memory.  The taps image holds the rows [-Pi; Pr; Pi] once, so the two A operands are
+// its rows 0..127 and 64..191; every MMA is M = 128, N = 256, K = 16 (full rate).
+//
+// The time operand B[u, k] = q[u0 + u + k] is a Hankel matrix.  It is not materialised:
+// shared memory holds Y[r] = q[u0 + r .. u0 + r + 7] (16 bytes per row, an eight-fold copy of
+// the q window) and the MMA reads it through a K-major, non-swizzled descriptor whose
+// K-direction and N-direction strides are both 128 bytes, so that element (u, k) lands on
+// Y[u + k - k mod 8][k mod 8] = q[u0 + u + k].  The taps (A) stream through shared memory in
+// 64-tap chunks by bulk copies; two accumulators in tensor memory let the epilogue drain one
+// item while the MMAs fill the next.
+//
+// Roles: warp 0 bulk copies, warp 1 issues the MMAs (and owns the TMEM allocation), warps
+// 4-7 build Y, warps 8-15 drain: a warp of lane quarter 2/3 (imaginary rows) hands its values
+// to the warp of quarter 0/1 (real rows, same templates) through shared memory, which forms
+// z, |z|^2 and the per-window maxima.  Every wait is bounded.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace rfd {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kN = 256;                 // output positions per item (MMA N)
+constexpr int kNT = 64;                 // templates per tile
+constexpr int kThreads = 512;
+constexpr int kAStages = 2;
+constexpr uint32_t kChunkImg = 3u * kNT * 128u;      // one 64-tap chunk, hi or lo: 24 KB
+constexpr uint32_t kChunkBytes = 2u * kChunkImg;     // hi + lo: 48 KB
+constexpr uint32_t kSpin = 1u << 22;
+
+enum {
+    kBarAFull = 0,      // kAStages
+    kBarAEmpty = 2,     // kAStages
+    kBarYFull = 4,      // 2
+    kBarYEmpty = 6,     // 2
+    kBarDFull = 8,      // 2
+    kBarDEmpty = 10,    // 2
+    kBarDone = 12,
+    kNumBars = 13
+};
+
+struct TlArgs {
+    const TcTile *tiles;
+    const int64_t *ranges;      // [gridDim.x + 1] item ranges
+    int64_t n_tb;               // time blocks per tile = n / 256
+    const uint8_t *taps;        // operand images
+    const uint16_t *q;          // q planes (fp16 or bf16 bits)
+    int64_t ld;
+    const int32_t *qscale;
+    const int32_t *perm;
+    const int32_t *off;
+    const float *scale;
+    int64_t n;
+    float thr;
+    uint32_t W;
+    rfd_candidate *cand;
+    int64_t cap;
+    unsigned long long *count;
+    uint32_t ystride;           // bytes per Y plane
+};
+
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag,
+                                         unsigned long long *count) {
+    for (uint32_t i = 0; i < kSpin; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1u;
+    atomicOr(count, 1ull << 62);   // reported as RFD_ERR_TIMEOUT by find_triggers
+    return false;
+}
+
+// Shared-memory descriptor of the Hankel operand: K-major, no swizzle, LBO = SBO = 128 B.
+__device__ __forceinline__ uint64_t desc_hankel(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(128 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Appends one candidate (thread-level; every float compare is on the p formed by the caller).
+__device__ __forceinline__ void emit_one(uint32_t j, uint32_t w, uint32_t pbits, uint32_t t, float zr, float zi,
+                                         rfd_candidate *__restrict__ cand, int64_t cap,
+                                         unsigned long long *__restrict__ count) {
+    const unsigned long long idx = atomicAdd(count, 1ull);
+    if ((int64_t)idx < cap) {
+        rfd_candidate c;
+        c.key = ((uint64_t)pbits << 32) | (uint64_t)(0xffffffffu - t);
+        c.j = j;
+        c.w = w;
+        c.zr = zr;
+        c.zi = zi;
+        cand[idx] = c;
+    }
+}
+
+template <int BF16>
+__global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *s_a = sm;                                              // kAStages x 48 KB
+    uint8_t *s_y = sm + kAStages * kChunkBytes;                     // 2 buffers x 4 planes
+    float *s_x = (float *)(s_y + 2u * 4u * A.ystride);              // 4 pairs x 2 x 32 x 33
+    uint64_t *bars = (uint64_t *)(s_x + 4 * 2 * 32 * 33);
+    uint32_t *s_misc = (uint32_t *)(bars + kNumBars);
+    volatile uint32_t *abort_flag = &s_misc[1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t it0 = A.ranges[blockIdx.x], it1 = A.ranges[blockIdx.x + 1];
+    const uint32_t bar0 = smem_u32(bars);
+#define BAR(i) (bar0 + 8u * (uint32_t)(i))
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kAStages; ++s) {
+            mbar_init(BAR(kBarAFull + s), 1);
+            mbar_init(BAR(kBarAEmpty + s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(BAR(kBarYFull + b), 4);
+            mbar_init(BAR(kBarYEmpty + b), 1);
+            mbar_init(BAR(kBarDFull + b), 1);
+            mbar_init(BAR(kBarDEmpty + b), 8);
+        }
+        mbar_init(BAR(kBarDone), 1);
+        s_misc[1] = 0u;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(smem_u32(&s_misc[0]), 512);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_misc[0];
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer: taps chunks
+        if (lane == 0) {
+            uint32_t ka = 0;
+            for (int64_t it = it0; it < it1; ++it) {
+                const TcTile T = A.tiles[it / A.n_tb];
+                bool ok = true;
+                for (int c = 0; c < T.nch; ++c, ++ka) {
+                    const uint32_t st = ka % kAStages, r = ka / kAStages;
+                    if (!wait_bar(BAR(kBarAEmpty + st), (r & 1u) ^ 1u, abort_flag, A.count)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(BAR(kBarAFull + st), kChunkBytes);
+                    const uint8_t *src = A.taps + T.taps_off + (int64_t)c * kChunkBytes;
+                    bulk_g2s(smem_u32(s_a + st * kChunkBytes), src, kChunkImg, BAR(kBarAFull + st));
+                    bulk_g2s(smem_u32(s_a + st * kChunkBytes) + kChunkImg, src + kChunkImg, kChunkImg,
+                             BAR(kBarAFull + st));
+                }
+                if (!ok) break;
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t ka = 0, li = 0;
+            const uint32_t idn = idesc_f16(128, kN, BF16, 0);
+            const uint32_t a_base = smem_u32(s_a), y_base = smem_u32(s_y);
+            for (int64_t it = it0; it < it1; ++it, ++li) {
+                const TcTile T = A.tiles[it / A.n_tb];
+                const uint32_t acc = li & 1u, yb = li & 1u, use = li >> 1;
+                if (!wait_bar(BAR(kBarDEmpty + acc), (use & 1u) ^ 1u, abort_flag, A.count)) break;
+                if (!wait_bar(BAR(kBarYFull + yb), use & 1u, abort_flag, A.count)) break;
+                fence_after();
+                const uint32_t d = tmem + acc * (uint32_t)kN;
+                const uint32_t y0 = y_base + yb * 4u * A.ystride;
+                bool ok = true;
+                for (int c = 0; c < T.nch; ++c, ++ka) {
+                    const uint32_t st = ka % kAStages, r = ka / kAStages;
+                    if (!wait_bar(BAR(kBarAFull + st), r & 1u, abort_flag, A.count)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t ah = a_base + st * kChunkBytes, al = ah + kChunkImg;
+                    const int s_end = min(4, T.nk16 - 4 * c);
+                    for (int s = 0; s < s_end; ++s) {
+                        const uint32_t o = (uint32_t)s * 32u;
+                        const uint64_t A2h = desc_sw128(ah + o), A2l = desc_sw128(al + o);               // [-Pi; Pr]
+                        const uint64_t A1h = desc_sw128(ah + kNT * 128u + o), A1l = desc_sw128(al + kNT * 128u + o);  // [Pr; Pi]
+                        const uint32_t yk = y0 + (uint32_t)(64 * c + 16 * s) * 16u;
+                        const uint64_t Qrh = desc_hankel(yk), Qih = desc_hankel(yk + A.ystride);
+                        const uint64_t Qrl = desc_hankel(yk + 2u * A.ystride), Qil = desc_hankel(yk + 3u * A.ystride);
+                        const uint32_t first = (c == 0 && s == 0) ? 0u : 1u;
+                        // the products and their order match the other kernel's (q_h p_h, q_h p_l,
+                        // q_l p_h per plane), so both give bit-identical sums
+                        mma_ss(d, A1h, Qrh, idn, first);
+                        mma_ss(d, A1l, Qrh, idn, 1u);
+                        mma_ss(d, A1h, Qrl, idn, 1u);
+                        mma_ss(d, A2h, Qih, idn, 1u);
+                        mma_ss(d, A2l, Qih, idn, 1u);
+                        mma_ss(d, A2h, Qil, idn, 1u);
+                    }
+                    mma_commit(BAR(kBarAEmpty + st));
+                }
+                if (!ok) break;
+                mma_commit(BAR(kBarDFull + acc));
+                mma_commit(BAR(kBarYEmpty + yb));
+            }
+            // every MMA this thread issued has completed before TMEM is released
+            mma_commit(BAR(kBarDone));
+            for (uint32_t i = 0; i < kSpin && !mbar_try_wait(BAR(kBarDone), 0); ++i) {
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ------------------------------------------------------------ Y builders
+        const int bt = (warp - 4) * 32 + lane;          // 0..127
+        uint32_t li = 0;
+        for (int64_t it = it0; it < it1; ++it, ++li) {
+            const int64_t ti = it / A.n_tb, tb = it - ti * A.n_tb;
+            const TcTile T = A.tiles[ti];
+            const uint32_t yb = li & 1u, use = li >> 1;
+            bool ok = wait_bar(BAR(kBarYEmpty + yb), (use & 1u) ^ 1u, abort_flag, A.count);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const int groups = (kN - 8 + T.kpad) / 8;  // rows 0 .. 248 + kpad - 1 in groups of 8
+            uint8_t *y0 = s_y + yb * 4u * A.ystride;
+            for (int g = bt; g < 4 * groups; g += 128) {
+                const int p = g / groups, gr = g - p * groups;
+                const uint16_t *src = A.q + (int64_t)(4 * T.ref + p) * A.ld + tb * kN + 8 * gr;
+                const uint4 lo = *(const uint4 *)src, hi = *(const uint4 *)(src + 8);
+                const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+                uint4 *dst = (uint4 *)(y0 + p * A.ystride + (uint32_t)(8 * gr) * 16u);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    uint4 v;
+                    if ((i & 1) == 0) {
+                        v = make_uint4(w[i / 2], w[i / 2 + 1], w[i / 2 + 2], w[i / 2 + 3]);
+                    } else {
+                        const int b = i / 2;
+                        v = make_uint4(__funnelshift_r(w[b], w[b + 1], 16), __funnelshift_r(w[b + 1], w[b + 2], 16),
+                                       __funnelshift_r(w[b + 2], w[b + 3], 16), __funnelshift_r(w[b + 3], w[b + 4], 16));
+                    }
+                    dst[i] = v;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(BAR(kBarYFull + yb));
+        }
+    } else if (warp >= 8) {
+        // ------------------------------------------------------------ epilogue (pairs)
+        const uint32_t lq = (uint32_t)warp & 3u;             // TMEM lane quarter
+        const int half = (warp - 8) >> 2;                    // which 128 of the 256 columns
+        const bool is_re = lq < 2u;
+        const int pair = (int)(lq & 1u) + 2 * half;
+        float *X = s_x + pair * 2 * 32 * 33;
+        const uint32_t tlane = (lq * 32u) << 16;
+        uint32_t li = 0, xb = 0;
+        for (int64_t it = it0; it < it1; ++it, ++li) {
+            const int64_t ti = it / A.n_tb, tb = it - ti * A.n_tb;
+            const TcTile T = A.tiles[ti];
+            const uint32_t acc = li & 1u, use = li >> 1;
+            const bool ok = wait_bar(BAR(kBarDFull + acc), use & 1u, abort_flag, A.count);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            fence_after();
+            // this thread's template (real warps): a = 32 (quarter & 1) + lane
+            const int a = 32 * (int)(lq & 1u) + lane;
+            const bool valid = a < T.count;
+            const int64_t slot = (int64_t)T.first + (valid ? a : 0);
+            const float sc = valid && is_re ? A.scale[slot] * ldexpf(1.0f, -A.qscale[T.ref]) : 0.f;
+            const int32_t j = valid && is_re ? A.perm[slot] : 0;
+            const int32_t o = valid && is_re ? A.off[slot] : 0;
+            for (int cc = 0; cc < 4; ++cc, xb ^= 1u) {
+                const uint32_t c0 = (uint32_t)(half * 128 + cc * 32);
+                uint32_t v[32];
+                tmem_ld32(tmem + tlane + acc * (uint32_t)kN + c0, v);
+                tmem_ld_wait();
+                float *Xb = X + xb * 32 * 33;
+                if (!is_re) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) Xb[lane * 33 + i] = __uint_as_float(v[i]);
+                }
+                if (cc == 3) {
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(BAR(kBarDEmpty + acc));
+                }
+                named_sync(1u + (uint32_t)pair, 64u);
+                if (is_re && valid) {
+                    // z, |z|^2, threshold and the running maximum of each window along u
+                    uint32_t bw = 0xffffffffu, bp = 0u, bt = 0u;
+                    float bzr = 0.f, bzi = 0.f;
+                    const int64_t u0 = tb * kN + c0;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float zr = __fmul_rn(__uint_as_float(v[i]), sc);
+                        const float zi = __fmul_rn(Xb[lane * 33 + i], sc);
+                        const float p = __fadd_rn(__fmul_rn(zr, zr), __fmul_rn(zi, zi));
+                        if (p > A.thr) {
+                            const uint32_t t = (uint32_t)((u0 + i + o) & (A.n - 1));
+                            const uint32_t w = t / A.W;
+                            if (w != bw) {
+                                if (bw != 0xffffffffu) emit_one((uint32_t)j, bw, bp, bt, bzr, bzi, A.cand, A.cap, A.count);
+                                bw = w;
+                                bp = 0u;
+                            }
+                            const uint32_t pb = __float_as_uint(p);
+                            // ties keep the earlier (smaller) t
+                            if (pb > bp || (pb == bp && t < bt)) {
+                                bp = pb;
+                                bt = t;
+                                bzr = zr;
+                                bzi = zi;
+                            }
+                        }
+                    }
+                    if (bw != 0xffffffffu) emit_one((uint32_t)j, bw, bp, bt, bzr, bzi, A.cand, A.cap, A.count);
+                }
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc(tmem, 512);
+    }
+#undef BAR
+}
+
+// ------------------------------------------------------------------ taps packing
+template <typename H> __device__ __forceinline__ uint16_t hbits(H x);
+template <> __device__ __forceinline__ uint16_t hbits<__half>(__half x) { return __half_as_ushort(x); }
+template <> __device__ __forceinline__ uint16_t hbits<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat16_as_ushort(x); }
+template <typename H> __device__ __forceinline__ H toh(float x);
+template <> __device__ __forceinline__ __half toh<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 toh<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ float fromh(__half x) { return __half2float(x); }
+__device__ __forceinline__ float fromh(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// One block per tile: per-template power-of-two scale (max |component| * 2^e < 2^8), then the
+// A-operand image [chunk][hl][row][128 B], rows [-Pi (64); Pr (64); Pi (64)]; element e of
+// chunk c holds reversed tap k = 64 c + e, 16-byte units XOR-swizzled by row % 8.  Also the
+// per-slot lag offset and normalisation.
+template <typename H>
+__global__ void __launch_bounds__(256) k_pack_tl(const TcTile *__restrict__ tiles, const float2 *__restrict__ taps,
+                                                 int32_t k_stride, const int32_t *__restrict__ perm,
+                                                 const int32_t *__restrict__ kslot, const int32_t *__restrict__ lag,
+                                                 const double *__restrict__ sigma, int64_t n,
+                                                 uint8_t *__restrict__ out, int32_t *__restrict__ off,
+                                                 float *__restrict__ scale) {
+    __shared__ int s_exp[kNT], s_j[kNT], s_k[kNT];
+    const TcTile T = tiles[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int a = warp; a < kNT; a += (int)(blockDim.x >> 5)) {
+        float mx = 0.f;
+        int j = 0, K = 0;
+        if (a < T.count) {
+            j = perm[T.first + a];
+            K = kslot[T.first + a];
+            for (int k = lane; k < K; k += 32) {
+                const float2 v = taps[(int64_t)j * k_stride + k];
+                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) {
+            int e = 0;
+            if (mx > 0.f) {
+                int ex;
+                frexpf(mx, &ex);
+                e = 8 - ex;
+            }
+            s_exp[a] = e;
+            s_j[a] = j;
+            s_k[a] = K;
+        }
+    }
+    __syncthreads();
+    const int rows = 3 * kNT;
+    const int64_t total = (int64_t)T.nch * 2 * rows * 64;
+    uint8_t *img = out + T.taps_off;
+    for (int64_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int e = (int)(idx & 63);
+        const int64_t r1 = idx >> 6;
+        const int row = (int)(r1 % rows);
+        const int64_t r2 = r1 / rows;
+        const int hl = (int)(r2 & 1);
+        const int c = (int)(r2 >> 1);
+        const int a = row % kNT, part = row / kNT;     // 0: -Pi, 1: Pr, 2: Pi
+        const int k = 64 * c + e;
+        uint16_t bits = 0;
+        if (a < T.count && k < s_k[a]) {
+            const float2 v = taps[(int64_t)s_j[a] * k_stride + (s_k[a] - 1 - k)];
+            const float comp = part == 1 ? v.x : (part == 2 ? v.y : -v.y);
+            const float x = ldexpf(comp, s_exp[a]);
+            const H hi = toh<H>(x);
+            bits = hl ? hbits<H>(toh<H>(x - fromh(hi))) : hbits<H>(hi);
+        }
+        const int64_t rowbase = ((int64_t)(c * 2 + hl) * rows + row) * 128;
+        *(uint16_t *)(img + rowbase + ((((e >> 3) ^ (row & 7)) << 4)) + (e & 7) * 2) = bits;
+    }
+    for (int a = threadIdx.x; a < T.count; a += blockDim.x) {
+        const int64_t slot = (int64_t)T.first + a;
+        const int j = s_j[a], K = s_k[a];
+        off[slot] = (int32_t)((((int64_t)lag[j] + K - 1) % n + n) % n);
+        const double sg = sigma[j];
+        scale[slot] = sg > 0.0 ? (float)(ldexp(1.0, -s_exp[a]) / sg) : 0.f;
+    }
+}
+
+}  // namespace
+
+uint32_t tl_ystride(int32_t kpad_max) { return (uint32_t)(kN + kpad_max) * 16u; }
+
+size_t tl_smem_bytes(uint32_t ystride) {
+    return 1024 + (size_t)kAStages * kChunkBytes + 2u * 4u * ystride + 4 * 2 * 32 * 33 * 4 + kNumBars * 8 + 16;
+}
+
+int tl_rows_per_item() { return kN; }
+int tl_tile_templates() { return kNT; }
+
+rfd_status tl_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const int32_t *lag, const double *sigma,
+                   cudaStream_t s) {
+    const unsigned ntiles = (unsigned)plan->tl_tiles.size();
+    if (ntiles == 0) return RFD_OK;
+    if (plan->precision == RFD_PREC_FP16X3)
+        k_pack_tl<__half><<<ntiles, 256, 0, s>>>((const TcTile *)plan->d_tl_tiles.p, taps, k_stride,
+                                                  (const int32_t *)plan->d_perm.p, (const int32_t *)plan->d_kslot.p,
+                                                  lag, sigma, plan->grid.n, (uint8_t *)plan->d_tl_taps.p,
+                                                  (int32_t *)plan->d_off.p, (float *)plan->d_scale.p);
+    else
+        k_pack_tl<__nv_bfloat16><<<ntiles, 256, 0, s>>>(
+            (const TcTile *)plan->d_tl_tiles.p, taps, k_stride, (const int32_t *)plan->d_perm.p,
+            (const int32_t *)plan->d_kslot.p, lag, sigma, plan->grid.n, (uint8_t *)plan->d_tl_taps.p,
+            (int32_t *)plan->d_off.p, (float *)plan->d_scale.p);
+    RFD_LAUNCH_CHECK();
+    return RFD_OK;
+}
+
+rfd_status tl_launch(const rfd_plan *plan, const void *q, const int32_t *qscale, rfd_candidate *cand, int64_t cap,
+                     int64_t *count, cudaStream_t s) {
+    if (plan->tl_tiles.empty()) return RFD_OK;
+    TlArgs a;
+    a.tiles = (const TcTile *)plan->d_tl_tiles.p;
+    a.ranges = (const int64_t *)plan->d_tl_ranges.p;
+    a.n_tb = plan->grid.n / kN;
+    a.taps = (const uint8_t *)plan->d_tl_taps.p;
+    a.q = (const uint16_t *)q;
+    a.ld = plan->ld;
+    a.qscale = qscale;
+    a.perm = (const int32_t *)plan->d_perm.p;
+    a.off = (const int32_t *)plan->d_off.p;
+    a.scale = (const float *)plan->d_scale.p;
+    a.n = plan->grid.n;
+    a.thr = plan->threshold;
+    a.W = (uint32_t)plan->window;
+    a.cand = cand;
+    a.cap = cap;
+    a.count = (unsigned long long *)count;
+    a.ystride = plan->tl_ystride;
+    const size_t shm = tl_smem_bytes(a.ystride);
+    const unsigned grid = (unsigned)plan->tl_grid;
+    static size_t smem_set[64][2] = {};
+    const int dev = plan->ctx->device < 64 ? plan->ctx->device : 63;
+    const int bf = plan->precision == RFD_PREC_FP16X3 ? 0 : 1;
+    if (shm > smem_set[dev][bf]) {
+        if (bf == 0)
+            RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_tc_long<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        else
+            RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_tc_long<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        smem_set[dev][bf] = shm;
+    }
+    if (bf == 0)
+        k_rf_tc_long<0><<<grid, kThreads, shm, s>>>(a);
+    else
+        k_rf_tc_long<1><<<grid, kThreads, shm, s>>>(a);
+    RFD_LAUNCH_CHECK();
+    return RFD_OK;
+}
+
+}  // namespace rfd

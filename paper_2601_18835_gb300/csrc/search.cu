@@ -11,6 +11,8 @@ rfd_status filter_reference_impl(rfd_ctx *, const Grid &, const float2 *, const 
 rfd_status fir32_launch(const rfd_plan *, const float2 *, rfd_candidate *, int64_t, int64_t *, cudaStream_t);
 rfd_status tc_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
                      cudaStream_t);
+rfd_status tl_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
+                     cudaStream_t);
 void add_launches(int64_t n);
 int64_t launch_count();
 }  // namespace rfd
@@ -53,8 +55,10 @@ rfd_status enqueue_step(rfd_search *S, cudaStream_t s, bool capturing) {
     RFD_TRY_CUDA(record(S->ev0, s, capturing));
     if (p->precision == RFD_PREC_FP32)
         RFD_TRY(fir32_launch(p, (const float2 *)S->qref, S->cand, S->cap, S->count, s));
-    else
+    else {
         RFD_TRY(tc_launch(p, S->qref, S->qscale, S->cand, S->cap, S->count, s));
+        RFD_TRY(tl_launch(p, S->qref, S->qscale, S->cand, S->cap, S->count, s));
+    }
     RFD_TRY_CUDA(record(S->ev1, s, capturing));
     RFD_TRY(find_triggers_enqueue(p->ctx, p->n_tmpl, S->cand, S->count, S->cap, S->trig, S->trig_cap, S->host, s));
     RFD_TRY_CUDA(record(S->eve, s, capturing));

@@ -44,10 +44,10 @@ class GpuRun:
         torch.cuda.synchronize()
         return q, e, ld
 
-    def ratio_filter(self, taps, q, e, precision, halo, cand_cap=1 << 20, trig_cap=1 << 18):
+    def ratio_filter(self, taps, q, e, precision, halo, cand_cap=1 << 20, trig_cap=1 << 18, options=None):
         idx = taps["idx"]
         plan = rfd.Plan(self.ctx, self.grid, self.bank.n_ref, self.bank.ref_of_tmpl[idx], taps["K"], precision,
-                        self.cfg.window, self.cfg.threshold, halo)
+                        self.cfg.window, self.cfg.threshold, halo, options=options)
         plan.set_taps(taps["taps"], taps["k_stride"], taps["lag"], taps["sigma"])
         cand = torch.zeros(cand_cap * 24, dtype=torch.uint8, device="cuda")
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")

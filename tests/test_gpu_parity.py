@@ -270,6 +270,9 @@ def test_c2_full_size_fp32_sampled(ctx):
 # --------------------------------------------------------------------------- tensor-core path
 TOL_TC = 1e-3
 TC_PRECISIONS = [("fp16x3", 1), ("bf16x3", 2)]
+# the two tensor-core kernels: time on M with templates on N (K <= 128 by default), and
+# templates on M with time on N (the long-tap kernel, K > 128 by default), each forced for all
+TC_KERNELS = [("time_on_m", {"long_k": 512}), ("templates_on_m", {"long_k": 0})]
 
 
 def snr_errors(trig, sets, js):
@@ -284,13 +287,14 @@ def snr_errors(trig, sets, js):
     return worst
 
 
+@pytest.mark.parametrize("kernel,opts", TC_KERNELS)
 @pytest.mark.parametrize("name,prec", TC_PRECISIONS)
-def test_c1_triggers_tensor_core(c1, name, prec):
+def test_c1_triggers_tensor_core(c1, name, prec, kernel, opts):
     cfg, bank, data, ora, gpu = c1
     t = gpu.make_taps(cfg.k, match=False)
     halo = cfg.k - 1
     q, e, _ = gpu.filter_reference(halo, prec)
-    trig, ncand = gpu.ratio_filter(t, q, e, prec, halo)
+    trig, ncand = gpu.ratio_filter(t, q, e, prec, halo, options=opts)
     sets = {}
     for j in range(bank.n_tmpl):
         o = ora.design(j, cfg.k, with_match=False)
@@ -300,8 +304,9 @@ def test_c1_triggers_tensor_core(c1, name, prec):
     assert snr_errors(trig, sets, range(bank.n_tmpl)) < (2e-5 if prec == 1 else 2e-4)
 
 
+@pytest.mark.parametrize("kernel,opts", TC_KERNELS)
 @pytest.mark.parametrize("name,prec", TC_PRECISIONS)
-def test_ragged_bank_tensor_core(ctx, name, prec):
+def test_ragged_bank_tensor_core(ctx, name, prec, kernel, opts):
     """37 templates, K from 2 to 96 (tiles padded to 16-tap steps), window 37, low threshold."""
     cfg = workload.small_config(1, n_tmpl=37, window=37, threshold=6.0)
     bank, data = workload.make_workload(cfg)
@@ -311,7 +316,7 @@ def test_ragged_bank_tensor_core(ctx, name, prec):
     t = gpu.make_taps(K, k_stride=128, match=False)
     halo = int(((K.max() + 15) // 16) * 16) - 1
     q, e, _ = gpu.filter_reference(halo, prec)
-    trig, ncand = gpu.ratio_filter(t, q, e, prec, halo, cand_cap=1 << 22)
+    trig, ncand = gpu.ratio_filter(t, q, e, prec, halo, cand_cap=1 << 22, options=opts)
     sets = {}
     for j in range(bank.n_tmpl):
         o = ora.design(j, int(K[j]), with_match=False)
