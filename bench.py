@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--n-tmpl", type=int, default=None, help="smaller bank (profiling cases only)")
     ap.add_argument("--n-ref", type=int, default=None, help="fewer references (profiling cases only)")
     ap.add_argument("--no-graph", action="store_true", help="separate launches instead of one CUDA graph")
+    ap.add_argument("--long-k", type=int, default=None,
+                    help="fix the plan's long_k instead of autotuning (profiling cases)")
     ap.add_argument("--n-train", type=int, default=200000, help="learned taps: training tap sets (config 4)")
     ap.add_argument("--epochs", type=int, default=400, help="learned taps: training epochs (config 4)")
     ap.add_argument("--spot-stride", type=int, default=8, help="learned taps: one spot check per this many templates")
@@ -364,8 +366,10 @@ def learned_taps(cfg, bank, ctx, grid, psd, stream, n_train, epochs, spot_stride
 class GpuSearch:
     """Set-up (templates, taps, autotuned plan) and the per-segment search as one CUDA graph."""
 
-    def __init__(self, cfg, bank, data, precision, device, use_graph=True, autotune_cache=None, learned=None):
+    def __init__(self, cfg, bank, data, precision, device, use_graph=True, autotune_cache=None, learned=None,
+                 options=None):
         self.learned = learned
+        self.fixed_options = options
         import torch
         import paper_2601_18835_gb300 as rfd
         from paper_2601_18835_gb300 import autotune
@@ -421,7 +425,9 @@ class GpuSearch:
         rfd.filter_reference(self.ctx, self.grid, self.d, self.psd, self.href, self.halo, precision, self.q,
                              self.e, stream=self.stream)
         self.options, self.tuning = {}, None
-        if precision != 0:
+        if self.fixed_options is not None:
+            self.options = dict(self.fixed_options)
+        elif precision != 0:
             self.options, self.tuning = autotune.autotune(
                 self.ctx, self.grid, bank.n_ref, bank.ref_of_tmpl, self.K, precision, cfg.window, cfg.threshold,
                 self.halo, self.taps, k_stride, self.lag, self.sig, self.q, self.e, cache_path=autotune_cache)
@@ -563,7 +569,7 @@ def run_ours(args):
                    "spot_stride": args.spot_stride}
     tune_cache = os.path.join(ROOT, "paper_2601_18835_gb300", "_build", "autotune.json")
     s = GpuSearch(cfg, bank, data, prec, local, use_graph=not args.no_graph, autotune_cache=tune_cache,
-                  learned=learned)
+                  learned=learned, options={"mix_k": 1, "long_k": args.long_k} if args.long_k is not None else None)
     J, dur = bank.n_tmpl, cfg.duration
 
     def barrier():

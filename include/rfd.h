@@ -218,7 +218,7 @@ typedef struct {
                              template, 512 = none (tile_nt[1], tile_nt[2] then apply) */
     int32_t reserved[2];  /* must be 0 */
 } rfd_plan_options;
-/* Fills the defaults: tile_nt = {128, 64, 32}, mix_k = 1, grid_ctas = 0, long_k = 128. */
+/* Fills the defaults: tile_nt = {128, 64, 32}, mix_k = 1, grid_ctas = 0, long_k = 64. */
 void rfd_plan_options_default(rfd_plan_options *options);
 /* rfd_plan_create with explicit tile choices (NULL = defaults). */
 rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,

@@ -23,7 +23,7 @@ DEFAULT_CANDIDATES = [
     {"mix_k": 1, "tile_nt": [64, 64, 32]},
     {"mix_k": 0, "tile_nt": [64, 64, 32]},
     {"mix_k": 1, "long_k": 512},
-    {"mix_k": 1, "long_k": 64},
+    {"mix_k": 1, "long_k": 128},
     {"mix_k": 1, "long_k": 0},
 ]
 

@@ -27,6 +27,7 @@ rfd_status tl_pack(rfd_plan *, const float2 *, int32_t, const int32_t *, const d
 rfd_status tl_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
                      cudaStream_t);
 uint32_t tl_ystride(int32_t kpad_max);
+uint32_t tl_qwin(int32_t kpad_max);
 int tl_rows_per_item();
 int tl_tile_templates();
 rfd_status tc_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
@@ -100,6 +101,7 @@ static rfd_status plan_tl_tiles(rfd_plan *p, const std::vector<int32_t> &order, 
                 "tensor-core path reads %d taps past each block: halo=%d too small (need >= %d)", kpad_max,
                 p->halo, kpad_max - 1);
     p->tl_ystride = tl_ystride(kpad_max);
+    p->tl_qwin = tl_qwin(kpad_max);
     std::vector<double> cost(ntiles);
     for (int64_t t = 0; t < ntiles; ++t) cost[t] = (double)p->tl_tiles[t].nk16 * 6.0 + 2.0;
     const int64_t G = std::max<int64_t>(1, std::min<int64_t>(opt.grid_ctas > 0 ? opt.grid_ctas : num_sms,
@@ -459,7 +461,7 @@ void rfd_plan_options_default(rfd_plan_options *o) {
     o->tile_nt[2] = 32;
     o->mix_k = 1;
     o->grid_ctas = 0;
-    o->long_k = 128;
+    o->long_k = 64;
 }
 
 rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,

@@ -1,5 +1,5 @@
-// Tensor-core ratio filter for long taps (K > 128), sm_103a: templates on the MMA's M side,
-// time on its N side.
+// Tensor-core ratio filter with templates on the MMA's M side and time on its N side (the
+// default for K > 64; full-width MMAs for any K <= 512), sm_103a.
 //
 // For a tile of 64 templates of one reference and one item of 256 output positions
 // u0 .. u0+255:
@@ -18,10 +18,12 @@
 // 64-tap chunks by bulk copies; two accumulators in tensor memory let the epilogue drain one
 // item while the MMAs fill the next.
 //
-// Roles: warp 0 bulk copies, warp 1 issues the MMAs (and owns the TMEM allocation), warps
-// 4-7 build Y, warps 8-15 drain: a warp of lane quarter 2/3 (imaginary rows) hands its values
-// to the warp of quarter 0/1 (real rows, same templates) through shared memory, which forms
-// z, |z|^2 and the per-window maxima.  Every wait is bounded.
+// Roles: warp 0 bulk copies (taps chunks and each item's q window), warp 1 issues the MMAs
+// (and owns the TMEM allocation), warps 4-7 expand the q window into Y (consecutive lanes on
+// consecutive rows: conflict-free), warps 8-15 drain: a warp of lane quarter 2/3 (imaginary
+// rows) and the warp of quarter 0/1 (real rows, same templates) swap half of each 32-column
+// chunk through shared memory, and each forms z, |z|^2 and the per-window maxima of its 16
+// columns.  Every wait is bounded.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -49,8 +51,10 @@ enum {
     kBarYEmpty = 6,     // 2
     kBarDFull = 8,      // 2
     kBarDEmpty = 10,    // 2
-    kBarDone = 12,
-    kNumBars = 13
+    kBarQFull = 12,     // 2
+    kBarQEmpty = 14,    // 2
+    kBarDone = 16,
+    kNumBars = 17
 };
 
 struct TlArgs {
@@ -71,6 +75,7 @@ struct TlArgs {
     int64_t cap;
     unsigned long long *count;
     uint32_t ystride;           // bytes per Y plane
+    uint32_t qwin;              // halfs per q-window plane
 };
 
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag,
@@ -124,8 +129,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *s_a = sm;                                              // kAStages x 48 KB
     uint8_t *s_y = sm + kAStages * kChunkBytes;                     // 2 buffers x 4 planes
-    float *s_x = (float *)(s_y + 2u * 4u * A.ystride);              // 4 pairs x 2 x 32 x 33
-    uint64_t *bars = (uint64_t *)(s_x + 4 * 2 * 32 * 33);
+    uint16_t *s_qw = (uint16_t *)(s_y + 2u * 4u * A.ystride);       // 2 buffers x 4 planes
+    float *s_x = (float *)(s_qw + 2u * 4u * A.qwin);                // 4 pairs x 2 x 32 x 17
+    uint64_t *bars = (uint64_t *)(s_x + 4 * 2 * 32 * 17);
     uint32_t *s_misc = (uint32_t *)(bars + kNumBars);
     volatile uint32_t *abort_flag = &s_misc[1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -143,6 +149,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
             mbar_init(BAR(kBarYEmpty + b), 1);
             mbar_init(BAR(kBarDFull + b), 1);
             mbar_init(BAR(kBarDEmpty + b), 8);
+            mbar_init(BAR(kBarQFull + b), 1);
+            mbar_init(BAR(kBarQEmpty + b), 4);
         }
         mbar_init(BAR(kBarDone), 1);
         s_misc[1] = 0u;
@@ -157,9 +165,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
     if (warp == 0) {
         // ------------------------------------------------------------ producer: taps chunks
         if (lane == 0) {
-            uint32_t ka = 0;
-            for (int64_t it = it0; it < it1; ++it) {
-                const TcTile T = A.tiles[it / A.n_tb];
+            uint32_t ka = 0, li = 0;
+            int64_t prev = -1;
+            TcTile T{};
+            for (int64_t it = it0; it < it1; ++it, ++li) {
+                const int64_t ti = it / A.n_tb, tb = it - ti * A.n_tb;
+                if (ti != prev) {
+                    T = A.tiles[ti];
+                    prev = ti;
+                }
+                // this item's q window, 256 + kpad samples of each plane
+                const uint32_t qb = li & 1u, use = li >> 1;
+                if (!wait_bar(BAR(kBarQEmpty + qb), (use & 1u) ^ 1u, abort_flag, A.count)) break;
+                const uint32_t wbytes = (uint32_t)(kN + T.kpad) * 2u;
+                mbar_arrive_expect_tx(BAR(kBarQFull + qb), 4u * wbytes);
+                for (int p = 0; p < 4; ++p)
+                    bulk_g2s(smem_u32(s_qw + (qb * 4u + (uint32_t)p) * A.qwin),
+                             A.q + (int64_t)(4 * T.ref + p) * A.ld + tb * kN, wbytes, BAR(kBarQFull + qb));
                 bool ok = true;
                 for (int c = 0; c < T.nch; ++c, ++ka) {
                     const uint32_t st = ka % kAStages, r = ka / kAStages;
@@ -182,8 +204,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
             uint32_t ka = 0, li = 0;
             const uint32_t idn = idesc_f16(128, kN, BF16, 0);
             const uint32_t a_base = smem_u32(s_a), y_base = smem_u32(s_y);
+            int64_t prev = -1;
+            TcTile T{};
             for (int64_t it = it0; it < it1; ++it, ++li) {
-                const TcTile T = A.tiles[it / A.n_tb];
+                if (it / A.n_tb != prev) {
+                    prev = it / A.n_tb;
+                    T = A.tiles[prev];
+                }
                 const uint32_t acc = li & 1u, yb = li & 1u, use = li >> 1;
                 if (!wait_bar(BAR(kBarDEmpty + acc), (use & 1u) ^ 1u, abort_flag, A.count)) break;
                 if (!wait_bar(BAR(kBarYFull + yb), use & 1u, abort_flag, A.count)) break;
@@ -232,36 +259,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
         // ------------------------------------------------------------ Y builders
         const int bt = (warp - 4) * 32 + lane;          // 0..127
         uint32_t li = 0;
+        int64_t prev = -1;
+        int kpad = 0;
         for (int64_t it = it0; it < it1; ++it, ++li) {
-            const int64_t ti = it / A.n_tb, tb = it - ti * A.n_tb;
-            const TcTile T = A.tiles[ti];
-            const uint32_t yb = li & 1u, use = li >> 1;
-            bool ok = wait_bar(BAR(kBarYEmpty + yb), (use & 1u) ^ 1u, abort_flag, A.count);
+            if (it / A.n_tb != prev) {
+                prev = it / A.n_tb;
+                kpad = A.tiles[prev].kpad;
+            }
+            const uint32_t b2 = li & 1u, use = li >> 1;
+            bool ok = wait_bar(BAR(kBarYEmpty + b2), (use & 1u) ^ 1u, abort_flag, A.count);
+            ok = ok && wait_bar(BAR(kBarQFull + b2), use & 1u, abort_flag, A.count);
             if (!__all_sync(0xffffffffu, ok)) break;
-            const int groups = (kN - 8 + T.kpad) / 8;  // rows 0 .. 248 + kpad - 1 in groups of 8
-            uint8_t *y0 = s_y + yb * 4u * A.ystride;
-            for (int g = bt; g < 4 * groups; g += 128) {
-                const int p = g / groups, gr = g - p * groups;
-                const uint16_t *src = A.q + (int64_t)(4 * T.ref + p) * A.ld + tb * kN + 8 * gr;
-                const uint4 lo = *(const uint4 *)src, hi = *(const uint4 *)(src + 8);
-                const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-                uint4 *dst = (uint4 *)(y0 + p * A.ystride + (uint32_t)(8 * gr) * 16u);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
+            const int rows = kN - 8 + kpad;             // Y rows 0 .. 248 + kpad - 1
+            uint8_t *y0 = s_y + b2 * 4u * A.ystride;
+#pragma unroll 1
+            for (int p = 0; p < 4; ++p) {
+                const uint32_t *W = (const uint32_t *)(s_qw + (b2 * 4u + (uint32_t)p) * A.qwin);
+                uint4 *Y = (uint4 *)(y0 + p * A.ystride);
+                for (int r = bt; r < rows; r += 128) {
+                    // Y[r] = q[r .. r+7]: four aligned words, shifted by one half when r is odd
+                    const int w0 = r >> 1;
+                    const uint32_t x0 = W[w0], x1 = W[w0 + 1], x2 = W[w0 + 2], x3 = W[w0 + 3];
                     uint4 v;
-                    if ((i & 1) == 0) {
-                        v = make_uint4(w[i / 2], w[i / 2 + 1], w[i / 2 + 2], w[i / 2 + 3]);
+                    if (r & 1) {
+                        const uint32_t x4 = W[w0 + 4];
+                        v = make_uint4(__funnelshift_r(x0, x1, 16), __funnelshift_r(x1, x2, 16),
+                                       __funnelshift_r(x2, x3, 16), __funnelshift_r(x3, x4, 16));
                     } else {
-                        const int b = i / 2;
-                        v = make_uint4(__funnelshift_r(w[b], w[b + 1], 16), __funnelshift_r(w[b + 1], w[b + 2], 16),
-                                       __funnelshift_r(w[b + 2], w[b + 3], 16), __funnelshift_r(w[b + 3], w[b + 4], 16));
+                        v = make_uint4(x0, x1, x2, x3);
                     }
-                    dst[i] = v;
+                    Y[r] = v;
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(BAR(kBarYFull + yb));
+            if (lane == 0) {
+                mbar_arrive(BAR(kBarYFull + b2));
+                mbar_arrive(BAR(kBarQEmpty + b2));
+            }
         }
     } else if (warp >= 8) {
         // ------------------------------------------------------------ epilogue (pairs)
@@ -269,50 +304,89 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
         const int half = (warp - 8) >> 2;                    // which 128 of the 256 columns
         const bool is_re = lq < 2u;
         const int pair = (int)(lq & 1u) + 2 * half;
-        float *X = s_x + pair * 2 * 32 * 33;
+        // Xs: what this warp hands over (Re of columns 16..31, or Im of columns 0..15); Xr: what it gets
+        float *Xs = s_x + (pair * 2 + (is_re ? 0 : 1)) * 32 * 17;
+        const float *Xr = s_x + (pair * 2 + (is_re ? 1 : 0)) * 32 * 17;
+        const int col_off = is_re ? 0 : 16;                  // this warp's 16 columns of each chunk
         const uint32_t tlane = (lq * 32u) << 16;
-        uint32_t li = 0, xb = 0;
+        uint32_t li = 0;
+        int64_t prev = -1;
+        bool valid = false;
+        float sc = 0.f;
+        int32_t j = 0, o = 0;
         for (int64_t it = it0; it < it1; ++it, ++li) {
             const int64_t ti = it / A.n_tb, tb = it - ti * A.n_tb;
-            const TcTile T = A.tiles[ti];
+            if (ti != prev) {
+                // this lane's template: a = 32 (quarter & 1) + lane, the same in both warps of the pair
+                prev = ti;
+                const TcTile T = A.tiles[ti];
+                const int a = 32 * (int)(lq & 1u) + lane;
+                valid = a < T.count;
+                const int64_t slot = (int64_t)T.first + (valid ? a : 0);
+                sc = valid ? A.scale[slot] * ldexpf(1.0f, -A.qscale[T.ref]) : 0.f;
+                j = valid ? A.perm[slot] : 0;
+                o = valid ? A.off[slot] : 0;
+            }
             const uint32_t acc = li & 1u, use = li >> 1;
             const bool ok = wait_bar(BAR(kBarDFull + acc), use & 1u, abort_flag, A.count);
             if (!__all_sync(0xffffffffu, ok)) break;
             fence_after();
-            // this thread's template (real warps): a = 32 (quarter & 1) + lane
-            const int a = 32 * (int)(lq & 1u) + lane;
-            const bool valid = a < T.count;
-            const int64_t slot = (int64_t)T.first + (valid ? a : 0);
-            const float sc = valid && is_re ? A.scale[slot] * ldexpf(1.0f, -A.qscale[T.ref]) : 0.f;
-            const int32_t j = valid && is_re ? A.perm[slot] : 0;
-            const int32_t o = valid && is_re ? A.off[slot] : 0;
-            for (int cc = 0; cc < 4; ++cc, xb ^= 1u) {
+            for (int cc = 0; cc < 4; ++cc) {
                 const uint32_t c0 = (uint32_t)(half * 128 + cc * 32);
                 uint32_t v[32];
                 tmem_ld32(tmem + tlane + acc * (uint32_t)kN + c0, v);
                 tmem_ld_wait();
-                float *Xb = X + xb * 32 * 33;
-                if (!is_re) {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) Xb[lane * 33 + i] = __uint_as_float(v[i]);
-                }
                 if (cc == 3) {
                     fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(BAR(kBarDEmpty + acc));
                 }
-                named_sync(1u + (uint32_t)pair, 64u);
-                if (is_re && valid) {
-                    // z, |z|^2, threshold and the running maximum of each window along u
-                    uint32_t bw = 0xffffffffu, bp = 0u, bt = 0u;
-                    float bzr = 0.f, bzi = 0.f;
-                    const int64_t u0 = tb * kN + c0;
+                // static register indices only (a runtime index would put v in local memory)
+                float re[16], im[16];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float zr = __fmul_rn(__uint_as_float(v[i]), sc);
-                        const float zi = __fmul_rn(Xb[lane * 33 + i], sc);
-                        const float p = __fadd_rn(__fmul_rn(zr, zr), __fmul_rn(zi, zi));
-                        if (p > A.thr) {
+                for (int i = 0; i < 16; ++i) {
+                    const float lo = __uint_as_float(v[i]), hi = __uint_as_float(v[16 + i]);
+                    Xs[lane * 17 + i] = is_re ? hi : lo;
+                    re[i] = lo;       // the real warp keeps its columns 0..15,
+                    im[i] = hi;       // the imaginary warp its columns 16..31
+                }
+                named_sync(1u + (uint32_t)pair, 64u);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float other = Xr[lane * 17 + i];
+                    if (is_re) {
+                        im[i] = other;
+                    } else {
+                        re[i] = other;
+                    }
+                }
+                if (valid) {
+                    // z and |z|^2 for the 16 samples first (no branch), one mask
+                    uint32_t hit = 0u;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        re[i] = __fmul_rn(re[i], sc);
+                        im[i] = __fmul_rn(im[i], sc);
+                        const float p = __fadd_rn(__fmul_rn(re[i], re[i]), __fmul_rn(im[i], im[i]));
+                        hit |= (p > A.thr ? 1u : 0u) << i;
+                    }
+                    if (hit) {
+                        // rare: the running maximum of each window along u, one candidate per
+                        // (window, run of samples); ties keep the earlier t
+                        uint32_t bw = 0xffffffffu, bp = 0u, bt = 0u;
+                        float bzr = 0.f, bzi = 0.f;
+                        const int64_t u0 = tb * kN + c0 + col_off;
+#pragma unroll 1
+                        for (int i = 0; i < 16; ++i) {
+                            if (!((hit >> i) & 1u)) continue;
+                            float zr = 0.f, zim = 0.f;
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                if (q == i) {
+                                    zr = re[q];
+                                    zim = im[q];
+                                }
+                            const float p = __fadd_rn(__fmul_rn(zr, zr), __fmul_rn(zim, zim));
                             const uint32_t t = (uint32_t)((u0 + i + o) & (A.n - 1));
                             const uint32_t w = t / A.W;
                             if (w != bw) {
@@ -321,17 +395,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                                 bp = 0u;
                             }
                             const uint32_t pb = __float_as_uint(p);
-                            // ties keep the earlier (smaller) t
                             if (pb > bp || (pb == bp && t < bt)) {
                                 bp = pb;
                                 bt = t;
                                 bzr = zr;
-                                bzi = zi;
+                                bzi = zim;
                             }
                         }
+                        if (bw != 0xffffffffu) emit_one((uint32_t)j, bw, bp, bt, bzr, bzi, A.cand, A.cap, A.count);
                     }
-                    if (bw != 0xffffffffu) emit_one((uint32_t)j, bw, bp, bt, bzr, bzi, A.cand, A.cap, A.count);
                 }
+                named_sync(5u + (uint32_t)pair, 64u);     // the buffers are free for the next chunk
             }
         }
     }
@@ -429,10 +503,12 @@ __global__ void __launch_bounds__(256) k_pack_tl(const TcTile *__restrict__ tile
 
 }  // namespace
 
-uint32_t tl_ystride(int32_t kpad_max) { return (uint32_t)(kN + kpad_max) * 16u; }
+uint32_t tl_ystride(int32_t kpad_max) { return (uint32_t)(kN - 8 + kpad_max) * 16u; }
+uint32_t tl_qwin(int32_t kpad_max) { return (uint32_t)(kN + kpad_max); }
 
-size_t tl_smem_bytes(uint32_t ystride) {
-    return 1024 + (size_t)kAStages * kChunkBytes + 2u * 4u * ystride + 4 * 2 * 32 * 33 * 4 + kNumBars * 8 + 16;
+size_t tl_smem_bytes(uint32_t ystride, uint32_t qwin) {
+    return 1024 + (size_t)kAStages * kChunkBytes + 2u * 4u * ystride + 2u * 4u * qwin * 2u + 4 * 2 * 32 * 17 * 4 +
+           kNumBars * 8 + 16;
 }
 
 int tl_rows_per_item() { return kN; }
@@ -477,7 +553,8 @@ rfd_status tl_launch(const rfd_plan *plan, const void *q, const int32_t *qscale,
     a.cap = cap;
     a.count = (unsigned long long *)count;
     a.ystride = plan->tl_ystride;
-    const size_t shm = tl_smem_bytes(a.ystride);
+    a.qwin = plan->tl_qwin;
+    const size_t shm = tl_smem_bytes(a.ystride, a.qwin);
     const unsigned grid = (unsigned)plan->tl_grid;
     static size_t smem_set[64][2] = {};
     const int dev = plan->ctx->device < 64 ? plan->ctx->device : 63;
