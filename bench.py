@@ -632,7 +632,15 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": alg_flops / filt_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     else:
-        kernel, src = "k_rf_tc", "rf_tc.cu"
+        # templates with K > long_k run in k_rf_tc_long (templates on M, time on N), the rest in k_rf_tc
+        long_k = int(s.options.get("long_k", 64))
+        n_long = int((s.K > long_k).sum())
+        if n_long == len(s.K):
+            kernel, src = "k_rf_tc_long", "rf_tc_long.cu"
+        elif n_long == 0:
+            kernel, src = "k_rf_tc", "rf_tc.cu"
+        else:
+            kernel, src = "k_rf_tc_long+k_rf_tc", "rf_tc_long.cu"
         peak_tf = peaks["bf16_tflops_sustained"]
         exec_flops = s.plan.executed_flops()
         roof = {"bound": "tensor", "achieved": alg_flops / filt_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
