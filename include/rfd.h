@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define RFD_VERSION 1
+#define RFD_VERSION 2
 
 typedef enum {
     RFD_OK = 0,

@@ -57,8 +57,13 @@ def _time_plan(plan, qref, qscale, cand, cnt, reps):
 
 def autotune(ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, taps, k_stride, lag, sigma,
              qref, qscale, cache_path=None, candidates=None, reps=3):
-    """Returns (options, report): the fastest candidate's options and every candidate's time (ms)."""
-    sig = signature(g, precision, ref_of, k)
+    """Returns (options, report): the fastest candidate's options and every candidate's time (ms).
+    The cache key covers the workload, the candidate list and the library version, so a cached
+    choice is never reused for a different set of choices or kernels."""
+    from . import _native
+    cands = candidates or DEFAULT_CANDIDATES
+    sig = signature(g, precision, ref_of, k) + "-" + hashlib.sha256(
+        (json.dumps(cands, sort_keys=True) + str(_native.load().rfd_version())).encode()).hexdigest()[:8]
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as fh:
@@ -68,7 +73,7 @@ def autotune(ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, taps,
     cand = torch.zeros((1 << 22) * CANDIDATE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     report = []
-    for opts in (candidates or DEFAULT_CANDIDATES):
+    for opts in cands:
         plan = Plan(ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, options=opts)
         plan.set_taps(taps, k_stride, lag, sigma)
         ms = _time_plan(plan, qref, qscale, cand, cnt, reps)

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
         uint32_t li = 0;
         int64_t prev = -1;
         bool valid = false;
-        float sc = 0.f;
+        float sc = 0.f, thr_raw = 0.f;
         int32_t j = 0, o = 0;
         for (int64_t it = it0; it < it1; ++it, ++li) {
             const int64_t ti = it / A.n_tb, tb = it - ti * A.n_tb;
@@ -321,11 +321,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                 prev = ti;
                 const TcTile T = A.tiles[ti];
                 const int a = 32 * (int)(lq & 1u) + lane;
-                valid = a < T.count;
-                const int64_t slot = (int64_t)T.first + (valid ? a : 0);
-                sc = valid ? A.scale[slot] * ldexpf(1.0f, -A.qscale[T.ref]) : 0.f;
+                const int64_t slot = (int64_t)T.first + (a < T.count ? a : 0);
+                sc = a < T.count ? A.scale[slot] * ldexpf(1.0f, -A.qscale[T.ref]) : 0.f;
+                valid = a < T.count && sc > 0.f;
                 j = valid ? A.perm[slot] : 0;
                 o = valid ? A.off[slot] : 0;
+                // screen on the unscaled |D|^2 against thr / sc^2 lowered by 2^-10 (far above the
+                // few-ulp difference to the scaled |z|^2); every hit is re-tested exactly below
+                thr_raw = valid ? A.thr / (sc * sc) * (1.0f - 0.0009765625f) : 0.f;
             }
             const uint32_t acc = li & 1u, use = li >> 1;
             const bool ok = wait_bar(BAR(kBarDFull + acc), use & 1u, abort_flag, A.count);
@@ -361,14 +364,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                     }
                 }
                 if (valid) {
-                    // z and |z|^2 for the 16 samples first (no branch), one mask
+                    // screen the 16 samples first (no branch), one mask
                     uint32_t hit = 0u;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        re[i] = __fmul_rn(re[i], sc);
-                        im[i] = __fmul_rn(im[i], sc);
-                        const float p = __fadd_rn(__fmul_rn(re[i], re[i]), __fmul_rn(im[i], im[i]));
-                        hit |= (p > A.thr ? 1u : 0u) << i;
+                        const float p_raw = fmaf(re[i], re[i], im[i] * im[i]);
+                        hit |= (p_raw > thr_raw ? 1u : 0u) << i;
                     }
                     if (hit) {
                         // rare: the running maximum of each window along u, one candidate per
@@ -383,10 +384,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
 #pragma unroll
                             for (int q = 0; q < 16; ++q)
                                 if (q == i) {
-                                    zr = re[q];
-                                    zim = im[q];
+                                    zr = __fmul_rn(re[q], sc);
+                                    zim = __fmul_rn(im[q], sc);
                                 }
+                            // z and |z|^2 exactly as the other kernel forms them
                             const float p = __fadd_rn(__fmul_rn(zr, zr), __fmul_rn(zim, zim));
+                            if (!(p > A.thr)) continue;
                             const uint32_t t = (uint32_t)((u0 + i + o) & (A.n - 1));
                             const uint32_t w = t / A.W;
                             if (w != bw) {

@@ -376,6 +376,35 @@ def test_c2_full_size_tensor_core_sampled(ctx, name, prec):
     assert compare_triggers(trig, sets, TOL_TC, sample, cfg.window) <= 4
 
 
+@pytest.mark.slow
+def test_c5_grid_long_taps_sampled(ctx):
+    """The C5 grid (512 s at 2048 Hz, n = 2^20, f_low 45 Hz, subsolar masses) with K = 512 on
+    the templates-on-M kernel: 256 templates over 2 references, every GPU trigger of a sampled
+    template re-evaluated by the oracle at its sample, and the sampled templates' oracle
+    trigger sets matched window by window."""
+    cfg = workload.small_config(5, n_tmpl=256, n_ref=2)
+    bank, data = workload.make_workload(cfg)
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP16X3)
+    trig, ncand = gpu.ratio_filter(t, q, e, rfd.PREC_FP16X3, halo, cand_cap=1 << 22)
+    inj = sorted({s for (_, _, _, s) in data.injections})
+    sample = sorted(set(inj[:2]) | {int(np.nonzero(bank.ref_of_tmpl == r)[0][-1]) for r in range(bank.n_ref)})
+    sets = {}
+    checked = 0
+    for j in sample:
+        o = ora.design(j, cfg.k, with_match=False)
+        sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
+        g = trig[trig["j"] == j]
+        if len(g):
+            zo = ora.snr_at(j, o, g["t"].astype(np.int64))
+            assert np.max(np.abs(np.sqrt(g["snr2"]) - np.abs(zo)) / np.abs(zo)) < TOL_TC
+            checked += len(g)
+    assert checked > 0
+    assert compare_triggers(trig, sets, TOL_TC, sample, cfg.window) <= 4
+
+
 # --------------------------------------------------------------------------- bucketed K (C3 shape)
 def test_bucketed_taps_and_uneven_k_tensor_core(ctx):
     """Spin-orbit bank over 1-20 Msun on a 32 s / 2048 Hz grid: K_j chosen from the buckets
