@@ -156,6 +156,26 @@ rfd_status rfd_make_taps(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_d
                          double tukey_alpha, void *taps_dev, int32_t *k_dev, int32_t *lag_dev,
                          double *sigma_dev, double *match_dev, void *stream);
 
+/* Chi^2-fitted taps (Sec. V.A, Eq. 4): instead of windowing, the taps minimise
+ *   sum_k w_k |G_k - A_k|^2 + lam |rho|^2,  A_k = sum_n rho_n exp(-2 pi i k (s_j + n) / n),
+ * G = conj(h_j / h_ref) (Eq. 2 conjugated), w_k = 4 df |h_ref,k|^2 / S_k on the reference band
+ * (the data reach the ratio filter band-passed by the reference), lam = ridge C_r[0]; i.e.
+ *   sum_m (C_r[n - m] + lam delta_nm) rho_m = b_n,  b_n = sum_k w_k G_k exp(+2 pi i k (s_j + n)/N),
+ * solved per template by the Levinson recursion in FP64.  The lag s_j is placed as in
+ * rfd_make_taps (window-energy rule with the Tukey window of K taps).  match_dev (required)
+ * receives the fitted taps' match to the template, |rho^H b| / (sigma_eff sigma_j).
+ * K: k_host int32 [n_tmpl] per template, or k_host = NULL and buckets_host [n_buckets]: each
+ * template gets the smallest bucket whose fitted match reaches match_target (the largest bucket
+ * otherwise), written to k_dev (may be NULL with k_host).  ridge in (0, 1); k_stride <= 512.
+ * Outputs as for rfd_make_taps.  Synchronises the stream before returning. */
+rfd_status rfd_make_taps_fit(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_dev,
+                             const rfd_params *refs_host, int32_t n_ref, const rfd_params *tmpl_host,
+                             const int32_t *ref_of_tmpl_host, int32_t n_tmpl, const int32_t *k_host,
+                             const int32_t *buckets_host, int32_t n_buckets, double match_target,
+                             double ridge, int32_t k_stride, double tukey_alpha, void *taps_dev,
+                             int32_t *k_dev, int32_t *lag_dev, double *sigma_dev, double *match_dev,
+                             void *stream);
+
 /* Taps at a given lag: as rfd_make_taps with fixed K, except that the placement s_j is
  * lag_host[j] (in [-n/2, n/2)) instead of the window-energy maximiser, so
  * rho_j[k] = w[k] g_j[(s_j + k) mod n].  These are the targets the learned-tap networks are

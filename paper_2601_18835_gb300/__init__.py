@@ -21,7 +21,8 @@ from . import _native
 from ._native import (CANDIDATE_DTYPE, PN_SO, PN_TIDAL, PREC_BF16X3, PREC_FP16X3, PREC_FP32,  # noqa: F401
                       TRIGGER_DTYPE, RfdError, check)
 
-__all__ = ["Context", "Plan", "Search", "Mlp", "grid", "gen_templates", "make_taps", "make_taps_at_lag",
+__all__ = ["Context", "Plan", "Search", "Mlp", "grid", "gen_templates", "make_taps", "make_taps_fit",
+           "make_taps_at_lag",
            "filter_reference",
            "find_triggers", "find_triggers_noalloc", "findchirp", "ifft_c2c", "qref_ld", "candidates_to_numpy",
            "triggers_to_numpy", "CANDIDATE_DTYPE", "TRIGGER_DTYPE"]
@@ -124,6 +125,24 @@ def make_taps(ctx, g, psd, refs, tmpl, ref_of, k, k_stride, alpha, taps, lag, si
     check(_lib().rfd_make_taps(ctx.handle, ctypes.byref(g), _ptr(psd), ra, nr, ta, rop, nt, kp, bkp, nbk,
                                float(energy_frac), int(k_stride), float(alpha), _ptr(taps), _ptr(k_out),
                                _ptr(lag), _ptr(sigma), _ptr(match), _stream(stream)))
+
+
+def make_taps_fit(ctx, g, psd, refs, tmpl, ref_of, k, k_stride, alpha, taps, lag, sigma, match, ridge=1e-6,
+                  buckets=None, match_target=0.99, k_out=None, stream=None):
+    """Chi^2-fitted taps (Sec. V.A): k per template, or k=None with buckets and a target match."""
+    ra, nr = _params(refs)
+    ta, nt = _params(tmpl)
+    ro, rop = _i32_host(ref_of)
+    if k is None:
+        kp = None
+        bk, bkp = _i32_host(buckets)
+        nbk = len(bk)
+    else:
+        kk, kp = _i32_host(k)
+        bkp, nbk = None, 0
+    check(_lib().rfd_make_taps_fit(ctx.handle, ctypes.byref(g), _ptr(psd), ra, nr, ta, rop, nt, kp, bkp, nbk,
+                                   float(match_target), float(ridge), int(k_stride), float(alpha), _ptr(taps),
+                                   _ptr(k_out), _ptr(lag), _ptr(sigma), _ptr(match), _stream(stream)))
 
 
 def make_taps_at_lag(ctx, g, psd, refs, tmpl, ref_of, k, lag, k_stride, alpha, taps, sigma, match=None,

@@ -91,6 +91,8 @@ SIGNATURES = {
     "rfd_ifft_c2c": (_i32, [_vp, _i64, _i32, _vp, _vp, _vp]),
     "rfd_make_taps_at_lag": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _i32,
                                     _dbl, _vp, _vp, _vp, _vp]),
+    "rfd_make_taps_fit": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _dbl,
+                                 _dbl, _i32, _dbl, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rfd_mlp_param_count": (_i64, []),
     "rfd_mlp_create": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, ctypes.POINTER(_vp)]),
     "rfd_mlp_destroy": (None, [_vp]),

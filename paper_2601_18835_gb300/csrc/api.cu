@@ -394,6 +394,53 @@ rfd_status rfd_make_taps(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_d
                           (float2 *)taps_dev, k_dev, lag_dev, sigma_dev, match_dev, (cudaStream_t)stream);
 }
 
+rfd_status rfd_make_taps_fit(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_dev, const rfd_params *refs_host,
+                             int32_t n_ref, const rfd_params *tmpl_host, const int32_t *ref_of_tmpl_host,
+                             int32_t n_tmpl, const int32_t *k_host, const int32_t *buckets_host, int32_t n_buckets,
+                             double match_target, double ridge, int32_t k_stride, double tukey_alpha, void *taps_dev,
+                             int32_t *k_dev, int32_t *lag_dev, double *sigma_dev, double *match_dev, void *stream) {
+    RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
+    Grid g;
+    RFD_TRY(check_grid(grid, &g));
+    RFD_REQUIRE(n_ref >= 1 && n_tmpl >= 0, RFD_ERR_SHAPE, "need n_ref >= 1 and n_tmpl >= 0");
+    if (n_tmpl == 0) return RFD_OK;
+    RFD_REQUIRE(psd_dev && refs_host && tmpl_host && ref_of_tmpl_host && taps_dev && lag_dev && sigma_dev && match_dev,
+                RFD_ERR_ARG, "NULL argument");
+    RFD_REQUIRE(k_host || (buckets_host && n_buckets >= 1), RFD_ERR_ARG, "give either k_host or a non-empty bucket list");
+    RFD_REQUIRE(std::isfinite(ridge) && ridge > 0.0 && ridge < 1.0, RFD_ERR_ARG, "ridge must be in (0, 1)");
+    RFD_REQUIRE(k_stride >= 1 && k_stride <= 512 && k_stride <= g.n, RFD_ERR_SHAPE,
+                "k_stride=%d out of [1, min(512, n)] for the fitted taps", k_stride);
+    RFD_REQUIRE(std::isfinite(tukey_alpha) && tukey_alpha >= 0.0, RFD_ERR_ARG, "tukey_alpha must be >= 0");
+    std::vector<int32_t> ref_of(ref_of_tmpl_host, ref_of_tmpl_host + n_tmpl), K, buckets;
+    for (int32_t j = 0; j < n_tmpl; ++j)
+        RFD_REQUIRE(ref_of[j] >= 0 && ref_of[j] < n_ref, RFD_ERR_ARG, "ref_of_tmpl[%d]=%d out of range", j, ref_of[j]);
+    if (k_host) {
+        K.assign(k_host, k_host + n_tmpl);
+        for (int32_t j = 0; j < n_tmpl; ++j)
+            RFD_REQUIRE(K[j] >= 1 && K[j] <= k_stride, RFD_ERR_SHAPE, "K[%d]=%d not in [1, k_stride]", j, K[j]);
+    } else {
+        RFD_REQUIRE(std::isfinite(match_target) && match_target <= 1.0, RFD_ERR_ARG, "match_target must be <= 1");
+        buckets.assign(buckets_host, buckets_host + n_buckets);
+        for (int32_t i = 0; i < n_buckets; ++i)
+            RFD_REQUIRE(buckets[i] >= 1 && buckets[i] <= k_stride, RFD_ERR_SHAPE, "bucket %d=%d not in [1, k_stride]",
+                        i, buckets[i]);
+    }
+    RFD_TRY_CUDA(cudaSetDevice(ctx->device));
+    std::vector<PNParams> refs, tmpl;
+    RFD_TRY(make_pn_vec(g, refs_host, n_ref, &refs));
+    RFD_TRY(make_pn_vec(g, tmpl_host, n_tmpl, &tmpl));
+    for (int32_t r = 0; r < n_ref; ++r)
+        RFD_REQUIRE(refs[r].k_hi >= g.k_lo, RFD_ERR_ARG, "reference %d has an empty band (ISCO below f_low)", r);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (k_host) {
+        RFD_TRY(make_taps_impl(ctx, g, psd_dev, refs, tmpl, ref_of, K, {}, {}, 1.0, k_stride, tukey_alpha,
+                               (float2 *)taps_dev, k_dev, lag_dev, sigma_dev, match_dev, s, ridge));
+        return RFD_OK;
+    }
+    return make_taps_fit_dynamic(ctx, g, psd_dev, refs, tmpl, ref_of, buckets, match_target, ridge, k_stride,
+                                 tukey_alpha, (float2 *)taps_dev, k_dev, lag_dev, sigma_dev, match_dev, s);
+}
+
 rfd_status rfd_make_taps_at_lag(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_dev,
                                 const rfd_params *refs_host, int32_t n_ref, const rfd_params *tmpl_host,
                                 const int32_t *ref_of_tmpl_host, int32_t n_tmpl, const int32_t *k_host,

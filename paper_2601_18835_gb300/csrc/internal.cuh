@@ -106,12 +106,19 @@ rfd_status fft_c2c(rfd_ctx *ctx, int64_t n, int64_t batch, const typename Cplx<T
 
 // ------------------------------------------------------------------ taps (taps.cu)
 // lag_in empty: the lag is searched (Sec. V placement); otherwise it is taken from lag_in.
-// K empty: K chosen from `buckets`.
+// K empty: K chosen from `buckets`.  fit_eps > 0: the taps are the chi^2 fit of Sec. V.A with
+// ridge fit_eps C_r[0] (at the same lag), and `match` is its closed form.
 rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd, const std::vector<PNParams> &refs,
                           const std::vector<PNParams> &tmpl, const std::vector<int32_t> &ref_of,
                           const std::vector<int32_t> &K, const std::vector<int32_t> &buckets,
                           const std::vector<int32_t> &lag_in, double energy_frac, int32_t k_stride, double alpha,
-                          float2 *taps, int32_t *k_out, int32_t *lag, double *sigma, double *match, cudaStream_t s);
+                          float2 *taps, int32_t *k_out, int32_t *lag, double *sigma, double *match, cudaStream_t s,
+                          double fit_eps = 0.0);
+rfd_status make_taps_fit_dynamic(rfd_ctx *ctx, const Grid &g, const double *psd, const std::vector<PNParams> &refs,
+                                 const std::vector<PNParams> &tmpl, const std::vector<int32_t> &ref_of,
+                                 const std::vector<int32_t> &buckets, double target, double eps, int32_t k_stride,
+                                 double alpha, float2 *taps, int32_t *k_out, int32_t *lag, double *sigma,
+                                 double *match, cudaStream_t s);
 rfd_status ref_autocorr_impl(rfd_ctx *ctx, const Grid &g, const double *psd, const PNParams *refs_dev, int64_t R,
                              int32_t kmax, double2 *C, cudaStream_t s);
 rfd_status make_pn_vec(const Grid &g, const rfd_params *p, int32_t n, std::vector<PNParams> *out);

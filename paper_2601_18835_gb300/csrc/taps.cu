@@ -427,6 +427,166 @@ __global__ void k_match_final(const double *__restrict__ part, int64_t nb, int32
 
 // Workspace slots: ws[6] jobs, ws[7] G / placed taps, ws[8] g / A, ws[9] FFT tmp, ws[10] E,
 // ws[11] per-template scalars (emax, lagkey) + rho64 + C_r rows + match partials.
+// ------------------------------------------------------------------ chi^2-fitted taps (Sec. V.A)
+// w G on the reference band (w = 4 df |h_r|^2 / S, the reference's SNR density), zero elsewhere
+// and above n/2, in place: its inverse transform read at the lag window is the right-hand side
+// of the fit's normal equations.
+__global__ void __launch_bounds__(256) k_weight_spectrum(const TapJob *__restrict__ jobs,
+                                                         const double *__restrict__ psd, double df, int64_t n,
+                                                         int64_t k_lo, double2 *__restrict__ G) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int b = blockIdx.y;
+    const int64_t k_hi = jobs[b].tr.k_hi;
+    double2 *gk = G + (int64_t)b * n + k;
+    if (k >= k_lo && k <= k_hi) {
+        const double f = (double)k * df;
+        const double amp = pow(f, -7.0 / 6.0);
+        const double w = 4.0 * df * (amp * amp) / psd[k];
+        *gk = make_double2(w * gk->x, w * gk->y);
+    } else {
+        *gk = make_double2(0.0, 0.0);
+    }
+}
+
+__device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cdiv_d(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// Block-wide sum of three complex values (256 threads); every thread gets the totals.
+__device__ __forceinline__ void block_sum3(double2 &a, double2 &b, double2 &c, double *red) {
+    double v[6] = {a.x, a.y, b.x, b.y, c.x, c.y};
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) red[(threadIdx.x >> 5) * 6 + q] = v[q];
+    __syncthreads();
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) t[q] += red[w * 6 + q];
+    a = make_double2(t[0], t[1]);
+    b = make_double2(t[2], t[3]);
+    c = make_double2(t[4], t[5]);
+}
+
+// The ridge-regularised normal equations sum_m (C_r[n-m] + lam delta) rho_m = b_n, n < K,
+// solved by the Levinson recursion (forward / backward vectors of the Hermitian Toeplitz
+// matrix, O(K^2)), one block per template, FP64.  b_n = bw[(s + n) mod N] (bw: the inverse
+// transform of w G).  Writes the taps (FP64 and FP32), the lag and rho^H b (for the match).
+__global__ void __launch_bounds__(256) k_fit_levinson(const TapJob *__restrict__ jobs,
+                                                      const double2 *__restrict__ bw, int64_t n,
+                                                      const double2 *__restrict__ Cc, int32_t kmax, double eps,
+                                                      const unsigned long long *__restrict__ lagkey,
+                                                      int32_t j0, int32_t k_stride, double2 *__restrict__ rho64,
+                                                      float2 *__restrict__ taps, int32_t *__restrict__ lag,
+                                                      double2 *__restrict__ bdot) {
+    extern __shared__ double2 lv[];
+    __shared__ double red[8 * 6];
+    const int b = blockIdx.x;
+    const int K = jobs[b].K;
+    double2 *c = lv, *y = lv + kmax, *f = lv + 2 * kmax, *g = lv + 3 * kmax, *x = lv + 4 * kmax;
+    const double2 *Cr = Cc + (int64_t)jobs[b].ref * (2 * kmax - 1) + (kmax - 1);   // Cr[l], |l| < kmax
+    const int64_t s = (int64_t)(lagkey[b] & 0xffffffffull) - n / 2;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+        c[i] = Cr[i];
+        y[i] = bw[(int64_t)b * n + (((s + i) % n) + n) % n];
+        f[i] = g[i] = x[i] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        c[0].x += eps * c[0].x;
+        const double2 inv = cdiv_d(make_double2(1.0, 0.0), c[0]);
+        f[0] = g[0] = inv;
+        x[0] = cmul_d(y[0], inv);
+    }
+    __syncthreads();
+    for (int m = 1; m < K; ++m) {
+        // errors of the extended vectors: ef = sum_i T[m][i] f_i, eb = sum_i T[0][i+1] g_i,
+        // ex = sum_i T[m][i] x_i with T[a][b] = C[a - b], C[-l] = conj(C[l])
+        double2 ef = make_double2(0.0, 0.0), eb = ef, ex = ef;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double2 cm = c[m - i], ci = c[i + 1];
+            const double2 fi = f[i], gi = g[i], xi = x[i];
+            ef.x += cm.x * fi.x - cm.y * fi.y;
+            ef.y += cm.x * fi.y + cm.y * fi.x;
+            eb.x += ci.x * gi.x + ci.y * gi.y;          // conj(c[i+1]) g_i
+            eb.y += ci.x * gi.y - ci.y * gi.x;
+            ex.x += cm.x * xi.x - cm.y * xi.y;
+            ex.y += cm.x * xi.y + cm.y * xi.x;
+        }
+        block_sum3(ef, eb, ex, red);
+        const double2 d = make_double2(1.0 - (ef.x * eb.x - ef.y * eb.y), -(ef.x * eb.y + ef.y * eb.x));
+        const double2 a1 = cdiv_d(make_double2(1.0, 0.0), d), af = cdiv_d(ef, d), ab = cdiv_d(eb, d);
+        // new f_i = a1 [f;0]_i - af [0;g]_i,  new g_i = a1 [0;g]_i - ab [f;0]_i  (K <= 512)
+        double2 nf[2], ng[2];
+        int cnt = 0;
+        for (int i = threadIdx.x; i <= m && cnt < 2; i += blockDim.x, ++cnt) {
+            const double2 fo = i < m ? f[i] : make_double2(0.0, 0.0);
+            const double2 go = i >= 1 ? g[i - 1] : make_double2(0.0, 0.0);
+            const double2 t1 = cmul_d(a1, fo), t2 = cmul_d(af, go), t3 = cmul_d(a1, go), t4 = cmul_d(ab, fo);
+            nf[cnt] = make_double2(t1.x - t2.x, t1.y - t2.y);
+            ng[cnt] = make_double2(t3.x - t4.x, t3.y - t4.y);
+        }
+        __syncthreads();
+        const double2 e = make_double2(y[m].x - ex.x, y[m].y - ex.y);
+        cnt = 0;
+        for (int i = threadIdx.x; i <= m && cnt < 2; i += blockDim.x, ++cnt) {
+            f[i] = nf[cnt];
+            g[i] = ng[cnt];
+            const double2 xo = i < m ? x[i] : make_double2(0.0, 0.0);
+            const double2 u = cmul_d(e, ng[cnt]);
+            x[i] = make_double2(xo.x + u.x, xo.y + u.y);
+        }
+        __syncthreads();
+    }
+    // taps, rho^H b
+    double2 p = make_double2(0.0, 0.0), z0 = p, z1 = p;
+    for (int i = threadIdx.x; i < k_stride; i += blockDim.x) {
+        const double2 r = i < K ? x[i] : make_double2(0.0, 0.0);
+        rho64[(int64_t)b * k_stride + i] = r;
+        taps[(int64_t)(j0 + b) * k_stride + i] = make_float2((float)r.x, (float)r.y);
+        if (i < K) {
+            p.x += r.x * y[i].x + r.y * y[i].y;      // conj(rho_i) b_i
+            p.y += r.x * y[i].y - r.y * y[i].x;
+        }
+    }
+    block_sum3(p, z0, z1, red);
+    if (threadIdx.x == 0) {
+        lag[j0 + b] = (int32_t)s;
+        bdot[b] = p;
+    }
+}
+
+// sigma_j^2 = 4 df sum |h_j|^2 / S over the template's band, and the fitted taps' match
+// |rho^H b| / (sigma_eff sigma_j) (sigma_eff = sqrt(rho^H C_r rho), from k_sigma_eff).
+__global__ void __launch_bounds__(256) k_fit_match(const TapJob *__restrict__ jobs, const double *__restrict__ psd,
+                                                   double df, int64_t n, int64_t k_lo,
+                                                   const double2 *__restrict__ bdot, const double *__restrict__ sigma,
+                                                   int32_t j0, double *__restrict__ match) {
+    __shared__ double sm[8];
+    const int b = blockIdx.x;
+    const int64_t k_hi = min(jobs[b].tj.k_hi, n / 2);
+    double part = 0.0;
+    for (int64_t k = k_lo + threadIdx.x; k <= k_hi; k += blockDim.x) {
+        const double f = (double)k * df;
+        part += pow(f, -7.0 / 3.0) / psd[k];
+    }
+    const double tot = block_sum_d(part, sm) * 4.0 * df;
+    if (threadIdx.x == 0) {
+        const double2 p = bdot[b];
+        const double se = sigma[j0 + b];
+        match[j0 + b] = (se > 0.0 && tot > 0.0) ? sqrt(p.x * p.x + p.y * p.y) / (se * sqrt(tot)) : 0.0;
+    }
+}
+
 // C_r[l] = sum_k 4 df |h_r|^2/S exp(+2 pi i k l / n) for |l| < kmax, one inverse FFT per
 // reference (Eq. 6 on the sample grid): C[r][l + kmax - 1], complex128.  refs_dev: PNParams[R].
 // Scratch: ws[7], ws[8], ws[9] (R n complex128 each).
@@ -450,8 +610,9 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
                           const std::vector<int32_t> &ref_of, const std::vector<int32_t> &K,
                           const std::vector<int32_t> &buckets, const std::vector<int32_t> &lag_in,
                           double energy_frac, int32_t k_stride, double alpha, float2 *taps, int32_t *k_out,
-                          int32_t *lag, double *sigma, double *match, cudaStream_t s) {
+                          int32_t *lag, double *sigma, double *match, cudaStream_t s, double fit_eps) {
     const bool fixed_lag = !lag_in.empty();
+    const bool fitted = fit_eps > 0.0;
     const int64_t n = g.n;
     const int64_t J = (int64_t)tmpl.size(), R = (int64_t)refs.size();
     const bool bucketed = K.empty();
@@ -471,7 +632,8 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
     const size_t off_rho = (off_bk + (size_t)std::max(nbk, 1) * sizeof(int32_t) + 15) / 16 * 16;
     const size_t off_C = off_rho + (size_t)B * k_stride * sizeof(double2);
     const size_t off_part = off_C + (size_t)R * (2 * kmax - 1) * sizeof(double2);
-    const size_t ws11 = off_part + (size_t)B * 4 * nb_match * sizeof(double);
+    const size_t off_bdot = off_part + (size_t)B * 4 * nb_match * sizeof(double);
+    const size_t ws11 = off_bdot + (size_t)B * sizeof(double2);
     RFD_TRY(ensure(ctx->ws[6], B * sizeof(TapJob)));
     RFD_TRY(ensure(ctx->ws[7], std::max(B, R) * n * sizeof(double2)));
     RFD_TRY(ensure(ctx->ws[8], std::max(B, R) * n * sizeof(double2)));
@@ -490,6 +652,7 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
     double2 *rho64 = (double2 *)(base11 + off_rho);
     double2 *C = (double2 *)(base11 + off_C);
     double *part = (double *)(base11 + off_part);
+    double2 *bdot = (double2 *)(base11 + off_bdot);
     double *E = (double *)ctx->ws[10].p;
     double *Pbuf = (double *)ctx->ws[15].p;
     if (bucketed)
@@ -560,14 +723,28 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
         k_lag_select<<<dim3((unsigned)(n / 256), (unsigned)nbt), 256, 0, s>>>(dj, E, n, emax, lagkey);
         RFD_LAUNCH_CHECK();
         }
-        if (match) RFD_TRY_CUDA(cudaMemsetAsync(Gb, 0, nbt * n * sizeof(double2), s));
-        k_place<<<(unsigned)nbt, 256, 0, s>>>(dj, gb, n, alpha, lagkey, (int32_t)j0, k_stride, rho64,
-                                              taps, lag, match ? Gb : nullptr);
-        RFD_LAUNCH_CHECK();
+        if (fitted) {
+            // Sec. V.A: taps fitted to the ratio in the reference's SNR-weighted band, ridge eps
+            k_weight_spectrum<<<dim3((unsigned)(n / 256), (unsigned)nbt), 256, 0, s>>>(dj, psd, g.df, n, g.k_lo,
+                                                                                      Gb);
+            RFD_LAUNCH_CHECK();
+            RFD_TRY(fft_c2c<double>(ctx, n, nbt, Gb, n, gb, n, tmp, true, s));
+            k_fit_levinson<<<(unsigned)nbt, 256, (size_t)5 * kmax * sizeof(double2), s>>>(
+                dj, gb, n, C, kmax, fit_eps, lagkey, (int32_t)j0, k_stride, rho64, taps, lag, bdot);
+            RFD_LAUNCH_CHECK();
+        } else {
+            if (match) RFD_TRY_CUDA(cudaMemsetAsync(Gb, 0, nbt * n * sizeof(double2), s));
+            k_place<<<(unsigned)nbt, 256, 0, s>>>(dj, gb, n, alpha, lagkey, (int32_t)j0, k_stride, rho64,
+                                                  taps, lag, match ? Gb : nullptr);
+            RFD_LAUNCH_CHECK();
+        }
         k_sigma_eff<<<(unsigned)nbt, 256, (size_t)kmax * sizeof(double2), s>>>(dj, rho64, k_stride, C,
                                                                            kmax, (int32_t)j0, sigma);
         RFD_LAUNCH_CHECK();
-        if (match) {
+        if (fitted && match) {
+            k_fit_match<<<(unsigned)nbt, 256, 0, s>>>(dj, psd, g.df, n, g.k_lo, bdot, sigma, (int32_t)j0, match);
+            RFD_LAUNCH_CHECK();
+        } else if (match) {
             RFD_TRY(fft_c2c<double>(ctx, n, nbt, Gb, n, gb, n, tmp, false, s));
             k_match_partial<<<dim3((unsigned)nb_match, (unsigned)nbt), 256, 0, s>>>(
                 dj, g.pn_flags, psd, g.df, n, g.k_lo, gb, part);
@@ -579,6 +756,114 @@ rfd_status make_taps_impl(rfd_ctx *ctx, const Grid &g, const double *psd,
         RFD_TRY_CUDA(cudaStreamSynchronize(s));
     }
     return RFD_OK;
+}
+
+namespace {
+__global__ void k_scatter_fit_rows(const float2 *__restrict__ st, const int32_t *__restrict__ sl,
+                                   const double *__restrict__ ss, const double *__restrict__ sm,
+                                   const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int32_t K,
+                                   int32_t k_stride, float2 *__restrict__ taps, int32_t *__restrict__ lag,
+                                   double *__restrict__ sigma, double *__restrict__ match, int32_t *__restrict__ k_out) {
+    const int64_t i = src[blockIdx.x], j = dst[blockIdx.x];
+    for (int k = threadIdx.x; k < k_stride; k += blockDim.x) taps[j * k_stride + k] = st[i * k_stride + k];
+    if (threadIdx.x == 0) {
+        lag[j] = sl[i];
+        sigma[j] = ss[i];
+        match[j] = sm[i];
+        if (k_out) k_out[j] = K;
+    }
+}
+}  // namespace
+
+// Sec. V.A's dynamic tap count: every template is fitted at the smallest bucket whose fitted
+// match reaches `target` (the largest bucket otherwise).  One fit pass per bucket over the
+// templates still pending.
+rfd_status make_taps_fit_dynamic(rfd_ctx *ctx, const Grid &g, const double *psd, const std::vector<PNParams> &refs,
+                                 const std::vector<PNParams> &tmpl, const std::vector<int32_t> &ref_of,
+                                 const std::vector<int32_t> &buckets, double target, double eps, int32_t k_stride,
+                                 double alpha, float2 *taps, int32_t *k_out, int32_t *lag, double *sigma,
+                                 double *match, cudaStream_t s) {
+    const int64_t J = (int64_t)tmpl.size();
+    std::vector<int32_t> pending(J);
+    for (int64_t j = 0; j < J; ++j) pending[j] = (int32_t)j;
+    std::vector<int32_t> sorted(buckets);
+    std::sort(sorted.begin(), sorted.end());
+    DevBuf buf;
+    rfd_status st = RFD_OK;
+    for (size_t bi = 0; bi < sorted.size() && !pending.empty() && st == RFD_OK; ++bi) {
+        const int32_t K = sorted[bi];
+        const int64_t np = (int64_t)pending.size();
+        auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+        const size_t bt = up((size_t)np * k_stride * sizeof(float2));
+        if ((st = ensure(buf, bt + up(np * 4) * 2 + up(np * 8) * 2)) != RFD_OK) break;
+        char *base = (char *)buf.p;
+        float2 *t_taps = (float2 *)base;
+        int32_t *t_lag = (int32_t *)(base + bt);
+        int32_t *t_idx = (int32_t *)(base + bt + up(np * 4));
+        double *t_sig = (double *)(base + bt + 2 * up(np * 4));
+        double *t_match = (double *)(base + bt + 2 * up(np * 4) + up(np * 8));
+        std::vector<PNParams> sub(np);
+        std::vector<int32_t> sub_ref(np), sub_k(np, K);
+        for (int64_t i = 0; i < np; ++i) {
+            sub[i] = tmpl[pending[i]];
+            sub_ref[i] = ref_of[pending[i]];
+        }
+        if ((st = make_taps_impl(ctx, g, psd, refs, sub, sub_ref, sub_k, {}, {}, 1.0, k_stride, alpha, t_taps,
+                                 nullptr, t_lag, t_sig, t_match, s, eps)) != RFD_OK)
+            break;
+        std::vector<double> hm(np);
+        cudaError_t e = cudaMemcpyAsync(hm.data(), t_match, np * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            set_error("reading the fitted matches failed: %s", cudaGetErrorString(e));
+            st = RFD_ERR_CUDA;
+            break;
+        }
+        const bool last = bi + 1 == sorted.size();
+        std::vector<int32_t> take_src, take_dst, still;
+        for (int64_t i = 0; i < np; ++i) {
+            if (last || hm[i] >= target) {
+                take_src.push_back((int32_t)i);
+                take_dst.push_back(pending[i]);
+            } else {
+                still.push_back(pending[i]);
+            }
+        }
+        if (!take_src.empty()) {
+            // compact the accepted rows to the front of the scratch, then scatter them into place
+            const int64_t na = (int64_t)take_src.size();
+            std::vector<int32_t> dst(na);
+            for (int64_t i = 0; i < na; ++i) dst[i] = take_dst[i];
+            // the scatter reads row take_src[i]: pass the source rows through an index remap
+            std::vector<int32_t> src_rows(take_src);
+            DevBuf ib;
+            if ((st = ensure(ib, (size_t)na * 8)) != RFD_OK) break;
+            int32_t *d_src = (int32_t *)ib.p, *d_dst = d_src + na;
+            if ((e = cudaMemcpyAsync(d_src, src_rows.data(), na * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(d_dst, dst.data(), na * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+                (void)cudaGetLastError();
+                set_error("cudaMemcpyAsync failed: %s", cudaGetErrorString(e));
+                st = RFD_ERR_CUDA;
+                release(ib);
+                break;
+            }
+            k_scatter_fit_rows<<<(unsigned)na, 128, 0, s>>>(t_taps, t_lag, t_sig, t_match, d_src, d_dst, K, k_stride,
+                                                            taps, lag, sigma, match, k_out);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            release(ib);
+            if (e != cudaSuccess) {
+                set_error("scattering the fitted taps failed: %s", cudaGetErrorString(e));
+                st = RFD_ERR_CUDA;
+                break;
+            }
+            count_launch();
+        }
+        pending.swap(still);
+    }
+    release(buf);
+    return st;
 }
 
 }  // namespace rfd
