@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--n-tmpl", type=int, default=None, help="smaller bank (profiling cases only)")
     ap.add_argument("--n-ref", type=int, default=None, help="fewer references (profiling cases only)")
     ap.add_argument("--no-graph", action="store_true", help="separate launches instead of one CUDA graph")
+    ap.add_argument("--taps", default="windowed", choices=["windowed", "fit"],
+                    help="fit: the chi^2-fitted ridge taps of Sec. V.A (with --match-target, K per template is "
+                         "the smallest bucket reaching it; buckets 32..512 for a fixed-K config)")
+    ap.add_argument("--match-target", type=float, default=0.99)
+    ap.add_argument("--ridge", type=float, default=1e-6)
     ap.add_argument("--long-k", type=int, default=None,
                     help="fix the plan's long_k instead of autotuning (profiling cases)")
     ap.add_argument("--n-train", type=int, default=200000, help="learned taps: training tap sets (config 4)")
@@ -367,9 +372,10 @@ class GpuSearch:
     """Set-up (templates, taps, autotuned plan) and the per-segment search as one CUDA graph."""
 
     def __init__(self, cfg, bank, data, precision, device, use_graph=True, autotune_cache=None, learned=None,
-                 options=None, reuse=None):
+                 options=None, reuse=None, fit=None):
         self.learned = learned
         self.reuse = reuse
+        self.fit = fit
         self.fixed_options = options
         import torch
         import paper_2601_18835_gb300 as rfd
@@ -407,6 +413,15 @@ class GpuSearch:
             r = self.reuse
             self.taps, self.lag, self.sig, self.match = r.taps, r.lag, r.sig, r.match
             kout.copy_(torch.from_numpy(r.K.astype(np.int32)))
+        elif self.fit is not None:
+            # Sec. V.A: chi^2-fitted ridge taps, K per template from the match target
+            buckets = list(cfg.k_buckets) if bucketed else [32, 64, 128, 256, 512]
+            k_stride = max(buckets)
+            self.taps = torch.zeros((J, k_stride), dtype=torch.complex64, device="cuda")
+            rfd.make_taps_fit(self.ctx, self.grid, self.psd, bank.ref_params(), bank.params(), bank.ref_of_tmpl,
+                              None, k_stride, cfg.tukey_alpha, self.taps, self.lag, self.sig, self.match,
+                              ridge=self.fit["ridge"], buckets=buckets, match_target=self.fit["target"], k_out=kout,
+                              stream=self.stream)
         elif self.learned is not None:
             self.taps, self.lag, self.sig, self.learned_report = learned_taps(
                 cfg, bank, self.ctx, self.grid, self.psd, self.stream, **self.learned)
@@ -578,8 +593,10 @@ def run_ours(args):
         learned = {"n_train": args.n_train, "epochs": args.epochs, "dense_train": dense_train,
                    "spot_stride": args.spot_stride}
     tune_cache = os.path.join(ROOT, "paper_2601_18835_gb300", "_build", "autotune.json")
+    fit = {"target": args.match_target, "ridge": args.ridge} if args.taps == "fit" else None
     s = GpuSearch(cfg, bank, data, prec, local, use_graph=not args.no_graph, autotune_cache=tune_cache,
-                  learned=learned, options={"mix_k": 1, "long_k": args.long_k} if args.long_k is not None else None)
+                  learned=learned, options={"mix_k": 1, "long_k": args.long_k} if args.long_k is not None else None,
+                  fit=fit)
     J, dur = bank.n_tmpl, cfg.duration
 
     def barrier():
@@ -706,8 +723,12 @@ def run_ours(args):
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": precision_name, "data": "synthetic",
         "config": {"workload": cfg.name, "n_tmpl": J, "n_ref": bank.n_ref,
-                   "k": cfg.k if cfg.k else {"buckets": list(cfg.k_buckets),
-                                             "histogram": {int(b): int((s.K == b).sum()) for b in cfg.k_buckets}},
+                   "k": (cfg.k if (cfg.k and fit is None) else
+                         {"buckets": sorted(set(int(x) for x in s.K)),
+                          "histogram": {int(b): int((s.K == b).sum()) for b in sorted(set(int(x) for x in s.K))},
+                          "mean": float(s.K.mean())}),
+                   "taps": ("chi2 fit, ridge %g, K to match %g" % (args.ridge, args.match_target))
+                   if fit is not None else "windowed",
                    "n": cfg.n, "fs": cfg.fs,
                    "segment_s": dur, "window": cfg.window, "threshold": cfg.threshold,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if ws > 1 else "single"},
