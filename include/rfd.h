@@ -354,6 +354,43 @@ rfd_status rfd_findchirp(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_
 rfd_status rfd_ifft_c2c(rfd_ctx *ctx, int64_t n, int32_t batch, const void *in_dev,
                         void *out_dev, void *stream);
 
+/* ------------------------------------------------------------------ sub-band chi^2
+ * The time-frequency chi^2 signal-consistency test through the ratio filter (Sec. VI): the
+ * reference's band is split into p sub-bands of equal reference SNR (w_k = 4 df |h_ref,k|^2 / S_k;
+ * edge e_b is one past the first bin at which the running FP64 sum of w from k_lo reaches
+ * b W / p); the data are matched-filtered per sub-band once per reference; a template's
+ * sub-band SNRs at a trigger are its ratio FIR (Eq. 3) of the reference's sub-band series,
+ *   z_b = (1/sigma_eff) sum_k rho[k] q_r,b[(t - s - k) mod n],  z = sum_b z_b,
+ * and chi^2 = sum_b |z_b - u_b z|^2 / u_b with u_b the effective template's share of power in
+ * band b (2 (p - 1) degrees of freedom in Gaussian noise).  Evaluated at the triggers only. */
+typedef struct rfd_subband rfd_subband;
+/* p in [2, 64]; computes the band edges (synchronous).  rfd_subband_edges copies them out as
+ * int32 [n_ref][p + 1]. */
+rfd_status rfd_subband_create(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_dev,
+                              const rfd_params *refs_host, int32_t n_ref, int32_t p,
+                              rfd_subband **out);
+void rfd_subband_destroy(rfd_subband *sb);
+rfd_status rfd_subband_edges(const rfd_subband *sb, int32_t *edges_host);
+/* q_r,b of every reference and band: qband_dev complex64 [n_ref][p][ld], ld = rfd_qref_ld(n,
+ * halo), wrap halo as for rfd_filter_reference; href_dev as for rfd_filter_reference. */
+rfd_status rfd_subband_filter_reference(rfd_subband *sb, const void *dtilde_dev, const double *psd_dev,
+                                        const void *href_dev, int32_t halo, void *qband_dev,
+                                        void *stream);
+/* u_dev float [n_tmpl][p]: each template's band shares (forward FFT of its placed taps).
+ * taps_dev complex64 [n_tmpl][k_stride], k_dev / lag_dev int32 [n_tmpl] (device), ref_of_host
+ * int32 [n_tmpl].  Per bank, set-up.  Synchronises the stream. */
+rfd_status rfd_subband_shares(rfd_subband *sb, const double *psd_dev, const void *taps_dev,
+                              int32_t k_stride, const int32_t *k_dev, const int32_t *lag_dev,
+                              const int32_t *ref_of_host, int32_t n_tmpl, float *u_dev, void *stream);
+/* chi^2 of each trigger (rfd_trigger [n_trig], device) into chi2_dev float [n_trig]; zb_dev
+ * complex64 [n_trig][p] (may be NULL) receives the sub-band SNRs.  sigma_dev float64 [n_tmpl].
+ * Synchronises the stream. */
+rfd_status rfd_subband_chi2(rfd_subband *sb, const void *qband_dev, int32_t halo, const void *taps_dev,
+                            int32_t k_stride, const int32_t *k_dev, const int32_t *lag_dev,
+                            const double *sigma_dev, const float *u_dev, const int32_t *ref_of_host,
+                            int32_t n_tmpl, const rfd_trigger *trig_dev, int64_t n_trig,
+                            float *chi2_dev, void *zb_dev, void *stream);
+
 /* ------------------------------------------------------------------ learned taps
  * A surrogate for make_taps: one network per reference maps a template to 128 complex taps
  * at the network's fixed lag.  Inputs (20): the features

@@ -21,7 +21,7 @@ from . import _native
 from ._native import (CANDIDATE_DTYPE, PN_SO, PN_TIDAL, PREC_BF16X3, PREC_FP16X3, PREC_FP32,  # noqa: F401
                       TRIGGER_DTYPE, RfdError, check)
 
-__all__ = ["Context", "Plan", "Search", "Mlp", "grid", "gen_templates", "make_taps", "make_taps_fit",
+__all__ = ["Context", "Plan", "Search", "Mlp", "Subband", "grid", "gen_templates", "make_taps", "make_taps_fit",
            "make_taps_at_lag",
            "filter_reference",
            "find_triggers", "find_triggers_noalloc", "findchirp", "ifft_c2c", "qref_ld", "candidates_to_numpy",
@@ -413,6 +413,56 @@ class Mlp:
     def close(self):
         if self.handle:
             _lib().rfd_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Subband:
+    """Sub-band chi^2 through the ratio filter (include/rfd.h, "sub-band chi^2")."""
+
+    def __init__(self, ctx, g, psd, refs, p=8):
+        ra, nr = _params(refs)
+        h = ctypes.c_void_p()
+        check(_lib().rfd_subband_create(ctx.handle, ctypes.byref(g), _ptr(psd), ra, nr, int(p), ctypes.byref(h)))
+        self.handle, self.n_ref, self.p, self.n = h, nr, int(p), int(g.n)
+
+    def edges(self):
+        e = np.empty((self.n_ref, self.p + 1), dtype=np.int32)
+        check(_lib().rfd_subband_edges(self.handle, e.ctypes.data_as(ctypes.c_void_p)))
+        return e
+
+    def filter_reference(self, dtilde, psd, href, halo, out=None, stream=None):
+        ld = qref_ld(self.n, halo)
+        if out is None:
+            out = torch.zeros((self.n_ref, self.p, ld), dtype=torch.complex64, device="cuda")
+        check(_lib().rfd_subband_filter_reference(self.handle, _ptr(dtilde), _ptr(psd), _ptr(href), int(halo),
+                                                  _ptr(out), _stream(stream)))
+        return out
+
+    def shares(self, psd, taps, k, lag, ref_of, stream=None):
+        ro, rop = _i32_host(ref_of)
+        u = torch.zeros((len(ro), self.p), dtype=torch.float32, device="cuda")
+        check(_lib().rfd_subband_shares(self.handle, _ptr(psd), _ptr(taps), int(taps.shape[-1]), _ptr(k), _ptr(lag),
+                                        rop, len(ro), _ptr(u), _stream(stream)))
+        return u
+
+    def chi2(self, qband, halo, taps, k, lag, sigma, u, ref_of, trig, n_trig, zb=False, stream=None):
+        ro, rop = _i32_host(ref_of)
+        c = torch.zeros(max(int(n_trig), 1), dtype=torch.float32, device="cuda")
+        z = torch.zeros((max(int(n_trig), 1), self.p), dtype=torch.complex64, device="cuda") if zb else None
+        check(_lib().rfd_subband_chi2(self.handle, _ptr(qband), int(halo), _ptr(taps), int(taps.shape[-1]), _ptr(k),
+                                      _ptr(lag), _ptr(sigma), _ptr(u), rop, len(ro), _ptr(trig), int(n_trig), _ptr(c),
+                                      _ptr(z), _stream(stream)))
+        return (c[:n_trig], z[:n_trig] if zb else None)
+
+    def close(self):
+        if self.handle:
+            _lib().rfd_subband_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

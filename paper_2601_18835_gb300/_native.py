@@ -93,6 +93,12 @@ SIGNATURES = {
                                     _dbl, _vp, _vp, _vp, _vp]),
     "rfd_make_taps_fit": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _dbl,
                                  _dbl, _i32, _dbl, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "rfd_subband_create": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _i32, ctypes.POINTER(_vp)]),
+    "rfd_subband_destroy": (None, [_vp]),
+    "rfd_subband_edges": (_i32, [_vp, _vp]),
+    "rfd_subband_filter_reference": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
+    "rfd_subband_shares": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32, _vp, _vp]),
+    "rfd_subband_chi2": (_i32, [_vp, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _i64, _vp, _vp, _vp]),
     "rfd_mlp_param_count": (_i64, []),
     "rfd_mlp_create": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, ctypes.POINTER(_vp)]),
     "rfd_mlp_destroy": (None, [_vp]),
