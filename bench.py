@@ -53,6 +53,8 @@ def parse():
                     help="fit: the chi^2-fitted ridge taps of Sec. V.A (with --match-target, K per template is "
                          "the smallest bucket reaching it; buckets 32..512 for a fixed-K config)")
     ap.add_argument("--match-target", type=float, default=0.99)
+    ap.add_argument("--chisq", type=int, default=0,
+                    help="also time the sub-band chi^2 (this many bands) of each step's triggers")
     ap.add_argument("--ridge", type=float, default=1e-6)
     ap.add_argument("--long-k", type=int, default=None,
                     help="fix the plan's long_k instead of autotuning (profiling cases)")
@@ -680,6 +682,33 @@ def run_ours(args):
     roof["kernel_ms"] = filt_s * 1e3
     roof["algorithmic_flops_per_launch"] = alg_flops
 
+    chisq_rep = None
+    if args.chisq and prec != 0:
+        # the sub-band chi^2 of the step's triggers: per-band reference series (once per segment)
+        # and the per-trigger sub-band FIRs; the band shares are per-bank set-up
+        sb = rfd.Subband(s.ctx, s.grid, s.psd, bank.ref_params(), args.chisq)
+        kd = torch.from_numpy(s.K.astype(np.int32)).cuda()
+        with torch.cuda.stream(s.stream):
+            u = sb.shares(s.psd, s.taps, kd, s.lag, bank.ref_of_tmpl, stream=s.stream)
+            qb = sb.filter_reference(s.d, s.psd, s.href, s.halo, stream=s.stream)
+            sig = s.sig
+            nt_step = s.step()[0]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            for _ in range(2):
+                ev[0].record(s.stream)
+                sb.filter_reference(s.d, s.psd, s.href, s.halo, out=qb, stream=s.stream)
+                ev[1].record(s.stream)
+                c2, _ = sb.chi2(qb, s.halo, s.taps, kd, s.lag, sig, u, bank.ref_of_tmpl, s.trig, nt_step,
+                                stream=s.stream)
+                ev[2].record(s.stream)
+            torch.cuda.synchronize()
+        c2 = c2.cpu().numpy()
+        chisq_rep = {"bands": args.chisq, "band_filter_ms": ev[0].elapsed_time(ev[1]),
+                     "chi2_ms": ev[1].elapsed_time(ev[2]), "triggers": int(nt_step),
+                     "chi2_median_over_dof": float(np.median(c2) / (2 * (args.chisq - 1))) if nt_step else None}
+        sb.close()
+        del qb
+
     comparisons = {}
     if not args.no_compare and rank == 0:
         if prec != 0:
@@ -750,6 +779,8 @@ def run_ours(args):
     }
     if s.learned_report is not None:
         line["learned_taps"] = s.learned_report
+    if chisq_rep is not None:
+        line["subband_chi2"] = chisq_rep
     s.close()
     if rank == 0:
         print(json.dumps(line))
