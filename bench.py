@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--ridge", type=float, default=1e-6)
     ap.add_argument("--long-k", type=int, default=None,
                     help="fix the plan's long_k instead of autotuning (profiling cases)")
+    ap.add_argument("--fft-k", type=int, default=None,
+                    help="fix the plan's fft_k (templates with fft_k < K <= 1024 on the block-FFT kernel) "
+                         "instead of autotuning")
     ap.add_argument("--n-train", type=int, default=200000, help="learned taps: training tap sets (config 4)")
     ap.add_argument("--epochs", type=int, default=400, help="learned taps: training epochs (config 4)")
     ap.add_argument("--spot-stride", type=int, default=8, help="learned taps: one spot check per this many templates")
@@ -149,6 +152,69 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------- helpers
+def roofline(prec, family, K, options, n, n_ref, secs, exec_flops, peaks, peak_kind):
+    """Roofline entry of one kernel family over the templates with tap counts K, one launch of
+    secs seconds: the FP32 direct FIR or the block-FFT kernel against the derived FP32 ALU peak,
+    the tensor-core contraction against the measured sustained bf16 peak."""
+    alg = 8.0 * float(np.asarray(K, dtype=np.float64).sum()) * n
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    fp32_src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+    if prec == 0:
+        kernel, src = "k_fir32", "fir32.cu"
+        roof = {"bound": "alu", "achieved": alg / secs / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                "peak_source": fp32_src}
+    elif family == "fft":
+        kernel, src = "k_block_spectra+k_rf_fft", "rf_fft.cu"
+        work = block_fft_flops(K, {"fft_k": 0}, n, n_ref)
+        roof = {"bound": "alu", "achieved": work / secs / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                "peak_source": fp32_src,
+                "work": "nominal FFT flops: per template and 2048-sample block 2048 (6 + 5 log2 2048), "
+                        "plus the same transform per reference and block",
+                "direct_fir_equiv_tflops": alg / secs / 1e12}
+    else:
+        # templates with K > long_k run in k_rf_tc_long (templates on M, time on N), the rest in k_rf_tc
+        long_k = int((options or {}).get("long_k", 64))
+        n_long = int((np.asarray(K) > long_k).sum())
+        if n_long == len(K):
+            kernel, src = "k_rf_tc_long", "rf_tc_long.cu"
+        elif n_long == 0:
+            kernel, src = "k_rf_tc", "rf_tc.cu"
+        else:
+            kernel, src = "k_rf_tc_long+k_rf_tc", "rf_tc_long.cu"
+        peak_tf = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": alg / secs / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                "peak_source": "%s bf16 dense sustained (fp16 has the same dense rate)" % peak_kind,
+                "executed_tflops": exec_flops / secs / 1e12,
+                "executed_frac": exec_flops / secs / 1e12 / peak_tf}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = recorded_traffic(kernel, src)
+    roof["kernel"] = kernel
+    roof["kernel_ms"] = secs * 1e3
+    roof["algorithmic_flops_per_launch"] = alg
+    return roof
+
+
+def fft_templates(K, options):
+    """Templates a plan with these options sends to the block-FFT kernel (fft_k < K <= 1024)."""
+    fft_k = int((options or {}).get("fft_k", 4096))
+    K = np.asarray(K)
+    return int(((K > fft_k) & (K <= 1024)).sum())
+
+
+def block_fft_flops(K, options, n, n_ref):
+    """Nominal flops of one block-FFT pass: 2048 (6 + 5 log2 2048) per template and block, and a
+    forward transform per reference and block (blocks of 2048 - K_max + 1 outputs)."""
+    fft_k = int((options or {}).get("fft_k", 4096))
+    K = np.asarray(K)
+    sel = (K > fft_k) & (K <= 1024)
+    if not sel.any():
+        return 0.0
+    M = 2048
+    L = M - int(K[sel].max()) + 1
+    nb = -(-n // L)
+    return float(sel.sum()) * nb * M * (6 + 5 * 11) + float(n_ref) * nb * M * 5 * 11
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -393,6 +459,7 @@ class GpuSearch:
 
     def _setup(self, cfg, bank, data, precision, device, autotune, autotune_cache):
         torch, rfd = self.torch, self.rfd
+        self.precision = precision
         self.ctx = rfd.Context(device)
         self.grid = rfd.grid(cfg.fs, cfg.n, cfg.f_low, cfg.pn_flags)
         self.psd = torch.from_numpy(data.psd).cuda()
@@ -469,6 +536,42 @@ class GpuSearch:
         if self.use_graph:
             self.search = rfd.Search(self.plan, self.d, self.psd, self.href, self.q, self.e, self.cand, self.cnt,
                                      self.trig, self.stream)
+
+    def kernel_parts(self, reps=3):
+        """For a plan that sends some templates to the block-FFT kernel and the rest to the tensor
+        cores: each family's templates in a plan of their own, timed (CUDA events on the search
+        stream, after one warm-up call) on the same q_ref.  Empty for a single-family plan."""
+        torch, rfd = self.torch, self.rfd
+        fft_k = int(self.options.get("fft_k", 4096))
+        sel_fft = (self.K > fft_k) & (self.K <= 1024)
+        if not sel_fft.any() or sel_fft.all():
+            return []
+        parts = []
+        for family, sel in (("direct", ~sel_fft), ("fft", sel_fft)):
+            idx = np.nonzero(sel)[0]
+            it = torch.from_numpy(idx).cuda()
+            opts = {k: v for k, v in self.options.items() if k != "fft_k"}
+            if family == "fft":
+                opts["fft_k"] = 0
+            plan = rfd.Plan(self.ctx, self.grid, self.bank.n_ref, self.bank.ref_of_tmpl[idx], self.K[idx],
+                            self.precision, self.cfg.window, self.cfg.threshold, self.halo, options=opts)
+            plan.set_taps(self.taps[it].contiguous(), self.taps.shape[1], self.lag[it].contiguous(),
+                          self.sig[it].contiguous(), stream=self.stream)
+            ts = []
+            with torch.cuda.stream(self.stream):
+                plan.ratio_filter_batch(self.q, self.e, self.cand, self.cnt, stream=self.stream)
+                for _ in range(reps):
+                    self.flush_l2()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(self.stream)
+                    plan.ratio_filter_batch(self.q, self.e, self.cand, self.cnt, stream=self.stream)
+                    b.record(self.stream)
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b))
+            parts.append({"family": family, "templates": int(len(idx)), "ms": float(np.mean(ts)), "idx": idx,
+                          "executed_flops": plan.executed_flops()})
+            plan.close()
+        return parts
 
     def alg_flops(self):
         return 8.0 * float(self.K.astype(np.float64).sum()) * self.cfg.n
@@ -596,9 +699,15 @@ def run_ours(args):
                    "spot_stride": args.spot_stride}
     tune_cache = os.path.join(ROOT, "paper_2601_18835_gb300", "_build", "autotune.json")
     fit = {"target": args.match_target, "ridge": args.ridge} if args.taps == "fit" else None
+    fixed = None
+    if args.long_k is not None or args.fft_k is not None:
+        fixed = {"mix_k": 1}
+        if args.long_k is not None:
+            fixed["long_k"] = args.long_k
+        if args.fft_k is not None:
+            fixed["fft_k"] = args.fft_k
     s = GpuSearch(cfg, bank, data, prec, local, use_graph=not args.no_graph, autotune_cache=tune_cache,
-                  learned=learned, options={"mix_k": 1, "long_k": args.long_k} if args.long_k is not None else None,
-                  fit=fit)
+                  learned=learned, options=fixed, fit=fit)
     J, dur = bank.n_tmpl, cfg.duration
 
     def barrier():
@@ -650,37 +759,24 @@ def run_ours(args):
         e2e_t.append(time.perf_counter() - t0)
     e2e_value = job_rate(ws, J, dur, max_over_ranks(sum(e2e_t) / len(e2e_t), ws))
 
-    # roofline of the dominant kernel: the ratio-filter contraction
+    # roofline of the dominant kernel: the ratio-filter contraction (or, for a plan that sends
+    # long templates to the block-FFT kernel, whichever family takes longer, timed on its own)
     peaks, peak_kind = measured_peaks()
     filt_s = sum(kernel_ms) / len(kernel_ms) / 1e3
     alg_flops = s.alg_flops()
-    if prec == 0:
-        kernel, src = "k_fir32", "fir32.cu"
-        # FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
-        peak_tf = 152 * 128 * 2 * 2.07e9 / 1e12
-        roof = {"bound": "alu", "achieved": alg_flops / filt_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    parts = s.kernel_parts() if prec != 0 else []
+    if parts:
+        dom = max(parts, key=lambda q: q["ms"])
+        roof = roofline(prec, dom["family"], s.K[dom["idx"]], s.options, cfg.n, bank.n_ref, dom["ms"] / 1e3,
+                        dom["executed_flops"], peaks, peak_kind)
+        for q in parts:
+            q["frac"] = roofline(prec, q["family"], s.K[q["idx"]], s.options, cfg.n, bank.n_ref, q["ms"] / 1e3,
+                                 q["executed_flops"], peaks, peak_kind)["frac"]
+        roof["parts"] = [{k: v for k, v in q.items() if k not in ("idx", "executed_flops")} for q in parts]
     else:
-        # templates with K > long_k run in k_rf_tc_long (templates on M, time on N), the rest in k_rf_tc
-        long_k = int(s.options.get("long_k", 64))
-        n_long = int((s.K > long_k).sum())
-        if n_long == len(s.K):
-            kernel, src = "k_rf_tc_long", "rf_tc_long.cu"
-        elif n_long == 0:
-            kernel, src = "k_rf_tc", "rf_tc.cu"
-        else:
-            kernel, src = "k_rf_tc_long+k_rf_tc", "rf_tc_long.cu"
-        peak_tf = peaks["bf16_tflops_sustained"]
-        exec_flops = s.plan.executed_flops()
-        roof = {"bound": "tensor", "achieved": alg_flops / filt_s / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
-                "peak_source": "%s bf16 dense sustained (fp16 has the same dense rate)" % peak_kind,
-                "executed_tflops": exec_flops / filt_s / 1e12,
-                "executed_frac": exec_flops / filt_s / 1e12 / peak_tf}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = recorded_traffic(kernel, src)
-    roof["kernel"] = kernel
-    roof["kernel_ms"] = filt_s * 1e3
-    roof["algorithmic_flops_per_launch"] = alg_flops
+        family = "fft" if fft_templates(s.K, s.options) == len(s.K) and prec != 0 else "direct"
+        roof = roofline(prec, family, s.K, s.options, cfg.n, bank.n_ref, filt_s,
+                        s.plan.executed_flops() if prec != 0 else 0.0, peaks, peak_kind)
 
     chisq_rep = None
     if args.chisq and prec != 0:

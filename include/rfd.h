@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define RFD_VERSION 2
+#define RFD_VERSION 3
 
 typedef enum {
     RFD_OK = 0,
@@ -236,9 +236,14 @@ typedef struct {
                              on the MMA's M side, 256 output positions on its N side, taps
                              streamed, so every MMA is full width for any K <= 512): 0 = every
                              template, 512 = none (tile_nt[1], tile_nt[2] then apply) */
-    int32_t reserved[2];  /* must be 0 */
+    int32_t fft_k;        /* templates with fft_k < K <= 1024 go to the block-FFT kernel instead
+                             (overlap-save blocks of 2048 samples, FP32 transforms in shared
+                             memory, the paper's own realisation of the FIR): 0 = every template
+                             with K <= 1024, 4096 = none */
+    int32_t reserved;     /* must be 0 */
 } rfd_plan_options;
-/* Fills the defaults: tile_nt = {128, 64, 32}, mix_k = 1, grid_ctas = 0, long_k = 64. */
+/* Fills the defaults: tile_nt = {128, 64, 32}, mix_k = 1, grid_ctas = 0, long_k = 64,
+ * fft_k = 4096. */
 void rfd_plan_options_default(rfd_plan_options *options);
 /* rfd_plan_create with explicit tile choices (NULL = defaults). */
 rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
@@ -297,7 +302,11 @@ rfd_status rfd_find_triggers(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *
  * captures it on `stream`, which must be a created stream (not the legacy default stream),
  * and synchronises.  rfd_search_run launches the graph on `stream`, waits for it, and returns
  * the trigger count in *n_trig_host with the status rules of rfd_find_triggers.  The plan and
- * the buffers must outlive the search; runs of one search must not overlap. */
+ * the buffers must outlive the search; runs of one search must not overlap.  The graph also
+ * holds the context's scratch buffers: while any search exists, a later call that needs a
+ * larger scratch buffer gets a new one and the old block stays allocated (freed when the last
+ * search is destroyed), so other calls on the same context may run between replays, in the
+ * same stream order (not concurrently on another stream). */
 typedef struct rfd_search rfd_search;
 rfd_status rfd_search_create(rfd_plan *plan, const void *dtilde_dev, const double *psd_dev,
                              const void *href_dev, void *qref_dev, int32_t *qscale_dev,
@@ -353,6 +362,15 @@ rfd_status rfd_findchirp(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_
  * with the library's Stockham kernels: in_dev and out_dev may not overlap. */
 rfd_status rfd_ifft_c2c(rfd_ctx *ctx, int64_t n, int32_t batch, const void *in_dev,
                         void *out_dev, void *stream);
+
+/* The same transform in either direction and precision: fp64 = 0 for complex64 rows, 1 for
+ * complex128 rows; inverse = 1 for exp(+2 pi i k m / n), 0 for exp(-2 pi i k m / n); no
+ * normalisation.  n a power of two in [4, 2^24]; for 2^12 <= n <= 2^22 the rows go through the
+ * two-pass (four-step) form, otherwise one pass per radix.  in_dev and out_dev hold batch * n
+ * elements on the device and may not overlap.  RFD_ERR_SHAPE / RFD_ERR_ARG on bad sizes or
+ * pointers, before any launch. */
+rfd_status rfd_fft_c2c(rfd_ctx *ctx, int64_t n, int32_t batch, int32_t fp64, int32_t inverse,
+                       const void *in_dev, void *out_dev, void *stream);
 
 /* ------------------------------------------------------------------ sub-band chi^2
  * The time-frequency chi^2 signal-consistency test through the ratio filter (Sec. VI): the

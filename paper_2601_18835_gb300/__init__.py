@@ -169,7 +169,8 @@ class Plan:
     """One bank's ratio-filter schedule (templates tiled per reference) and packed taps."""
 
     def __init__(self, ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, options=None):
-        """options: dict with any of tile_nt (3 ints), mix_k (0/1), grid_ctas (int), long_k (int)."""
+        """options: dict with any of tile_nt (3 ints), mix_k (0/1), grid_ctas (int), long_k (int),
+        fft_k (int: templates with fft_k < K <= 1024 use the block-FFT kernel)."""
         ro, rop = _i32_host(ref_of)
         kk, kp = _i32_host(k)
         h = ctypes.c_void_p()
@@ -186,6 +187,8 @@ class Plan:
                 opt.grid_ctas = int(options["grid_ctas"])
             if "long_k" in options:
                 opt.long_k = int(options["long_k"])
+            if "fft_k" in options:
+                opt.fft_k = int(options["fft_k"])
         check(_lib().rfd_plan_create_ex(ctx.handle, ctypes.byref(g), int(n_ref), len(ro), rop, kp,
                                         int(precision), int(window), float(threshold), int(halo),
                                         ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))
@@ -300,6 +303,16 @@ def ifft_c2c(ctx, x, out, stream=None):
     n = x.shape[-1]
     batch = x.numel() // n
     check(_lib().rfd_ifft_c2c(ctx.handle, int(n), int(batch), _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+def fft_c2c(ctx, x, out, inverse, stream=None):
+    """Unnormalised FFT of the rows of x (complex64 or complex128, last axis a power of two)."""
+    n = x.shape[-1]
+    batch = x.numel() // n
+    assert x.dtype == out.dtype and x.dtype in (torch.complex64, torch.complex128)
+    check(_lib().rfd_fft_c2c(ctx.handle, int(n), int(batch), int(x.dtype == torch.complex128), int(bool(inverse)),
+                             _ptr(x), _ptr(out), _stream(stream)))
     return out
 
 

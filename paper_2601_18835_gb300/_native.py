@@ -35,7 +35,7 @@ class Grid(ctypes.Structure):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("tile_nt", ctypes.c_int32 * 3), ("mix_k", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
-                ("long_k", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("long_k", ctypes.c_int32), ("fft_k", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -89,6 +89,7 @@ SIGNATURES = {
     "rfd_findchirp": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _vp, _i32, _i32, _flt, _vp, _i64, _vp,
                              _vp]),
     "rfd_ifft_c2c": (_i32, [_vp, _i64, _i32, _vp, _vp, _vp]),
+    "rfd_fft_c2c": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp]),
     "rfd_make_taps_at_lag": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _i32,
                                     _dbl, _vp, _vp, _vp, _vp]),
     "rfd_make_taps_fit": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _dbl,

@@ -2,8 +2,9 @@
 
 The choices (rfd_plan_options): templates per tile for each K class, whether a tile may mix
 templates of different K (padding the short ones) or must split where K changes, the number
-of persistent CTAs, and above which K templates go to the long-tap kernel (templates on the
-MMA's M side, time on its N side).  Each candidate plan is built through the C ABI, given the bank's
+of persistent CTAs, above which K templates go to the long-tap kernel (templates on the
+MMA's M side, time on its N side), and above which K they go to the block-FFT kernel (FP32
+overlap-save transforms on the CUDA cores, cheaper than the contraction for long taps).  Each candidate plan is built through the C ABI, given the bank's
 taps, and timed on the q_ref buffer with CUDA events; the fastest wins.  Results are cached
 in a JSON file keyed by the workload's signature (grid, precision, the (reference, K)
 histogram, the device), so a bank is tuned once.
@@ -25,6 +26,9 @@ DEFAULT_CANDIDATES = [
     {"mix_k": 1, "long_k": 512},
     {"mix_k": 1, "long_k": 128},
     {"mix_k": 1, "long_k": 0},
+    {"mix_k": 1, "fft_k": 256},
+    {"mix_k": 1, "fft_k": 128},
+    {"mix_k": 1, "fft_k": 0},
 ]
 
 

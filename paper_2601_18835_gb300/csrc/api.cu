@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 
 #include "internal.cuh"
@@ -33,6 +34,12 @@ int tl_tile_templates();
 rfd_status tc_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
                      cudaStream_t);
 int tc_rows_per_item();
+int fft_fir_block_len();
+int fft_fir_tile_templates();
+int fft_fir_blocks_per_cta();
+rfd_status fft_pack(rfd_plan *, const float2 *, int32_t, const int32_t *, const double *, cudaStream_t);
+rfd_status fft_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
+                      cudaStream_t);
 
 // Tensor-core tiles: per reference, templates in increasing K, cut so that a tile holds at
 // most 128 templates (64 once its K exceeds 128, 32 once it exceeds 256: the taps image,
@@ -117,6 +124,59 @@ static rfd_status plan_tl_tiles(rfd_plan *p, const std::vector<int32_t> &order, 
     return RFD_OK;
 }
 
+// Block-FFT tiles: per reference, up to 64 templates (order: by reference, then K), appended
+// to the plan's slot order.  Blocks of L = 2048 - K_max + 1 outputs, four per CTA item; item
+// ranges per persistent CTA balance the templates transformed.
+static rfd_status plan_fft_tiles(rfd_plan *p, const std::vector<int32_t> &order, int num_sms,
+                                 const rfd_plan_options &opt) {
+    if (order.empty()) return RFD_OK;
+    const int32_t M = fft_fir_block_len(), nt = fft_fir_tile_templates(), gpc = fft_fir_blocks_per_cta();
+    int32_t kmax = 0;
+    for (int32_t j : order) kmax = std::max(kmax, p->k_of[j]);
+    p->fft_L = M - kmax + 1;
+    p->fft_nb = (int32_t)((p->grid.n + p->fft_L - 1) / p->fft_L);
+    p->fft_nbg = (p->fft_nb + gpc - 1) / gpc;
+    p->fft_slot0 = (int64_t)p->perm.size();
+    size_t i = 0;
+    while (i < order.size()) {
+        const int32_t r = p->ref_of[order[i]];
+        FftTile t{};
+        t.ref = r;
+        t.first = (int32_t)p->perm.size();
+        while (i < order.size() && p->ref_of[order[i]] == r && t.count < nt) {
+            p->perm.push_back(order[i]);
+            ++t.count;
+            ++i;
+        }
+        if (p->fft_refs.empty() || p->fft_refs.back() != r) p->fft_refs.push_back(r);
+        p->fft_tiles.push_back(t);
+    }
+    p->fft_nslots = (int64_t)p->perm.size() - p->fft_slot0;
+    const double log2m = std::log2((double)M);
+    p->fft_flops = (double)p->fft_nslots * p->fft_nb * M * (6.0 + 5.0 * log2m) +
+                   (double)p->fft_refs.size() * p->fft_nb * M * 5.0 * log2m;
+    const int64_t ntiles = (int64_t)p->fft_tiles.size();
+    std::vector<double> cost(ntiles);
+    for (int64_t t = 0; t < ntiles; ++t) cost[t] = (double)p->fft_tiles[t].count + 0.5;
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(opt.grid_ctas > 0 ? opt.grid_ctas : num_sms,
+                                                           ntiles * p->fft_nbg));
+    const std::vector<int64_t> ranges = balanced_ranges(cost, p->fft_nbg, G);
+    p->fft_grid = (int32_t)G;
+    RFD_TRY(fft_stage_twiddles32(p->ctx, 11, &p->fft_stw, 0));
+    RFD_TRY_CUDA(cudaStreamSynchronize(0));
+    RFD_TRY(ensure(p->d_fft_ranges, (G + 1) * sizeof(int64_t)));
+    RFD_TRY_CUDA(cudaMemcpy(p->d_fft_ranges.p, ranges.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    RFD_TRY(ensure(p->d_fft_tiles, ntiles * sizeof(FftTile)));
+    RFD_TRY_CUDA(
+        cudaMemcpy(p->d_fft_tiles.p, p->fft_tiles.data(), ntiles * sizeof(FftTile), cudaMemcpyHostToDevice));
+    RFD_TRY(ensure(p->d_fft_refs, p->fft_refs.size() * sizeof(int32_t)));
+    RFD_TRY_CUDA(cudaMemcpy(p->d_fft_refs.p, p->fft_refs.data(), p->fft_refs.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice));
+    RFD_TRY(ensure(p->d_fft_P, (size_t)p->fft_nslots * M * sizeof(float2)));
+    RFD_TRY(ensure(p->d_fft_X, (size_t)p->n_ref * p->fft_nb * M * sizeof(float2)));
+    return RFD_OK;
+}
+
 static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &all, int num_sms,
                                 const rfd_plan_options &opt) {
     const int64_t n_tt = p->grid.n / tc_rows_per_item();
@@ -194,12 +254,42 @@ void set_error(const char *fmt, ...) {
     va_end(ap);
 }
 
+// A captured graph (rfd_search) holds raw pointers into workspaces and plan buffers.  While
+// any graph is alive, a block that is replaced or released is kept (retired) instead of
+// freed, and the retired blocks are freed when the last graph goes away.
+static std::mutex g_retire_mu;
+static int g_live_graphs = 0;
+static std::vector<void *> g_retired;
+
+void graphs_pin() {
+    std::lock_guard<std::mutex> lk(g_retire_mu);
+    ++g_live_graphs;
+}
+
+void graphs_unpin() {
+    std::lock_guard<std::mutex> lk(g_retire_mu);
+    if (--g_live_graphs > 0) return;
+    g_live_graphs = 0;
+    if (g_retired.empty()) return;
+    cudaDeviceSynchronize();
+    for (void *p : g_retired) cudaFree(p);
+    g_retired.clear();
+}
+
+static void free_or_retire(void *p) {
+    std::lock_guard<std::mutex> lk(g_retire_mu);
+    if (g_live_graphs > 0)
+        g_retired.push_back(p);
+    else
+        cudaFree(p);
+}
+
 rfd_status ensure(DevBuf &b, size_t bytes) {
     if (bytes <= b.bytes && b.p) return RFD_OK;
     if (b.p) {
         // earlier stream work may still use the old block
         RFD_TRY_CUDA(cudaDeviceSynchronize());
-        RFD_TRY_CUDA(cudaFree(b.p));
+        free_or_retire(b.p);
         b.p = nullptr;
         b.bytes = 0;
     }
@@ -216,7 +306,7 @@ rfd_status ensure(DevBuf &b, size_t bytes) {
 }
 
 void release(DevBuf &b) {
-    if (b.p) cudaFree(b.p);
+    if (b.p) free_or_retire(b.p);
     b.p = nullptr;
     b.bytes = 0;
 }
@@ -324,6 +414,8 @@ void rfd_ctx_destroy(rfd_ctx *ctx) {
     cudaDeviceSynchronize();
     for (auto &kv : ctx->tw32) cudaFree(kv.second);
     for (auto &kv : ctx->tw64) cudaFree(kv.second);
+    for (auto &kv : ctx->stw32) cudaFree(kv.second);
+    for (auto &kv : ctx->stw64) cudaFree(kv.second);
     for (auto &b : ctx->ws) release(b);
     delete ctx;
 }
@@ -509,6 +601,7 @@ void rfd_plan_options_default(rfd_plan_options *o) {
     o->mix_k = 1;
     o->grid_ctas = 0;
     o->long_k = 64;
+    o->fft_k = 4096;
 }
 
 rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
@@ -525,7 +618,8 @@ rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref,
                         "tile_nt[%d]=%d must be a multiple of 16 in [16, %d]", c, opt.tile_nt[c], cap[c]);
         RFD_REQUIRE(opt.grid_ctas >= 0, RFD_ERR_ARG, "grid_ctas must be >= 0");
         RFD_REQUIRE(opt.long_k >= 0 && opt.long_k <= 512, RFD_ERR_ARG, "long_k must be in [0, 512]");
-        RFD_REQUIRE(opt.reserved[0] == 0 && opt.reserved[1] == 0, RFD_ERR_ARG, "reserved options must be 0");
+        RFD_REQUIRE(opt.fft_k >= 0 && opt.fft_k <= 4096, RFD_ERR_ARG, "fft_k must be in [0, 4096]");
+        RFD_REQUIRE(opt.reserved == 0, RFD_ERR_ARG, "reserved options must be 0");
     }
     RFD_REQUIRE(ctx && out, RFD_ERR_ARG, "NULL ctx or out");
     *out = nullptr;
@@ -568,8 +662,14 @@ rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref,
         if (p->ref_of[a] != p->ref_of[b]) return p->ref_of[a] < p->ref_of[b];
         return p->k_of[a] < p->k_of[b];
     });
+    // templates with fft_k < K <= 1024 go to the block-FFT path
+    std::vector<int32_t> order_fft, order_rest;
+    for (int32_t j : order) (p->k_of[j] > opt.fft_k && p->k_of[j] <= 1024 ? order_fft : order_rest).push_back(j);
+    order.swap(order_rest);
     if (precision != RFD_PREC_FP32) {
         rfd_status st = plan_tc_tiles(p, order, ctx->num_sms, opt);
+        if (st == RFD_OK) st = plan_fft_tiles(p, order_fft, ctx->num_sms, opt);
+        if (st == RFD_OK) p->n_slots = (int64_t)p->perm.size();
         if (st == RFD_OK) {
             do {
                 if ((st = ensure(p->d_perm, p->n_slots * sizeof(int32_t))) != RFD_OK) break;
@@ -615,9 +715,10 @@ rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref,
         p->executed_flops += 8.0 * t.k_tile * (double)p->tile_j * (double)g.n;
         i = e;
     }
-    p->n_slots = slot;
-    rfd_status st = RFD_OK;
+    rfd_status st = plan_fft_tiles(p, order_fft, ctx->num_sms, opt);
+    p->n_slots = (int64_t)p->perm.size();
     do {
+        if (st != RFD_OK) break;
         if ((st = ensure(p->d_tiles, p->tiles.size() * sizeof(RfdTile))) != RFD_OK) break;
         if ((st = ensure(p->d_perm, p->n_slots * sizeof(int32_t))) != RFD_OK) break;
         if ((st = ensure(p->d_kslot, p->n_slots * sizeof(int32_t))) != RFD_OK) break;
@@ -659,6 +760,11 @@ void rfd_plan_destroy(rfd_plan *plan) {
     release(plan->d_tl_tiles);
     release(plan->d_tl_ranges);
     release(plan->d_tl_taps);
+    release(plan->d_fft_tiles);
+    release(plan->d_fft_ranges);
+    release(plan->d_fft_refs);
+    release(plan->d_fft_P);
+    release(plan->d_fft_X);
     delete plan;
 }
 
@@ -674,9 +780,29 @@ rfd_status rfd_plan_set_taps(rfd_plan *plan, const void *taps_dev, int32_t k_str
         RFD_TRY(tc_pack(plan, (const float2 *)taps_dev, k_stride, lag_dev, sigma_dev, (cudaStream_t)stream));
         RFD_TRY(tl_pack(plan, (const float2 *)taps_dev, k_stride, lag_dev, sigma_dev, (cudaStream_t)stream));
     }
+    RFD_TRY(fft_pack(plan, (const float2 *)taps_dev, k_stride, lag_dev, sigma_dev, (cudaStream_t)stream));
     plan->taps_set = true;
     return RFD_OK;
 }
+
+}  // extern "C"
+
+namespace rfd {
+// Every filtering kernel of a plan, in order, on one stream (the call and the search graph
+// both go through here).
+rfd_status ratio_filter_enqueue(const rfd_plan *plan, const void *q, const int32_t *qscale, rfd_candidate *cand,
+                                int64_t cap, int64_t *count, cudaStream_t s) {
+    if (plan->precision == RFD_PREC_FP32) {
+        RFD_TRY(fir32_launch(plan, (const float2 *)q, cand, cap, count, s));
+    } else {
+        RFD_TRY(tc_launch(plan, q, qscale, cand, cap, count, s));
+        RFD_TRY(tl_launch(plan, q, qscale, cand, cap, count, s));
+    }
+    return fft_launch(plan, q, qscale, cand, cap, count, s);
+}
+}  // namespace rfd
+
+extern "C" {
 
 rfd_status rfd_ratio_filter_batch(rfd_plan *plan, const void *qref_dev, const int32_t *qscale_dev,
                                   rfd_candidate *cand_dev, int64_t cand_capacity, int64_t *cand_count_dev,
@@ -689,10 +815,7 @@ rfd_status rfd_ratio_filter_batch(rfd_plan *plan, const void *qref_dev, const in
     RFD_TRY_CUDA(cudaSetDevice(plan->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     RFD_TRY_CUDA(cudaMemsetAsync(cand_count_dev, 0, sizeof(int64_t), s));
-    if (plan->precision == RFD_PREC_FP32)
-        return fir32_launch(plan, (const float2 *)qref_dev, cand_dev, cand_capacity, cand_count_dev, s);
-    RFD_TRY(tc_launch(plan, qref_dev, qscale_dev, cand_dev, cand_capacity, cand_count_dev, s));
-    return tl_launch(plan, qref_dev, qscale_dev, cand_dev, cand_capacity, cand_count_dev, s);
+    return ratio_filter_enqueue(plan, qref_dev, qscale_dev, cand_dev, cand_capacity, cand_count_dev, s);
 }
 
 double rfd_plan_executed_flops(const rfd_plan *plan) { return plan ? plan->executed_flops : 0.0; }
@@ -736,6 +859,26 @@ rfd_status rfd_ifft_c2c(rfd_ctx *ctx, int64_t n, int32_t batch, const void *in_d
     RFD_TRY(ensure(ctx->ws[14], (size_t)batch * n * sizeof(float2)));
     return fft_c2c<float>(ctx, n, batch, (const float2 *)in_dev, n, (float2 *)out_dev, n, (float2 *)ctx->ws[14].p,
                           true, (cudaStream_t)stream);
+}
+
+rfd_status rfd_fft_c2c(rfd_ctx *ctx, int64_t n, int32_t batch, int32_t fp64, int32_t inverse, const void *in_dev,
+                       void *out_dev, void *stream) {
+    RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
+    RFD_REQUIRE(n >= 4 && n <= (int64_t(1) << 24) && (n & (n - 1)) == 0, RFD_ERR_SHAPE, "n must be a power of two");
+    RFD_REQUIRE(batch >= 0, RFD_ERR_SHAPE, "batch < 0");
+    RFD_REQUIRE(fp64 == 0 || fp64 == 1, RFD_ERR_ARG, "fp64 must be 0 or 1");
+    RFD_REQUIRE(inverse == 0 || inverse == 1, RFD_ERR_ARG, "inverse must be 0 or 1");
+    if (batch == 0) return RFD_OK;
+    RFD_REQUIRE(in_dev && out_dev && in_dev != out_dev, RFD_ERR_ARG, "NULL or aliased buffers");
+    RFD_TRY_CUDA(cudaSetDevice(ctx->device));
+    if (fp64) {
+        RFD_TRY(ensure(ctx->ws[14], (size_t)batch * n * sizeof(double2)));
+        return fft_c2c<double>(ctx, n, batch, (const double2 *)in_dev, n, (double2 *)out_dev, n,
+                               (double2 *)ctx->ws[14].p, inverse != 0, (cudaStream_t)stream);
+    }
+    RFD_TRY(ensure(ctx->ws[14], (size_t)batch * n * sizeof(float2)));
+    return fft_c2c<float>(ctx, n, batch, (const float2 *)in_dev, n, (float2 *)out_dev, n, (float2 *)ctx->ws[14].p,
+                          inverse != 0, (cudaStream_t)stream);
 }
 
 }  // extern "C"

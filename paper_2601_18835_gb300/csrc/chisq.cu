@@ -175,6 +175,7 @@ struct rfd_subband {
     std::vector<rfd::PNParams> refs;
     std::vector<int32_t> edges;        // [R][p + 1]
     rfd::DevBuf d_edges, d_refs, d_ref_of, d_work;
+    rfd::DevBuf w1, w2, w3;            // own FFT scratch (not the context's shared slots)
 };
 
 using namespace rfd;
@@ -187,6 +188,9 @@ void rfd_subband_destroy(rfd_subband *S) {
     release(S->d_refs);
     release(S->d_ref_of);
     release(S->d_work);
+    release(S->w1);
+    release(S->w2);
+    release(S->w3);
     delete S;
 }
 
@@ -265,17 +269,17 @@ rfd_status rfd_subband_filter_reference(rfd_subband *S, const void *dtilde_dev, 
     const int64_t n = g.n, ld = rfd_qref_ld(n, halo), rows = (int64_t)S->R * S->p;
     int64_t B = std::max<int64_t>(1, ((int64_t)1 << 30) / (n * (int64_t)sizeof(float2)));
     B = std::min<int64_t>(std::min<int64_t>(B, rows), 65535);
-    RFD_TRY(ensure(ctx->ws[1], B * n * sizeof(float2)));
-    RFD_TRY(ensure(ctx->ws[2], B * n * sizeof(float2)));
-    RFD_TRY(ensure(ctx->ws[3], B * n * sizeof(float2)));
-    float2 *c = (float2 *)ctx->ws[1].p, *q = (float2 *)ctx->ws[2].p;
+    RFD_TRY(ensure(S->w1, B * n * sizeof(float2)));
+    RFD_TRY(ensure(S->w2, B * n * sizeof(float2)));
+    RFD_TRY(ensure(S->w3, B * n * sizeof(float2)));
+    float2 *c = (float2 *)S->w1.p, *q = (float2 *)S->w2.p;
     for (int64_t r0 = 0; r0 < rows; r0 += B) {
         const int64_t nb = std::min<int64_t>(B, rows - r0);
         k_band_spectrum<<<dim3((unsigned)(n / 256), (unsigned)nb), 256, 0, s>>>(
             (const float2 *)dtilde_dev, psd_dev, (const float2 *)href_dev, g.nf, g.df, n,
             (const int32_t *)S->d_edges.p, S->p, r0, c);
         RFD_LAUNCH_CHECK();
-        RFD_TRY(fft_c2c<float>(ctx, n, nb, c, n, q, n, (float2 *)ctx->ws[3].p, true, s));
+        RFD_TRY(fft_c2c<float>(ctx, n, nb, c, n, q, n, (float2 *)S->w3.p, true, s));
         k_band_finalize<<<dim3((unsigned)((ld + 255) / 256), (unsigned)nb), 256, 0, s>>>(q, n, ld, n + halo,
                                                                                        (float2 *)qband_dev + r0 * ld);
         RFD_LAUNCH_CHECK();
@@ -301,16 +305,16 @@ rfd_status rfd_subband_shares(rfd_subband *S, const double *psd_dev, const void 
     RFD_TRY_CUDA(cudaMemcpyAsync(S->d_ref_of.p, ref_of_host, (size_t)n_tmpl * 4, cudaMemcpyHostToDevice, s));
     int64_t B = std::max<int64_t>(1, ((int64_t)1 << 30) / (n * (int64_t)sizeof(float2)));
     B = std::min<int64_t>(B, n_tmpl);
-    RFD_TRY(ensure(ctx->ws[1], B * n * sizeof(float2)));
-    RFD_TRY(ensure(ctx->ws[2], B * n * sizeof(float2)));
-    RFD_TRY(ensure(ctx->ws[3], B * n * sizeof(float2)));
-    float2 *a = (float2 *)ctx->ws[1].p, *A = (float2 *)ctx->ws[2].p;
+    RFD_TRY(ensure(S->w1, B * n * sizeof(float2)));
+    RFD_TRY(ensure(S->w2, B * n * sizeof(float2)));
+    RFD_TRY(ensure(S->w3, B * n * sizeof(float2)));
+    float2 *a = (float2 *)S->w1.p, *A = (float2 *)S->w2.p;
     for (int64_t j0 = 0; j0 < n_tmpl; j0 += B) {
         const int64_t nb = std::min<int64_t>(B, n_tmpl - j0);
         RFD_TRY_CUDA(cudaMemsetAsync(a, 0, nb * n * sizeof(float2), s));
         k_place_rows<<<(unsigned)nb, 128, 0, s>>>((const float2 *)taps_dev, k_stride, k_dev, lag_dev, j0, n, a);
         RFD_LAUNCH_CHECK();
-        RFD_TRY(fft_c2c<float>(ctx, n, nb, a, n, A, n, (float2 *)ctx->ws[3].p, false, s));
+        RFD_TRY(fft_c2c<float>(ctx, n, nb, a, n, A, n, (float2 *)S->w3.p, false, s));
         k_band_shares<<<(unsigned)nb, 256, 0, s>>>(A, n, (const int32_t *)S->d_edges.p, S->p,
                                                    (const int32_t *)S->d_ref_of.p, psd_dev, g.df, j0, u_dev);
         RFD_LAUNCH_CHECK();

@@ -89,6 +89,10 @@ struct DevBuf {
 };
 // Grow-only device buffer.  Growing synchronises the device before freeing the old block.
 rfd_status ensure(DevBuf &b, size_t bytes);
+// While a captured graph is alive (graphs_pin .. graphs_unpin), ensure() and release() keep
+// replaced blocks allocated, so the graph's pointers stay valid.
+void graphs_pin();
+void graphs_unpin();
 void release(DevBuf &b);
 
 template <typename T> struct Cplx;
@@ -103,6 +107,11 @@ template <typename T>
 rfd_status fft_c2c(rfd_ctx *ctx, int64_t n, int64_t batch, const typename Cplx<T>::type *in,
                    int64_t in_stride, typename Cplx<T>::type *out, int64_t out_stride,
                    typename Cplx<T>::type *tmp, bool inverse, cudaStream_t s);
+// Stage twiddles of a length-2^logL Stockham transform (the passes in order: a radix-2, -4 or
+// -8 pass first when logL is not a multiple of 4, then radix 16; pass p with radix R after
+// ns = product of the earlier radices holds exp(+2 pi i r k / (ns R)) at
+// base_p + (r - 1) ns + k), FP32, cached in the context.
+rfd_status fft_stage_twiddles32(rfd_ctx *ctx, int logL, const float2 **out, cudaStream_t s);
 
 // ------------------------------------------------------------------ taps (taps.cu)
 // lag_in empty: the lag is searched (Sec. V placement); otherwise it is taken from lag_in.
@@ -146,6 +155,7 @@ struct rfd_ctx {
     int device = 0;
     int num_sms = 0;
     std::map<int64_t, void *> tw32, tw64;   // twiddle tables exp(+2 pi i m / n), m < n
+    std::map<int64_t, void *> stw32, stw64; // per-pass (stage) twiddles of short transforms, by log2 length
     rfd::DevBuf ws[16];                      // scratch slots, see the users for their roles
 };
 
@@ -166,6 +176,11 @@ struct TcTile {
     int32_t nt, nch, nk16, kpad;
     int64_t taps_off;
     int32_t taps_bytes, pad;
+};
+
+// Tile of the block-FFT ratio filter (rf_fft.cu): up to 64 templates of one reference.
+struct FftTile {
+    int32_t ref, first, count, pad;
 };
 
 struct rfd_plan {
@@ -199,4 +214,12 @@ struct rfd_plan {
     uint32_t tc_taps_cap = 0, tc_win = 0;
     int32_t tc_grid = 0;
     double executed_flops = 0.0;     // tensor (or FMA) flops one ratio_filter_batch executes
+    // block-FFT path (rf_fft.cu): templates with fft_k < K <= 1024
+    std::vector<FftTile> fft_tiles;
+    std::vector<int32_t> fft_refs;   // references with block-FFT templates
+    rfd::DevBuf d_fft_tiles, d_fft_ranges, d_fft_refs, d_fft_P, d_fft_X;
+    const float2 *fft_stw = nullptr; // stage twiddles of length 2048 (context-owned)
+    int32_t fft_grid = 0, fft_L = 0, fft_nb = 0, fft_nbg = 0;
+    int64_t fft_slot0 = 0, fft_nslots = 0;
+    double fft_flops = 0.0;          // nominal FP32 flops of the block-FFT path per call
 };

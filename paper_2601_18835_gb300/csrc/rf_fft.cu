@@ -1,0 +1,333 @@
+// Block-FFT (overlap-save) realisation of the ratio filter (Eq. 3) on CUDA cores, the form in
+// which the paper applies its short FIR (Sec. III, Table II: FFT blocks of about 2048
+// samples), with the fused trigger epilogue.
+//
+// With off_j = (s_j + K_j - 1) mod n, the FIR of Eq. 3 reads
+//   z_j[(u + off_j) mod n] = sum_{m < K_j} c_j[m] q_r[(u + m) mod n],
+//   c_j[m] = rho_j[K_j - 1 - m] / sigma_eff,j.
+// Output positions u are cut into blocks of L = M - K_max + 1 (M = 2048, K_max the largest K
+// on this path); block b starts at u_0 = b L and sees x_b[i] = q_r[(u_0 + i) mod n], i < M.
+// For l < L no product wraps around the block, so
+//   z_j[(u_0 + l + off_j) mod n] = sum_k X_b[k] P_j[k] exp(+2 pi i k l / M),
+//   X_b[k] = sum_i x_b[i] exp(-2 pi i k i / M)      (per reference and block, every segment),
+//   P_j[k] = (1/M) sum_m c_j[m] exp(+2 pi i k m / M) (per template, when the taps are set).
+// A CTA holds four 128-thread groups, one block b each.  The templates of a tile stream
+// through shared memory (the next template's P_j copied with cp.async while the current one
+// is transformed); every group multiplies its X_b, kept in registers, by P_j, runs the inverse
+// transform (Stockham passes of radix 8, 16, 16 through two padded tiles) and screens |z|^2.
+#include "epilogue.cuh"
+#include "fft_reg.cuh"
+#include "internal.cuh"
+
+namespace rfd {
+
+namespace {
+
+constexpr int kM = 2048;                     // block transform length
+constexpr int kGT = 128;                     // threads per block transform, 16 elements each
+constexpr int kGroups = 4;                   // block transforms per CTA
+constexpr int kThreads = kGT * kGroups;
+constexpr int kTileLd = kM + kM / 16 + 2;    // padded shared-memory tile (one pad per 16)
+constexpr int kTileTemplates = 64;           // templates per tile (one reference)
+
+__device__ __forceinline__ int tpos(int i) { return i + (i >> 4); }
+
+__device__ __forceinline__ void group_bar(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kGT) : "memory");
+}
+
+// Length-2048 transform by one 128-thread group: thread t holds elements t + 128 r (r < 16) in
+// v on entry and on exit (natural order).  Passes: radix 8 (ns = 1) into tile A, radix 16
+// (ns = 8) from A into B, radix 16 (ns = 128) from B into registers.  stw: the stage twiddles
+// of length 2048 (7 + 120 + 1920 entries).  Every thread of the group calls this; bar is the
+// group's named barrier.  Two calls in a row are safe: a thread writes A again only after
+// every thread of the group passed the barrier that follows its reads of A, and likewise B.
+template <bool INV>
+__device__ __forceinline__ void group_fft(float2 (&v)[16], float2 *A, float2 *B, const float2 *stw, int t,
+                                          int bar) {
+    {
+        float2 a[8], b[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            a[r] = v[2 * r];          // butterfly j = t: elements t + 256 r
+            b[r] = v[2 * r + 1];      // butterfly j = t + 128
+        }
+        dft_reg<float, 8, INV>(a);
+        dft_reg<float, 8, INV>(b);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            A[tpos(8 * t + r)] = a[r];
+            A[tpos(8 * (t + kGT) + r)] = b[r];
+        }
+    }
+    group_bar(bar);
+    {
+        const int k = t & 7;
+        float2 a[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) a[r] = A[tpos(t + kGT * r)];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+            const float2 w = stw[7 + (r - 1) * 8 + k];
+            a[r] = INV ? cmul(a[r], w) : cmulc(a[r], w);
+        }
+        dft_reg<float, 16, INV>(a);
+        const int idx = ((t - k) << 4) + k;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) B[tpos(idx + 8 * r)] = a[r];
+    }
+    group_bar(bar);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = B[tpos(t + kGT * r)];
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+        const float2 w = stw[127 + (r - 1) * kGT + t];
+        v[r] = INV ? cmul(v[r], w) : cmulc(v[r], w);
+    }
+    dft_reg<float, 16, INV>(v);
+}
+
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+
+// One template's P (16 KB) into shared memory: 1024 copies of 16 B, two per thread.
+__device__ __forceinline__ void stage_p(float2 *dst, const float2 *__restrict__ src) {
+#pragma unroll
+    for (int c = threadIdx.x; c < kM / 2; c += kThreads) cp_async16(dst + 2 * c, src + 2 * c);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// q_r[m] as FP32 from the stored reference series (complex64, or the four hi/lo planes of
+// the split precisions with hi + lo = q 2^e_r).
+template <int PREC>
+__device__ __forceinline__ float2 load_q(const void *__restrict__ q, int r, int64_t ld, int64_t m, float sc) {
+    if (PREC == RFD_PREC_FP32) return ((const float2 *)q)[(int64_t)r * ld + m];
+    const uint16_t *h = (const uint16_t *)q;
+    const int64_t base = (int64_t)4 * r * ld + m;
+    float v[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const uint16_t u = h[base + p * ld];
+        v[p] = PREC == RFD_PREC_FP16X3 ? __half2float(__ushort_as_half(u)) : __bfloat162float(__ushort_as_bfloat16(u));
+    }
+    return make_float2((v[0] + v[2]) * sc, (v[1] + v[3]) * sc);
+}
+
+// X[r][b][k] for the references in refs (blockIdx.y) and blocks b = 4 blockIdx.x + group.
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_block_spectra(const void *__restrict__ q,
+                                                            const int32_t *__restrict__ qscale, int64_t ld,
+                                                            int64_t n, int32_t L, int32_t nb,
+                                                            const int32_t *__restrict__ refs,
+                                                            float2 *__restrict__ X,
+                                                            const float2 *__restrict__ stw_g) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    float2 *stw = (float2 *)sm;
+    float2 *tl = stw + kM;
+    const int g = threadIdx.x / kGT, t = threadIdx.x % kGT;
+    float2 *TA = tl + (2 * g) * kTileLd, *TB = TA + kTileLd;
+    for (int i = threadIdx.x; i < kM - 1; i += kThreads) stw[i] = stw_g[i];
+    __syncthreads();
+    const int r = refs[blockIdx.y];
+    const int b = blockIdx.x * kGroups + g;
+    const bool bvalid = b < nb;                         // uniform within the group
+    const int64_t u0 = (int64_t)(bvalid ? b : 0) * L;
+    const float sc = PREC == RFD_PREC_FP32 ? 1.f : ldexpf(1.f, -qscale[r]);
+    float2 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = load_q<PREC>(q, r, ld, (u0 + t + kGT * i) & (n - 1), sc);
+    group_fft<false>(v, TA, TB, stw, t, 1 + g);
+    if (bvalid) {
+        float2 *dst = X + ((int64_t)r * nb + b) * kM;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) dst[t + kGT * i] = v[i];
+    }
+}
+
+struct RfFftArgs {
+    const FftTile *tiles;
+    const int64_t *ranges;      // item ranges per CTA; item = tile * nbg + block group
+    int32_t nbg, nb, L;
+    const float2 *X, *stw;
+    const float2 *P;            // [slot - slot0][kM]
+    int64_t slot0;              // first block-FFT slot
+    const int32_t *perm, *off;
+    int64_t n;
+    float thr;
+    uint32_t W;
+    rfd_candidate *cand;
+    int64_t cap;
+    unsigned long long *count;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_rf_fft(const RfFftArgs a) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    float2 *stw = (float2 *)sm;                 // [kM] stage twiddles
+    float2 *Ps = stw + kM;                      // [2][kM] template spectra, double-buffered
+    float2 *tl = Ps + 2 * kM;                   // [kGroups][2][kTileLd]
+    const int g = threadIdx.x / kGT, t = threadIdx.x % kGT;
+    float2 *TA = tl + (2 * g) * kTileLd, *TB = TA + kTileLd;
+    for (int i = threadIdx.x; i < kM - 1; i += kThreads) stw[i] = a.stw[i];
+    const int64_t it0 = a.ranges[blockIdx.x], it1 = a.ranges[blockIdx.x + 1];
+    for (int64_t it = it0; it < it1; ++it) {
+        const int64_t ti = it / a.nbg;
+        const int bg = (int)(it - ti * a.nbg);
+        const FftTile tile = a.tiles[ti];
+        const int b = bg * kGroups + g;
+        const bool bvalid = b < a.nb;
+        const int64_t u0 = (int64_t)b * a.L;
+        const float2 *Xb = a.X + ((int64_t)tile.ref * a.nb + (bvalid ? b : 0)) * kM;
+        float2 x[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) x[r] = Xb[t + kGT * r];
+        __syncthreads();                        // every reader of Ps in the previous item is done
+        const float2 *Pt = a.P + (tile.first - a.slot0) * kM;
+        stage_p(Ps, Pt);
+        for (int q = 0; q < tile.count; ++q) {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();                    // P_q visible to all; buffer (q + 1) & 1 free
+            if (q + 1 < tile.count) stage_p(Ps + ((q + 1) & 1) * kM, Pt + (int64_t)(q + 1) * kM);
+            const float2 *Pq = Ps + (q & 1) * kM;
+            float2 v[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = cmul(x[r], Pq[t + kGT * r]);
+            group_fft<true>(v, TA, TB, stw, t, 1 + g);
+            // epilogue: v[r] = z at u = u0 + t + 128 r
+            bool hit = false;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int l = t + kGT * r;
+                const bool valid = bvalid && l < a.L && u0 + l < a.n;
+                const float p = __fadd_rn(__fmul_rn(v[r].x, v[r].x), __fmul_rn(v[r].y, v[r].y));
+                hit |= valid && (p > a.thr);
+            }
+            if (__any_sync(0xffffffffu, hit)) {
+                const int64_t slot = tile.first + q;
+                const int32_t j = a.perm[slot];
+                const int32_t o = a.off[slot];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const int l = t + kGT * r;
+                    const bool valid = bvalid && l < a.L && u0 + l < a.n;
+                    const uint32_t tt = (uint32_t)((u0 + l + o) & (a.n - 1));
+                    emit_window_max(valid, (uint32_t)j, tt, v[r].x, v[r].y, a.thr, a.W, a.cand, a.cap, a.count);
+                }
+            }
+        }
+    }
+}
+
+// P_j for block-FFT slots slot0 + s_off + blockIdx.x (one 128-thread block each; P holds the
+// block-FFT slots only, from slot0) and off_j.
+__global__ void __launch_bounds__(kGT) k_taps_spectra(const float2 *__restrict__ taps, int32_t k_stride,
+                                                      const int32_t *__restrict__ perm,
+                                                      const int32_t *__restrict__ kslot,
+                                                      const int32_t *__restrict__ lag,
+                                                      const double *__restrict__ sigma, int64_t n, int64_t slot0,
+                                                      int64_t s_off, float2 *__restrict__ P, int32_t *__restrict__ off,
+                                                      const float2 *__restrict__ stw) {
+    __shared__ __align__(16) float2 tiles[2 * kTileLd];
+    const int64_t local = s_off + blockIdx.x;
+    const int64_t slot = slot0 + local;
+    const int t = threadIdx.x;
+    const int32_t j = perm[slot], K = kslot[slot];
+    const double s = sigma[j];
+    // a window with no weight has sigma_eff = 0: zero spectrum, no triggers
+    const double inv = s > 0.0 ? 1.0 / (s * (double)kM) : 0.0;
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int m = t + kGT * r;
+        if (m < K) {
+            const float2 c = taps[(int64_t)j * k_stride + (K - 1 - m)];
+            v[r] = make_float2((float)((double)c.x * inv), (float)((double)c.y * inv));
+        } else {
+            v[r] = make_float2(0.f, 0.f);
+        }
+    }
+    group_fft<true>(v, tiles, tiles + kTileLd, stw, t, 1);
+    float2 *dst = P + local * kM;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) dst[t + kGT * r] = v[r];
+    if (t == 0) off[slot] = (int32_t)((((int64_t)lag[j] + K - 1) % n + n) % n);
+}
+
+constexpr size_t kSmemSpectra = (size_t)(kM + 2 * kGroups * kTileLd) * sizeof(float2);
+constexpr size_t kSmemFilter = (size_t)(3 * kM + 2 * kGroups * kTileLd) * sizeof(float2);
+
+}  // namespace
+
+int fft_fir_block_len() { return kM; }
+int fft_fir_tile_templates() { return kTileTemplates; }
+int fft_fir_blocks_per_cta() { return kGroups; }
+
+rfd_status fft_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const int32_t *lag, const double *sigma,
+                    cudaStream_t s) {
+    if (plan->fft_nslots == 0) return RFD_OK;
+    for (int64_t s0 = 0; s0 < plan->fft_nslots; s0 += 65535) {
+        const unsigned nblk = (unsigned)std::min<int64_t>(65535, plan->fft_nslots - s0);
+        k_taps_spectra<<<nblk, kGT, 0, s>>>(taps, k_stride, (const int32_t *)plan->d_perm.p,
+                                             (const int32_t *)plan->d_kslot.p, lag, sigma, plan->grid.n,
+                                             plan->fft_slot0, s0, (float2 *)plan->d_fft_P.p,
+                                             (int32_t *)plan->d_off.p, plan->fft_stw);
+        RFD_LAUNCH_CHECK();
+    }
+    return RFD_OK;
+}
+
+rfd_status fft_launch(const rfd_plan *plan, const void *q, const int32_t *qscale, rfd_candidate *cand, int64_t cap,
+                      int64_t *count, cudaStream_t s) {
+    if (plan->fft_tiles.empty()) return RFD_OK;
+    static bool attr_set = false;
+    if (!attr_set) {
+        RFD_TRY_CUDA(cudaFuncSetAttribute(k_block_spectra<RFD_PREC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kSmemSpectra));
+        RFD_TRY_CUDA(cudaFuncSetAttribute(k_block_spectra<RFD_PREC_FP16X3>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSpectra));
+        RFD_TRY_CUDA(cudaFuncSetAttribute(k_block_spectra<RFD_PREC_BF16X3>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSpectra));
+        RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFilter));
+        attr_set = true;
+    }
+    const dim3 gs((unsigned)plan->fft_nbg, (unsigned)plan->fft_refs.size());
+    const int32_t *refs = (const int32_t *)plan->d_fft_refs.p;
+    float2 *X = (float2 *)plan->d_fft_X.p;
+    if (plan->precision == RFD_PREC_FP32)
+        k_block_spectra<RFD_PREC_FP32><<<gs, kThreads, kSmemSpectra, s>>>(q, qscale, plan->ld, plan->grid.n,
+                                                                            plan->fft_L, plan->fft_nb, refs, X,
+                                                                            plan->fft_stw);
+    else if (plan->precision == RFD_PREC_FP16X3)
+        k_block_spectra<RFD_PREC_FP16X3><<<gs, kThreads, kSmemSpectra, s>>>(q, qscale, plan->ld, plan->grid.n,
+                                                                              plan->fft_L, plan->fft_nb, refs, X,
+                                                                              plan->fft_stw);
+    else
+        k_block_spectra<RFD_PREC_BF16X3><<<gs, kThreads, kSmemSpectra, s>>>(q, qscale, plan->ld, plan->grid.n,
+                                                                              plan->fft_L, plan->fft_nb, refs, X,
+                                                                              plan->fft_stw);
+    RFD_LAUNCH_CHECK();
+    RfFftArgs a;
+    a.tiles = (const FftTile *)plan->d_fft_tiles.p;
+    a.ranges = (const int64_t *)plan->d_fft_ranges.p;
+    a.nbg = plan->fft_nbg;
+    a.nb = plan->fft_nb;
+    a.L = plan->fft_L;
+    a.X = X;
+    a.P = (const float2 *)plan->d_fft_P.p;
+    a.slot0 = plan->fft_slot0;
+    a.stw = plan->fft_stw;
+    a.perm = (const int32_t *)plan->d_perm.p;
+    a.off = (const int32_t *)plan->d_off.p;
+    a.n = plan->grid.n;
+    a.thr = plan->threshold;
+    a.W = (uint32_t)plan->window;
+    a.cand = cand;
+    a.cap = cap;
+    a.count = (unsigned long long *)count;
+    k_rf_fft<<<(unsigned)plan->fft_grid, kThreads, kSmemFilter, s>>>(a);
+    RFD_LAUNCH_CHECK();
+    return RFD_OK;
+}
+
+}  // namespace rfd

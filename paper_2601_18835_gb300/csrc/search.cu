@@ -8,11 +8,8 @@
 namespace rfd {
 rfd_status filter_reference_impl(rfd_ctx *, const Grid &, const float2 *, const double *, const float2 *,
                                  int64_t, int32_t, int32_t, void *, int32_t *, cudaStream_t);
-rfd_status fir32_launch(const rfd_plan *, const float2 *, rfd_candidate *, int64_t, int64_t *, cudaStream_t);
-rfd_status tc_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
-                     cudaStream_t);
-rfd_status tl_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
-                     cudaStream_t);
+rfd_status ratio_filter_enqueue(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t,
+                                int64_t *, cudaStream_t);
 void add_launches(int64_t n);
 int64_t launch_count();
 }  // namespace rfd
@@ -35,6 +32,7 @@ struct rfd_search {
     int64_t kernels_per_run = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the ratio-filter kernel, inside the graph
     cudaEvent_t evs = nullptr, eve = nullptr;   // first and last node of the graph
+    bool pinned = false;                        // holds a graphs_pin()
 };
 
 namespace rfd {
@@ -53,12 +51,7 @@ rfd_status enqueue_step(rfd_search *S, cudaStream_t s, bool capturing) {
                                   S->qscale, s));
     RFD_TRY_CUDA(cudaMemsetAsync(S->count, 0, sizeof(int64_t), s));
     RFD_TRY_CUDA(record(S->ev0, s, capturing));
-    if (p->precision == RFD_PREC_FP32)
-        RFD_TRY(fir32_launch(p, (const float2 *)S->qref, S->cand, S->cap, S->count, s));
-    else {
-        RFD_TRY(tc_launch(p, S->qref, S->qscale, S->cand, S->cap, S->count, s));
-        RFD_TRY(tl_launch(p, S->qref, S->qscale, S->cand, S->cap, S->count, s));
-    }
+    RFD_TRY(ratio_filter_enqueue(p, S->qref, S->qscale, S->cand, S->cap, S->count, s));
     RFD_TRY_CUDA(record(S->ev1, s, capturing));
     RFD_TRY(find_triggers_enqueue(p->ctx, p->n_tmpl, S->cand, S->count, S->cap, S->trig, S->trig_cap, S->host, s));
     RFD_TRY_CUDA(record(S->eve, s, capturing));
@@ -75,6 +68,7 @@ extern "C" {
 void rfd_search_destroy(rfd_search *S) {
     if (!S) return;
     if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->pinned) graphs_unpin();
     if (S->graph) cudaGraphDestroy(S->graph);
     if (S->host) cudaFreeHost(S->host);
     if (S->ev0) cudaEventDestroy(S->ev0);
@@ -155,6 +149,8 @@ rfd_status rfd_search_create(rfd_plan *plan, const void *dtilde_dev, const doubl
             st = RFD_ERR_CUDA;
             break;
         }
+        graphs_pin();
+        S->pinned = true;
     } while (0);
     if (st != RFD_OK) {
         rfd_search_destroy(S);

@@ -76,6 +76,27 @@ def test_ifft_matches_numpy(ctx, n, batch):
     assert np.max(np.abs(got - ref)) / rms < 2e-6
 
 
+# every size class of the transform: one pass per radix below 2^12, the two-pass (four-step)
+# form from 2^12 (N1 = N2 = 64) to 2^22 (N1 = 2048, N2 = 2048: the largest shared-memory tile),
+# odd log2 n (N1 = 2 N2) and one pass per radix again above 2^22
+@pytest.mark.parametrize("n,batch", [(256, 5), (2048, 3), (4096, 3), (8192, 2), (131072, 2), (524288, 3),
+                                     (4194304, 1), (8388608, 1)])
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_fft_both_directions_and_precisions(ctx, n, batch, fp64, inverse):
+    rng = np.random.default_rng(n + 7 * batch)
+    x = rng.standard_normal((batch, n)) + 1j * rng.standard_normal((batch, n))
+    x = x.astype(np.complex128 if fp64 else np.complex64)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xd)
+    rfd.fft_c2c(ctx, xd, out, inverse)
+    ref = np.fft.ifft(x.astype(np.complex128), axis=1) * n if inverse else np.fft.fft(x.astype(np.complex128), axis=1)
+    got = out.cpu().numpy()
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    # radix-16 Stockham error grows like log2 n eps: 2e-6 (FP32) and 1e-14 (FP64) of the rms
+    assert np.max(np.abs(got - ref)) / rms < (1e-14 if fp64 else 2e-6)
+
+
 # --------------------------------------------------------------------------- templates
 def test_gen_templates_match_oracle(ctx):
     from oracle import waveform as wf
@@ -270,9 +291,10 @@ def test_c2_full_size_fp32_sampled(ctx):
 # --------------------------------------------------------------------------- tensor-core path
 TOL_TC = 1e-3
 TC_PRECISIONS = [("fp16x3", 1), ("bf16x3", 2)]
-# the two tensor-core kernels: time on M with templates on N (K <= 128 by default), and
-# templates on M with time on N (the long-tap kernel, K > 128 by default), each forced for all
-TC_KERNELS = [("time_on_m", {"long_k": 512}), ("templates_on_m", {"long_k": 0})]
+# the two tensor-core kernels: time on M with templates on N (K <= 64 by default), and
+# templates on M with time on N (the long-tap kernel, K > 64 by default), each forced for all;
+# and the block-FFT kernel (FP32 transforms of the split series' reconstruction) for all
+TC_KERNELS = [("time_on_m", {"long_k": 512}), ("templates_on_m", {"long_k": 0}), ("block_fft", {"fft_k": 0})]
 
 
 def snr_errors(trig, sets, js):
@@ -345,6 +367,55 @@ def test_long_taps_tensor_core(ctx, name, prec):
     for j in js:
         o = ora.design(j, int(K[j]), with_match=False)
         sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
+    n_or = sum(len(sets[j][0]) for j in js)
+    assert n_or > 100
+    assert compare_triggers(trig, sets, TOL_TC, js, cfg.window) <= 0.05 * n_or
+    assert snr_errors(trig, sets, js) < 2e-5
+
+
+def test_block_fft_fp32_c1_and_ragged(ctx, c1):
+    """The block-FFT kernel on an FP32 plan: C1 (K = 64) and a ragged bank (K from 2 to 96,
+    window 37, threshold 6; the last 2048-sample block only partly valid), FP32 tolerance."""
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP32)
+    trig, _ = gpu.ratio_filter(t, q, e, rfd.PREC_FP32, halo, options={"fft_k": 0})
+    sets = {j: ora.triggers(ora.snr(j, ora.design(j, cfg.k, with_match=False)), TOL_FP32)
+            for j in range(bank.n_tmpl)}
+    assert compare_triggers(trig, sets, TOL_FP32, range(bank.n_tmpl), cfg.window) <= 2
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < 2e-6
+    cfg = workload.small_config(1, n_tmpl=37, window=37, threshold=6.0)
+    bank, data = workload.make_workload(cfg)
+    rng = np.random.default_rng(7)
+    K = (2 * rng.integers(1, 49, size=bank.n_tmpl)).astype(np.int32)
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(K, k_stride=128, match=False)
+    halo = int(K.max()) - 1
+    q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP32)
+    trig, _ = gpu.ratio_filter(t, q, e, rfd.PREC_FP32, halo, cand_cap=1 << 22, options={"fft_k": 0})
+    sets = {j: ora.triggers(ora.snr(j, ora.design(j, int(K[j]), with_match=False)), TOL_FP32)
+            for j in range(bank.n_tmpl)}
+    n_or = sum(len(s[0]) for s in sets.values())
+    assert n_or > 1000
+    assert compare_triggers(trig, sets, TOL_FP32, range(bank.n_tmpl), cfg.window) <= 0.01 * n_or
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < 2e-6
+
+
+def test_block_fft_next_to_tensor_cores(ctx):
+    """K = 64 on the tensor cores and K = 320 / 512 on the block-FFT kernel (fft_k = 256) in one
+    plan and one call: every sampled template matches the oracle."""
+    cfg = workload.small_config(1, n_tmpl=80, threshold=9.0)
+    bank, data = workload.make_workload(cfg)
+    K = np.where(np.arange(bank.n_tmpl) % 3 == 0, 320, np.where(np.arange(bank.n_tmpl) % 3 == 1, 512, 64))
+    K = K.astype(np.int32)
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(K, k_stride=512, match=False)
+    halo = 511
+    q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP16X3)
+    trig, _ = gpu.ratio_filter(t, q, e, rfd.PREC_FP16X3, halo, cand_cap=1 << 22, options={"fft_k": 256})
+    js = list(range(0, bank.n_tmpl, 4))
+    sets = {j: ora.triggers(ora.snr(j, ora.design(j, int(K[j]), with_match=False)), TOL_TC) for j in js}
     n_or = sum(len(sets[j][0]) for j in js)
     assert n_or > 100
     assert compare_triggers(trig, sets, TOL_TC, js, cfg.window) <= 0.05 * n_or
@@ -449,9 +520,11 @@ def test_bucketed_taps_and_uneven_k_tensor_core(ctx):
 
 
 # --------------------------------------------------------------------------- graph and autotuner
-def test_search_graph_matches_separate_calls(c1):
+@pytest.mark.parametrize("opts", [None, {"fft_k": 32}])
+def test_search_graph_matches_separate_calls(c1, opts):
     """The whole segment as one CUDA graph (rfd_search_*) equals the three separate calls, on two
-    segments in a row (the second written into the bound spectrum buffer)."""
+    segments in a row (the second written into the bound spectrum buffer); also with the
+    block-FFT kernel in the plan."""
     cfg, bank, data, ora, gpu = c1
     t = gpu.make_taps(cfg.k, match=False)
     halo = cfg.k - 1
@@ -460,7 +533,7 @@ def test_search_graph_matches_separate_calls(c1):
     q = torch.zeros(bank.n_ref * ld * 8, dtype=torch.uint8, device="cuda")
     e = torch.zeros(bank.n_ref, dtype=torch.int32, device="cuda")
     plan = rfd.Plan(gpu.ctx, gpu.grid, bank.n_ref, bank.ref_of_tmpl, t["K"], rfd.PREC_FP16X3, cfg.window,
-                    cfg.threshold, halo)
+                    cfg.threshold, halo, options=opts)
     plan.set_taps(t["taps"], t["k_stride"], t["lag"], t["sigma"])
     cap, tcap = 1 << 18, 1 << 16
     cand = torch.zeros(cap * 24, dtype=torch.uint8, device="cuda")
@@ -486,6 +559,42 @@ def test_search_graph_matches_separate_calls(c1):
         nt2 = rfd.find_triggers(gpu.ctx, bank.n_tmpl, cand, cnt, trig2)
         assert nt_graph == nt2
         assert np.array_equal(got.view(np.uint8), rfd.triggers_to_numpy(trig2, nt2).view(np.uint8))
+    search.close()
+    plan.close()
+
+
+def test_search_survives_scratch_growth(c1):
+    """A call that needs larger context scratch buffers after the graph was captured (here a
+    filter_reference over four times as many references) leaves the graph's buffers valid:
+    the next replay gives the same triggers as before."""
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    href = gpu.templates(bank.ref_params())
+    ld = rfd.qref_ld(cfg.n, halo)
+    q = torch.zeros(bank.n_ref * ld * 8, dtype=torch.uint8, device="cuda")
+    e = torch.zeros(bank.n_ref, dtype=torch.int32, device="cuda")
+    plan = rfd.Plan(gpu.ctx, gpu.grid, bank.n_ref, bank.ref_of_tmpl, t["K"], rfd.PREC_FP16X3, cfg.window,
+                    cfg.threshold, halo)
+    plan.set_taps(t["taps"], t["k_stride"], t["lag"], t["sigma"])
+    cand = torch.zeros((1 << 18) * 24, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    trig = torch.zeros((1 << 16) * 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        search = rfd.Search(plan, gpu.d, gpu.psd, href, q, e, cand, cnt, trig, stream)
+    n0 = search.run()
+    before = rfd.triggers_to_numpy(trig, n0).view(np.uint8).copy()
+    R4 = 4 * bank.n_ref + 3
+    href4 = href.repeat(R4, 1)[:R4].contiguous()
+    q4 = torch.zeros(R4 * ld * 8, dtype=torch.uint8, device="cuda")
+    e4 = torch.zeros(R4, dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        rfd.filter_reference(gpu.ctx, gpu.grid, gpu.d, gpu.psd, href4, halo, rfd.PREC_FP16X3, q4, e4, stream=stream)
+    stream.synchronize()
+    n1 = search.run()
+    assert n1 == n0
+    assert np.array_equal(rfd.triggers_to_numpy(trig, n1).view(np.uint8), before)
     search.close()
     plan.close()
 
@@ -526,8 +635,21 @@ def test_autotuner_choices_give_identical_triggers(ctx, tmp_path):
         results.append(rfd.triggers_to_numpy(tb, nt).view(np.uint8).copy())
         plan.close()
     assert len(results[0]) > 0
-    for r in results[1:]:
-        assert np.array_equal(r, results[0])
+    # tensor-core choices: bit-identical; block-FFT choices (other arithmetic): the same windows
+    # and samples, |z| within the tensor-core tolerance
+    base = results[0].view(rfd.TRIGGER_DTYPE)
+    for c, r in zip(rep["candidates"][1:], results[1:]):
+        if "fft_k" not in c["options"]:
+            assert np.array_equal(r, results[0])
+            continue
+        got = r.view(rfd.TRIGGER_DTYPE)
+        a = {(int(x["j"]), int(x["w"])): x for x in base}
+        b = {(int(x["j"]), int(x["w"])): x for x in got}
+        diff = set(a) ^ set(b)
+        assert len(diff) <= 0.01 * len(a), (c["options"], len(diff))
+        for key in set(a) & set(b):
+            za, zb = math.sqrt(float(a[key]["snr2"])), math.sqrt(float(b[key]["snr2"]))
+            assert abs(za - zb) <= 2e-3 * za, (c["options"], key, za, zb)
 
 
 def test_search_graph_times_each_run(c1):
