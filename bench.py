@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--ridge", type=float, default=1e-6)
     ap.add_argument("--long-k", type=int, default=None,
                     help="fix the plan's long_k instead of autotuning (profiling cases)")
+    ap.add_argument("--stream-block", type=int, default=0,
+                    help="streaming (Sec. VII.A): each step filters the next block of this many output "
+                         "samples (a multiple of 512) after refreshing the reference series; 0 = whole segment")
     ap.add_argument("--fft-k", type=int, default=None,
                     help="fix the plan's fft_k (templates with fft_k < K <= 1024 on the block-FFT kernel) "
                          "instead of autotuning")
@@ -533,6 +536,7 @@ class GpuSearch:
         self.trig_host = torch.zeros(self.trig_cap * 20, dtype=torch.uint8).pin_memory()
         self.flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         self.search = None
+        self.u_next = 0
         if self.use_graph:
             self.search = rfd.Search(self.plan, self.d, self.psd, self.href, self.q, self.e, self.cand, self.cnt,
                                      self.trig, self.stream)
@@ -573,8 +577,13 @@ class GpuSearch:
             plan.close()
         return parts
 
+    @property
+    def out_len(self):
+        """Outputs per step: the segment, or the streaming block."""
+        return int(self.options.get("out_len", 0)) or self.cfg.n
+
     def alg_flops(self):
-        return 8.0 * float(self.K.astype(np.float64).sum()) * self.cfg.n
+        return 8.0 * float(self.K.astype(np.float64).sum()) * self.out_len
 
     def flush_l2(self):
         with self.torch.cuda.stream(self.stream):
@@ -588,7 +597,12 @@ class GpuSearch:
             if ev:
                 ev[0].record(self.stream)
             if self.search is not None:
-                nt = self.search.run()
+                if self.out_len < self.cfg.n:
+                    # streaming: the next block of outputs (window start advances around the segment)
+                    nt = self.search.run(u_begin=self.u_next)
+                    self.u_next = (self.u_next + self.out_len) % self.cfg.n
+                else:
+                    nt = self.search.run()
                 kms = self.search.filter_ms()
                 self.last_step_ms = self.search.step_ms()
             else:
@@ -700,8 +714,10 @@ def run_ours(args):
     tune_cache = os.path.join(ROOT, "paper_2601_18835_gb300", "_build", "autotune.json")
     fit = {"target": args.match_target, "ridge": args.ridge} if args.taps == "fit" else None
     fixed = None
-    if args.long_k is not None or args.fft_k is not None:
+    if args.long_k is not None or args.fft_k is not None or args.stream_block:
         fixed = {"mix_k": 1}
+        if args.stream_block:
+            fixed["out_len"] = args.stream_block
         if args.long_k is not None:
             fixed["long_k"] = args.long_k
         if args.fft_k is not None:
@@ -709,6 +725,7 @@ def run_ours(args):
     s = GpuSearch(cfg, bank, data, prec, local, use_graph=not args.no_graph, autotune_cache=tune_cache,
                   learned=learned, options=fixed, fit=fit)
     J, dur = bank.n_tmpl, cfg.duration
+    step_dur = s.out_len / cfg.fs          # seconds of SNR series per template and step
 
     def barrier():
         if ws > 1:
@@ -743,7 +760,7 @@ def run_ours(args):
     clk = clocks.stop(w0, w1)
     ms = sum(step_ms) / len(step_ms)
     ms_max = max_over_ranks(ms, ws)
-    value = job_rate(ws, J, dur, ms_max / 1e3)
+    value = job_rate(ws, J, step_dur, ms_max / 1e3)
 
     # end to end through host buffers
     for _ in range(2):
@@ -757,7 +774,7 @@ def run_ours(args):
         nt = s.step_e2e()
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
-    e2e_value = job_rate(ws, J, dur, max_over_ranks(sum(e2e_t) / len(e2e_t), ws))
+    e2e_value = job_rate(ws, J, step_dur, max_over_ranks(sum(e2e_t) / len(e2e_t), ws))
 
     # roofline of the dominant kernel: the ratio-filter contraction (or, for a plan that sends
     # long templates to the block-FFT kernel, whichever family takes longer, timed on its own)
@@ -767,15 +784,15 @@ def run_ours(args):
     parts = s.kernel_parts() if prec != 0 else []
     if parts:
         dom = max(parts, key=lambda q: q["ms"])
-        roof = roofline(prec, dom["family"], s.K[dom["idx"]], s.options, cfg.n, bank.n_ref, dom["ms"] / 1e3,
+        roof = roofline(prec, dom["family"], s.K[dom["idx"]], s.options, s.out_len, bank.n_ref, dom["ms"] / 1e3,
                         dom["executed_flops"], peaks, peak_kind)
         for q in parts:
-            q["frac"] = roofline(prec, q["family"], s.K[q["idx"]], s.options, cfg.n, bank.n_ref, q["ms"] / 1e3,
+            q["frac"] = roofline(prec, q["family"], s.K[q["idx"]], s.options, s.out_len, bank.n_ref, q["ms"] / 1e3,
                                  q["executed_flops"], peaks, peak_kind)["frac"]
         roof["parts"] = [{k: v for k, v in q.items() if k not in ("idx", "executed_flops")} for q in parts]
     else:
         family = "fft" if fft_templates(s.K, s.options) == len(s.K) and prec != 0 else "direct"
-        roof = roofline(prec, family, s.K, s.options, cfg.n, bank.n_ref, filt_s,
+        roof = roofline(prec, family, s.K, s.options, s.out_len, bank.n_ref, filt_s,
                         s.plan.executed_flops() if prec != 0 else 0.0, peaks, peak_kind)
 
     chisq_rep = None
@@ -847,7 +864,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": precision_name, "data": "synthetic",
-        "config": {"workload": cfg.name, "n_tmpl": J, "n_ref": bank.n_ref,
+        "config": {"workload": cfg.name + ("_stream%d" % s.out_len if s.out_len < cfg.n else ""),
+                   "n_tmpl": J, "n_ref": bank.n_ref,
                    "k": (cfg.k if (cfg.k and fit is None) else
                          {"buckets": sorted(set(int(x) for x in s.K)),
                           "histogram": {int(b): int((s.K == b).sum()) for b in sorted(set(int(x) for x in s.K))},
@@ -877,6 +895,14 @@ def run_ours(args):
         line["learned_taps"] = s.learned_report
     if chisq_rep is not None:
         line["subband_chi2"] = chisq_rep
+    if s.out_len < cfg.n:
+        srt = sorted(step_ms)
+        line["streaming"] = {"block_samples": s.out_len, "block_s": step_dur,
+                             "latency_ms_median": srt[len(srt) // 2], "latency_ms_max": srt[-1],
+                             "ratio_filter_ms": filt_s * 1e3,
+                             "note": "per block: every reference's matched filter over the whole segment "
+                                     "(Eq. 1, as an overlap-save stream re-transforms it), the ratio filter "
+                                     "over the block's outputs only, and the trigger merge"}
     s.close()
     if rank == 0:
         print(json.dumps(line))

@@ -240,10 +240,13 @@ typedef struct {
                              (overlap-save blocks of 2048 samples, FP32 transforms in shared
                              memory, the paper's own realisation of the FIR): 0 = every template
                              with K <= 1024, 4096 = none */
-    int32_t reserved;     /* must be 0 */
+    int32_t out_len;      /* outputs per filtering call: 0 = the whole segment (n); otherwise a
+                             multiple of 512 (n a multiple of 512 too): rfd_ratio_filter_window
+                             then filters out_len positions from a start held in device memory
+                             (streaming, Sec. VII.A) */
 } rfd_plan_options;
 /* Fills the defaults: tile_nt = {128, 64, 32}, mix_k = 1, grid_ctas = 0, long_k = 64,
- * fft_k = 4096. */
+ * fft_k = 4096, out_len = 0. */
 void rfd_plan_options_default(rfd_plan_options *options);
 /* rfd_plan_create with explicit tile choices (NULL = defaults). */
 rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
@@ -276,6 +279,18 @@ rfd_status rfd_plan_set_taps(rfd_plan *plan, const void *taps_dev, int32_t k_str
 rfd_status rfd_ratio_filter_batch(rfd_plan *plan, const void *qref_dev,
                                   const int32_t *qscale_dev, rfd_candidate *cand_dev,
                                   int64_t cand_capacity, int64_t *cand_count_dev, void *stream);
+
+/* The same over a window of the plan's out_len output positions u = u_0 .. u_0 + out_len - 1
+ * (mod n), u_0 = *u_begin_dev (int64 in device memory, read by the kernels, so that a captured
+ * graph can be replayed for the next window; taken modulo n and rounded down to a multiple of
+ * 512).  This is the streaming form of Sec. VII.A: the next block of SNR needs only the most
+ * recent reference series plus a K-sample halo.  The triggers of windows that tile the segment,
+ * merged per (j, window) by the maximum key, are those of rfd_ratio_filter_batch on a plan
+ * without a window (bit for bit on the tensor-core and FP32 kernels; the block-FFT kernel cuts
+ * its blocks at the window start, so there the SNRs agree to rounding). */
+rfd_status rfd_ratio_filter_window(rfd_plan *plan, const void *qref_dev, const int32_t *qscale_dev,
+                                   const int64_t *u_begin_dev, rfd_candidate *cand_dev,
+                                   int64_t cand_capacity, int64_t *cand_count_dev, void *stream);
 
 /* Tensor-core (or FMA) flops one rfd_ratio_filter_batch call of this plan executes. */
 double rfd_plan_executed_flops(const rfd_plan *plan);
@@ -314,6 +329,11 @@ rfd_status rfd_search_create(rfd_plan *plan, const void *dtilde_dev, const doubl
                              int64_t *cand_count_dev, rfd_trigger *trig_dev,
                              int64_t trig_capacity, void *stream, rfd_search **out);
 rfd_status rfd_search_run(rfd_search *search, void *stream, int64_t *n_trig_host);
+/* Streaming (Sec. VII.A) with a plan whose out_len is a window: the next run filters the
+ * window starting at u_begin (a multiple of 512 in [0, n); the value is copied to device
+ * memory the graph reads, then the graph is launched as by rfd_search_run).  A plan without a
+ * window ignores it. */
+rfd_status rfd_search_run_at(rfd_search *search, int64_t u_begin, void *stream, int64_t *n_trig_host);
 /* Kernels one run launches (they are counted in rfd_kernel_launches as they are replayed). */
 int64_t rfd_search_kernels_per_run(const rfd_search *search);
 /* Device time (ms) of the ratio-filter kernel in the last completed run (CUDA events recorded

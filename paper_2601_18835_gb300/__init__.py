@@ -170,7 +170,8 @@ class Plan:
 
     def __init__(self, ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, options=None):
         """options: dict with any of tile_nt (3 ints), mix_k (0/1), grid_ctas (int), long_k (int),
-        fft_k (int: templates with fft_k < K <= 1024 use the block-FFT kernel)."""
+        fft_k (int: templates with fft_k < K <= 1024 use the block-FFT kernel), out_len (int: outputs per
+        call, a multiple of 512; 0 = the whole segment)."""
         ro, rop = _i32_host(ref_of)
         kk, kp = _i32_host(k)
         h = ctypes.c_void_p()
@@ -189,6 +190,8 @@ class Plan:
                 opt.long_k = int(options["long_k"])
             if "fft_k" in options:
                 opt.fft_k = int(options["fft_k"])
+            if "out_len" in options:
+                opt.out_len = int(options["out_len"])
         check(_lib().rfd_plan_create_ex(ctx.handle, ctypes.byref(g), int(n_ref), len(ro), rop, kp,
                                         int(precision), int(window), float(threshold), int(halo),
                                         ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))
@@ -205,6 +208,12 @@ class Plan:
         cap = cand.numel() * cand.element_size() // CANDIDATE_DTYPE.itemsize
         check(_lib().rfd_ratio_filter_batch(self.handle, _ptr(qref), _ptr(qscale), _ptr(cand), int(cap),
                                             _ptr(cand_count), _stream(stream)))
+
+    def ratio_filter_window(self, qref, qscale, u_begin, cand, cand_count, stream=None):
+        """The plan's out_len outputs from the position held in u_begin (int64 device tensor)."""
+        cap = cand.numel() * cand.element_size() // CANDIDATE_DTYPE.itemsize
+        check(_lib().rfd_ratio_filter_window(self.handle, _ptr(qref), _ptr(qscale), _ptr(u_begin), _ptr(cand),
+                                             int(cap), _ptr(cand_count), _stream(stream)))
 
     def executed_flops(self):
         """Flops one ratio_filter_batch call executes (tensor-core or FMA)."""
@@ -250,10 +259,15 @@ class Search:
         """Device time of the ratio-filter kernel in the last run (events inside the graph)."""
         return float(_lib().rfd_search_filter_ms(self.handle))
 
-    def run(self):
-        """Replays the graph, waits, returns the number of triggers."""
+    def run(self, u_begin=None):
+        """Replays the graph, waits, returns the number of triggers.  u_begin: the window start
+        for a plan with out_len < n (streaming)."""
         n = ctypes.c_int64(0)
-        check(_lib().rfd_search_run(self.handle, _stream(self.stream), ctypes.byref(n)), needed=n.value)
+        if u_begin is None:
+            check(_lib().rfd_search_run(self.handle, _stream(self.stream), ctypes.byref(n)), needed=n.value)
+        else:
+            check(_lib().rfd_search_run_at(self.handle, int(u_begin), _stream(self.stream), ctypes.byref(n)),
+                  needed=n.value)
         return int(n.value)
 
     def close(self):

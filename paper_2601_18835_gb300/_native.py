@@ -35,7 +35,7 @@ class Grid(ctypes.Structure):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("tile_nt", ctypes.c_int32 * 3), ("mix_k", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
-                ("long_k", ctypes.c_int32), ("fft_k", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("long_k", ctypes.c_int32), ("fft_k", ctypes.c_int32), ("out_len", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -79,11 +79,13 @@ SIGNATURES = {
     "rfd_search_create": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _i64, _vp,
                                  ctypes.POINTER(_vp)]),
     "rfd_search_run": (_i32, [_vp, _vp, ctypes.POINTER(_i64)]),
+    "rfd_search_run_at": (_i32, [_vp, _i64, _vp, ctypes.POINTER(_i64)]),
     "rfd_search_kernels_per_run": (_i64, [_vp]),
     "rfd_search_filter_ms": (_dbl, [_vp]),
     "rfd_search_step_ms": (_dbl, [_vp]),
     "rfd_search_destroy": (None, [_vp]),
     "rfd_ratio_filter_batch": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "rfd_ratio_filter_window": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     "rfd_find_triggers": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(_i64), _vp]),
     "rfd_find_triggers_noalloc": (_i32, [_i32, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(_i64), _vp]),
     "rfd_findchirp": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _vp, _i32, _i32, _flt, _vp, _i64, _vp,

@@ -19,26 +19,29 @@ rfd_status filter_reference_impl(rfd_ctx *, const Grid &, const float2 *, const 
 rfd_status findchirp_impl(rfd_ctx *, const Grid &, const float2 *, const double *, const float2 *, int64_t,
                           int32_t, float, rfd_candidate *, int64_t, int64_t *, cudaStream_t);
 int fir32_tile_templates();
-rfd_status fir32_launch(const rfd_plan *, const float2 *, rfd_candidate *, int64_t, int64_t *,
+rfd_status fir32_launch(const rfd_plan *, const float2 *, const int64_t *, rfd_candidate *, int64_t, int64_t *,
                         cudaStream_t);
 rfd_status pack_taps_fp32(rfd_plan *, const float2 *, int32_t, const int32_t *, const double *,
                           cudaStream_t);
 rfd_status tc_pack(rfd_plan *, const float2 *, int32_t, const int32_t *, const double *, cudaStream_t);
 rfd_status tl_pack(rfd_plan *, const float2 *, int32_t, const int32_t *, const double *, cudaStream_t);
-rfd_status tl_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
+rfd_status tl_launch(const rfd_plan *, const void *, const int32_t *, const int64_t *, rfd_candidate *, int64_t,
+                     int64_t *,
                      cudaStream_t);
 uint32_t tl_ystride(int32_t kpad_max);
 uint32_t tl_qwin(int32_t kpad_max);
 int tl_rows_per_item();
 int tl_tile_templates();
-rfd_status tc_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
+rfd_status tc_launch(const rfd_plan *, const void *, const int32_t *, const int64_t *, rfd_candidate *, int64_t,
+                     int64_t *,
                      cudaStream_t);
 int tc_rows_per_item();
 int fft_fir_block_len();
 int fft_fir_tile_templates();
 int fft_fir_blocks_per_cta();
 rfd_status fft_pack(rfd_plan *, const float2 *, int32_t, const int32_t *, const double *, cudaStream_t);
-rfd_status fft_launch(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t, int64_t *,
+rfd_status fft_launch(const rfd_plan *, const void *, const int32_t *, const int64_t *, rfd_candidate *, int64_t,
+                      int64_t *,
                       cudaStream_t);
 
 // Tensor-core tiles: per reference, templates in increasing K, cut so that a tile holds at
@@ -73,7 +76,7 @@ static std::vector<int64_t> balanced_ranges(const std::vector<double> &cost, int
 // kernel); appended to the plan's slot order.
 static rfd_status plan_tl_tiles(rfd_plan *p, const std::vector<int32_t> &order, int num_sms,
                                 const rfd_plan_options &opt) {
-    const int64_t n_tb = p->grid.n / tl_rows_per_item();
+    const int64_t n_tb = p->out_len / tl_rows_per_item();
     const int32_t nt = tl_tile_templates();
     int64_t taps_off = 0;
     int32_t kpad_max = 0;
@@ -134,7 +137,7 @@ static rfd_status plan_fft_tiles(rfd_plan *p, const std::vector<int32_t> &order,
     int32_t kmax = 0;
     for (int32_t j : order) kmax = std::max(kmax, p->k_of[j]);
     p->fft_L = M - kmax + 1;
-    p->fft_nb = (int32_t)((p->grid.n + p->fft_L - 1) / p->fft_L);
+    p->fft_nb = (int32_t)((p->out_len + p->fft_L - 1) / p->fft_L);
     p->fft_nbg = (p->fft_nb + gpc - 1) / gpc;
     p->fft_slot0 = (int64_t)p->perm.size();
     size_t i = 0;
@@ -179,7 +182,7 @@ static rfd_status plan_fft_tiles(rfd_plan *p, const std::vector<int32_t> &order,
 
 static rfd_status plan_tc_tiles(rfd_plan *p, const std::vector<int32_t> &all, int num_sms,
                                 const rfd_plan_options &opt) {
-    const int64_t n_tt = p->grid.n / tc_rows_per_item();
+    const int64_t n_tt = p->out_len / tc_rows_per_item();
     int64_t taps_off = 0;
     int32_t kpad_max = 0;
     uint32_t cap = 0;
@@ -619,7 +622,8 @@ rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref,
         RFD_REQUIRE(opt.grid_ctas >= 0, RFD_ERR_ARG, "grid_ctas must be >= 0");
         RFD_REQUIRE(opt.long_k >= 0 && opt.long_k <= 512, RFD_ERR_ARG, "long_k must be in [0, 512]");
         RFD_REQUIRE(opt.fft_k >= 0 && opt.fft_k <= 4096, RFD_ERR_ARG, "fft_k must be in [0, 4096]");
-        RFD_REQUIRE(opt.reserved == 0, RFD_ERR_ARG, "reserved options must be 0");
+        RFD_REQUIRE(opt.out_len >= 0 && opt.out_len % 512 == 0, RFD_ERR_ARG,
+                    "out_len=%d must be 0 or a positive multiple of 512", opt.out_len);
     }
     RFD_REQUIRE(ctx && out, RFD_ERR_ARG, "NULL ctx or out");
     *out = nullptr;
@@ -652,6 +656,9 @@ rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref,
     p->threshold = threshold;
     p->halo = halo;
     p->ld = rfd_qref_ld(g.n, halo);
+    RFD_REQUIRE(opt.out_len <= g.n && (opt.out_len == 0 || g.n % 512 == 0), RFD_ERR_SHAPE,
+                "out_len=%d must be <= n=%lld, and n a multiple of 512 for a window", opt.out_len, (long long)g.n);
+    p->out_len = opt.out_len > 0 ? opt.out_len : g.n;
     p->k_max = kmax;
     p->ref_of.assign(ref_of_tmpl_host, ref_of_tmpl_host + n_tmpl);
     p->k_of.assign(k_host, k_host + n_tmpl);
@@ -712,7 +719,7 @@ rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref,
         }
         slot += t.count;
         p->tiles.push_back(t);
-        p->executed_flops += 8.0 * t.k_tile * (double)p->tile_j * (double)g.n;
+        p->executed_flops += 8.0 * t.k_tile * (double)p->tile_j * (double)p->out_len;
         i = e;
     }
     rfd_status st = plan_fft_tiles(p, order_fft, ctx->num_sms, opt);
@@ -790,15 +797,15 @@ rfd_status rfd_plan_set_taps(rfd_plan *plan, const void *taps_dev, int32_t k_str
 namespace rfd {
 // Every filtering kernel of a plan, in order, on one stream (the call and the search graph
 // both go through here).
-rfd_status ratio_filter_enqueue(const rfd_plan *plan, const void *q, const int32_t *qscale, rfd_candidate *cand,
-                                int64_t cap, int64_t *count, cudaStream_t s) {
+rfd_status ratio_filter_enqueue(const rfd_plan *plan, const void *q, const int32_t *qscale, const int64_t *u_begin,
+                                rfd_candidate *cand, int64_t cap, int64_t *count, cudaStream_t s) {
     if (plan->precision == RFD_PREC_FP32) {
-        RFD_TRY(fir32_launch(plan, (const float2 *)q, cand, cap, count, s));
+        RFD_TRY(fir32_launch(plan, (const float2 *)q, u_begin, cand, cap, count, s));
     } else {
-        RFD_TRY(tc_launch(plan, q, qscale, cand, cap, count, s));
-        RFD_TRY(tl_launch(plan, q, qscale, cand, cap, count, s));
+        RFD_TRY(tc_launch(plan, q, qscale, u_begin, cand, cap, count, s));
+        RFD_TRY(tl_launch(plan, q, qscale, u_begin, cand, cap, count, s));
     }
-    return fft_launch(plan, q, qscale, cand, cap, count, s);
+    return fft_launch(plan, q, qscale, u_begin, cand, cap, count, s);
 }
 }  // namespace rfd
 
@@ -815,7 +822,22 @@ rfd_status rfd_ratio_filter_batch(rfd_plan *plan, const void *qref_dev, const in
     RFD_TRY_CUDA(cudaSetDevice(plan->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     RFD_TRY_CUDA(cudaMemsetAsync(cand_count_dev, 0, sizeof(int64_t), s));
-    return ratio_filter_enqueue(plan, qref_dev, qscale_dev, cand_dev, cand_capacity, cand_count_dev, s);
+    return ratio_filter_enqueue(plan, qref_dev, qscale_dev, nullptr, cand_dev, cand_capacity, cand_count_dev, s);
+}
+
+rfd_status rfd_ratio_filter_window(rfd_plan *plan, const void *qref_dev, const int32_t *qscale_dev,
+                                   const int64_t *u_begin_dev, rfd_candidate *cand_dev, int64_t cand_capacity,
+                                   int64_t *cand_count_dev, void *stream) {
+    RFD_REQUIRE(plan, RFD_ERR_ARG, "plan is NULL");
+    RFD_REQUIRE(plan->taps_set, RFD_ERR_ARG, "rfd_plan_set_taps has not been called");
+    RFD_REQUIRE(qref_dev && u_begin_dev && cand_count_dev && (cand_dev || cand_capacity == 0), RFD_ERR_ARG,
+                "NULL argument");
+    RFD_REQUIRE(cand_capacity >= 0, RFD_ERR_SHAPE, "negative capacity");
+    RFD_REQUIRE(plan->precision == RFD_PREC_FP32 || qscale_dev, RFD_ERR_ARG, "qscale_dev is NULL");
+    RFD_TRY_CUDA(cudaSetDevice(plan->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    RFD_TRY_CUDA(cudaMemsetAsync(cand_count_dev, 0, sizeof(int64_t), s));
+    return ratio_filter_enqueue(plan, qref_dev, qscale_dev, u_begin_dev, cand_dev, cand_capacity, cand_count_dev, s);
 }
 
 double rfd_plan_executed_flops(const rfd_plan *plan) { return plan ? plan->executed_flops : 0.0; }

@@ -21,11 +21,11 @@ __global__ void __launch_bounds__(kThreads) k_fir32(
     const float2 *__restrict__ taps, int32_t k_stride, const int32_t *__restrict__ perm,
     const int32_t *__restrict__ off, const float *__restrict__ scale, int64_t n, float thr,
     uint32_t W, rfd_candidate *__restrict__ cand, int64_t cap,
-    unsigned long long *__restrict__ count) {
+    unsigned long long *__restrict__ count, const int64_t *__restrict__ u_begin) {
     extern __shared__ float2 sm[];
     const RfdTile tile = tiles[blockIdx.y];
     const int K = tile.k_tile;
-    const int64_t u0 = (int64_t)blockIdx.x * kTT;
+    const int64_t u0 = wrap_pos(window_base(u_begin, n), (int64_t)blockIdx.x * kTT, n);
     float2 *qs = sm;                       // [kTT + K - 1]
     float2 *ps = sm + kTT + K - 1;         // [kJT][K]
     const float2 *qr = q + (int64_t)tile.ref * ld + u0;
@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(kThreads) k_fir32(
 
 int fir32_tile_templates() { return kJT; }
 
-rfd_status fir32_launch(const rfd_plan *plan, const float2 *q, rfd_candidate *cand, int64_t cap,
-                        int64_t *count, cudaStream_t s) {
+rfd_status fir32_launch(const rfd_plan *plan, const float2 *q, const int64_t *u_begin, rfd_candidate *cand,
+                        int64_t cap, int64_t *count, cudaStream_t s) {
     const int64_t n = plan->grid.n;
     const size_t shm = (size_t)(kTT + plan->k_max - 1 + kJT * plan->k_max) * sizeof(float2);
     static size_t smem_set[64] = {};
@@ -93,12 +93,12 @@ rfd_status fir32_launch(const rfd_plan *plan, const float2 *q, rfd_candidate *ca
     }
     const unsigned ntiles = (unsigned)plan->tiles.size();
     for (unsigned t0 = 0; t0 < ntiles; t0 += 65535) {
-        dim3 grid((unsigned)(n / kTT), std::min(65535u, ntiles - t0));
+        dim3 grid((unsigned)(plan->out_len / kTT), std::min(65535u, ntiles - t0));
         k_fir32<<<grid, kThreads, shm, s>>>(
             (const RfdTile *)plan->d_tiles.p + t0, q, plan->ld, (const float2 *)plan->d_taps.p,
             plan->k_max, (const int32_t *)plan->d_perm.p, (const int32_t *)plan->d_off.p,
             (const float *)plan->d_scale.p, n, plan->threshold, (uint32_t)plan->window, cand, cap,
-            (unsigned long long *)count);
+            (unsigned long long *)count, u_begin);
         RFD_LAUNCH_CHECK();
     }
     return RFD_OK;

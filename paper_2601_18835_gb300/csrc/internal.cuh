@@ -74,6 +74,20 @@ struct PNParams {
 rfd_status make_pn(const Grid &g, const rfd_params *p, PNParams *out);
 
 // FP64 TaylorF2 phase Psi(f) (t_c = phi_c = 0).
+// Output window of a filtering call: its first position *u_begin (device memory, so that a
+// captured graph can be replayed for another window), taken modulo n and rounded down to a
+// multiple of 512; 0 without a window.  Positions inside it wrap around the circular segment.
+__device__ __forceinline__ int64_t window_base(const int64_t *u_begin, int64_t n) {
+    if (!u_begin) return 0;
+    int64_t b = *u_begin % n;
+    if (b < 0) b += n;
+    return b & ~(int64_t)511;
+}
+__device__ __forceinline__ int64_t wrap_pos(int64_t base, int64_t off, int64_t n) {
+    const int64_t u = base + off;    // base < n, off < n
+    return u >= n ? u - n : u;
+}
+
 __device__ __forceinline__ double pn_phase(double f, const PNParams &p, int flags) {
     const double v = cbrt(kPi * p.mt * f);
     const double v2 = v * v, v3 = v2 * v, v5 = v3 * v2;
@@ -189,6 +203,7 @@ struct rfd_plan {
     int32_t n_ref = 0, n_tmpl = 0, precision = 0, window = 1, halo = 0;
     float threshold = 0.f;
     int64_t ld = 0;                  // q_ref row length
+    int64_t out_len = 0;             // outputs per filtering call (n, or a window of it)
     int32_t k_max = 0;
     int32_t tile_j = 0;              // templates per tile
     std::vector<int32_t> ref_of, k_of;

@@ -122,7 +122,8 @@ __global__ void __launch_bounds__(kThreads) k_block_spectra(const void *__restri
                                                             int64_t n, int32_t L, int32_t nb,
                                                             const int32_t *__restrict__ refs,
                                                             float2 *__restrict__ X,
-                                                            const float2 *__restrict__ stw_g) {
+                                                            const float2 *__restrict__ stw_g,
+                                                            const int64_t *__restrict__ u_begin) {
     extern __shared__ __align__(16) uint8_t sm[];
     float2 *stw = (float2 *)sm;
     float2 *tl = stw + kM;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_block_spectra(const void *__restri
     const int r = refs[blockIdx.y];
     const int b = blockIdx.x * kGroups + g;
     const bool bvalid = b < nb;                         // uniform within the group
-    const int64_t u0 = (int64_t)(bvalid ? b : 0) * L;
+    const int64_t u0 = window_base(u_begin, n) + (int64_t)(bvalid ? b : 0) * L;
     const float sc = PREC == RFD_PREC_FP32 ? 1.f : ldexpf(1.f, -qscale[r]);
     float2 v[16];
 #pragma unroll
@@ -150,6 +151,8 @@ struct RfFftArgs {
     const FftTile *tiles;
     const int64_t *ranges;      // item ranges per CTA; item = tile * nbg + block group
     int32_t nbg, nb, L;
+    int64_t out_len;            // outputs of the window
+    const int64_t *u_begin;     // first output position of the window (device), or NULL
     const float2 *X, *stw;
     const float2 *P;            // [slot - slot0][kM]
     int64_t slot0;              // first block-FFT slot
@@ -171,13 +174,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_fft(const RfFftArgs a) {
     float2 *TA = tl + (2 * g) * kTileLd, *TB = TA + kTileLd;
     for (int i = threadIdx.x; i < kM - 1; i += kThreads) stw[i] = a.stw[i];
     const int64_t it0 = a.ranges[blockIdx.x], it1 = a.ranges[blockIdx.x + 1];
+    const int64_t ubase = window_base(a.u_begin, a.n);
     for (int64_t it = it0; it < it1; ++it) {
         const int64_t ti = it / a.nbg;
         const int bg = (int)(it - ti * a.nbg);
         const FftTile tile = a.tiles[ti];
         const int b = bg * kGroups + g;
         const bool bvalid = b < a.nb;
-        const int64_t u0 = (int64_t)b * a.L;
+        const int64_t u0 = ubase + (int64_t)b * a.L;
+        // outputs l of this block inside the window: l < lim
+        const int64_t rest = a.out_len - (int64_t)b * a.L;
+        const int lim = bvalid ? (int)(rest < a.L ? rest : a.L) : 0;
         const float2 *Xb = a.X + ((int64_t)tile.ref * a.nb + (bvalid ? b : 0)) * kM;
         float2 x[16];
 #pragma unroll
@@ -195,22 +202,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_fft(const RfFftArgs a) {
             for (int r = 0; r < 16; ++r) v[r] = cmul(x[r], Pq[t + kGT * r]);
             group_fft<true>(v, TA, TB, stw, t, 1 + g);
             // epilogue: v[r] = z at u = u0 + t + 128 r
-            bool hit = false;
+            // screen on the largest |z|^2 of the thread (invalid outputs included: a false
+            // alarm only costs the exact pass below, which drops them)
+            float pmax = 0.f;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
-                const int l = t + kGT * r;
-                const bool valid = bvalid && l < a.L && u0 + l < a.n;
-                const float p = __fadd_rn(__fmul_rn(v[r].x, v[r].x), __fmul_rn(v[r].y, v[r].y));
-                hit |= valid && (p > a.thr);
-            }
-            if (__any_sync(0xffffffffu, hit)) {
+            for (int r = 0; r < 16; ++r)
+                pmax = fmaxf(pmax, __fadd_rn(__fmul_rn(v[r].x, v[r].x), __fmul_rn(v[r].y, v[r].y)));
+            if (__any_sync(0xffffffffu, pmax > a.thr)) {
                 const int64_t slot = tile.first + q;
                 const int32_t j = a.perm[slot];
                 const int32_t o = a.off[slot];
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     const int l = t + kGT * r;
-                    const bool valid = bvalid && l < a.L && u0 + l < a.n;
+                    const bool valid = l < lim;
                     const uint32_t tt = (uint32_t)((u0 + l + o) & (a.n - 1));
                     emit_window_max(valid, (uint32_t)j, tt, v[r].x, v[r].y, a.thr, a.W, a.cand, a.cap, a.count);
                 }
@@ -277,8 +282,8 @@ rfd_status fft_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const 
     return RFD_OK;
 }
 
-rfd_status fft_launch(const rfd_plan *plan, const void *q, const int32_t *qscale, rfd_candidate *cand, int64_t cap,
-                      int64_t *count, cudaStream_t s) {
+rfd_status fft_launch(const rfd_plan *plan, const void *q, const int32_t *qscale, const int64_t *u_begin,
+                      rfd_candidate *cand, int64_t cap, int64_t *count, cudaStream_t s) {
     if (plan->fft_tiles.empty()) return RFD_OK;
     static bool attr_set = false;
     if (!attr_set) {
@@ -297,15 +302,15 @@ rfd_status fft_launch(const rfd_plan *plan, const void *q, const int32_t *qscale
     if (plan->precision == RFD_PREC_FP32)
         k_block_spectra<RFD_PREC_FP32><<<gs, kThreads, kSmemSpectra, s>>>(q, qscale, plan->ld, plan->grid.n,
                                                                             plan->fft_L, plan->fft_nb, refs, X,
-                                                                            plan->fft_stw);
+                                                                            plan->fft_stw, u_begin);
     else if (plan->precision == RFD_PREC_FP16X3)
         k_block_spectra<RFD_PREC_FP16X3><<<gs, kThreads, kSmemSpectra, s>>>(q, qscale, plan->ld, plan->grid.n,
                                                                               plan->fft_L, plan->fft_nb, refs, X,
-                                                                              plan->fft_stw);
+                                                                              plan->fft_stw, u_begin);
     else
         k_block_spectra<RFD_PREC_BF16X3><<<gs, kThreads, kSmemSpectra, s>>>(q, qscale, plan->ld, plan->grid.n,
                                                                               plan->fft_L, plan->fft_nb, refs, X,
-                                                                              plan->fft_stw);
+                                                                              plan->fft_stw, u_begin);
     RFD_LAUNCH_CHECK();
     RfFftArgs a;
     a.tiles = (const FftTile *)plan->d_fft_tiles.p;
@@ -313,6 +318,8 @@ rfd_status fft_launch(const rfd_plan *plan, const void *q, const int32_t *qscale
     a.nbg = plan->fft_nbg;
     a.nb = plan->fft_nb;
     a.L = plan->fft_L;
+    a.out_len = plan->out_len;
+    a.u_begin = u_begin;
     a.X = X;
     a.P = (const float2 *)plan->d_fft_P.p;
     a.slot0 = plan->fft_slot0;

@@ -54,7 +54,8 @@ enum {
 struct TcArgs {
     const TcTile *tiles;
     const int64_t *ranges;      // [gridDim.x + 1] item ranges
-    int64_t n_tt;               // time blocks per tile = n / 128
+    int64_t n_tt;               // time blocks per tile = window length / 128
+    const int64_t *u_begin;     // first output position of the window (device), or NULL
     const uint8_t *taps;        // operand images
     const uint16_t *q;          // q planes (fp16 or bf16 bits)
     int64_t ld;
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
     volatile uint32_t *abort_flag = &s_misc[1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t it0 = A.ranges[blockIdx.x], it1 = A.ranges[blockIdx.x + 1];
+    const int64_t ubase = window_base(A.u_begin, A.n);
     const uint32_t bar0 = smem_u32(bars);
 #define BAR(i) (bar0 + 8u * (uint32_t)(i))
 
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
                 const uint32_t wbytes = (uint32_t)(kM + T.kpad) * 2u;
                 mbar_arrive_expect_tx(BAR(kBarQFull + qb), 4u * wbytes);
                 for (int p = 0; p < 4; ++p) {
-                    const uint16_t *src = A.q + (int64_t)(4 * T.ref + p) * A.ld + tt * kM;
+                    const uint16_t *src = A.q + (int64_t)(4 * T.ref + p) * A.ld + wrap_pos(ubase, tt * kM, A.n);
                     bulk_g2s(smem_u32(s_q + (qb * 4 + p) * A.win), src, wbytes, BAR(kBarQFull + qb));
                 }
             }
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
             if (!__all_sync(0xffffffffu, ok)) break;
             fence_after();
             const float esc = ldexpf(1.0f, -A.qscale[T.ref]);
-            const int64_t u = tt * kM + row;
+            const int64_t u = wrap_pos(ubase, tt * kM, A.n) + row;
             const int per = T.nt >> 1;                    // templates per half (multiple of 8)
             const int a_begin = half * per, a_end = a_begin + per;
             if (per < 32 && half == 1) {
@@ -445,13 +447,14 @@ rfd_status tc_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const i
     return RFD_OK;
 }
 
-rfd_status tc_launch(const rfd_plan *plan, const void *q, const int32_t *qscale, rfd_candidate *cand, int64_t cap,
-                     int64_t *count, cudaStream_t s) {
+rfd_status tc_launch(const rfd_plan *plan, const void *q, const int32_t *qscale, const int64_t *u_begin,
+                     rfd_candidate *cand, int64_t cap, int64_t *count, cudaStream_t s) {
     if (plan->tc_tiles.empty()) return RFD_OK;
     TcArgs a;
     a.tiles = (const TcTile *)plan->d_tiles.p;
     a.ranges = (const int64_t *)plan->d_ranges.p;
-    a.n_tt = plan->grid.n / kM;
+    a.n_tt = plan->out_len / kM;
+    a.u_begin = u_begin;
     a.taps = (const uint8_t *)plan->d_taps.p;
     a.q = (const uint16_t *)q;
     a.ld = plan->ld;

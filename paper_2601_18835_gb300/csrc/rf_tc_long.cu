@@ -60,7 +60,8 @@ enum {
 struct TlArgs {
     const TcTile *tiles;
     const int64_t *ranges;      // [gridDim.x + 1] item ranges
-    int64_t n_tb;               // time blocks per tile = n / 256
+    int64_t n_tb;               // time blocks per tile = window length / 256
+    const int64_t *u_begin;     // first output position of the window (device), or NULL
     const uint8_t *taps;        // operand images
     const uint16_t *q;          // q planes (fp16 or bf16 bits)
     int64_t ld;
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
     volatile uint32_t *abort_flag = &s_misc[1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t it0 = A.ranges[blockIdx.x], it1 = A.ranges[blockIdx.x + 1];
+    const int64_t ubase = window_base(A.u_begin, A.n);
     const uint32_t bar0 = smem_u32(bars);
 #define BAR(i) (bar0 + 8u * (uint32_t)(i))
 
@@ -181,7 +183,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                 mbar_arrive_expect_tx(BAR(kBarQFull + qb), 4u * wbytes);
                 for (int p = 0; p < 4; ++p)
                     bulk_g2s(smem_u32(s_qw + (qb * 4u + (uint32_t)p) * A.qwin),
-                             A.q + (int64_t)(4 * T.ref + p) * A.ld + tb * kN, wbytes, BAR(kBarQFull + qb));
+                             A.q + (int64_t)(4 * T.ref + p) * A.ld + wrap_pos(ubase, tb * kN, A.n), wbytes,
+                             BAR(kBarQFull + qb));
                 bool ok = true;
                 for (int c = 0; c < T.nch; ++c, ++ka) {
                     const uint32_t st = ka % kAStages, r = ka / kAStages;
@@ -376,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                         // (window, run of samples); ties keep the earlier t
                         uint32_t bw = 0xffffffffu, bp = 0u, bt = 0u;
                         float bzr = 0.f, bzi = 0.f;
-                        const int64_t u0 = tb * kN + c0 + col_off;
+                        const int64_t u0 = wrap_pos(ubase, tb * kN, A.n) + c0 + col_off;
 #pragma unroll 1
                         for (int i = 0; i < 16; ++i) {
                             if (!((hit >> i) & 1u)) continue;
@@ -535,13 +538,14 @@ rfd_status tl_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const i
     return RFD_OK;
 }
 
-rfd_status tl_launch(const rfd_plan *plan, const void *q, const int32_t *qscale, rfd_candidate *cand, int64_t cap,
-                     int64_t *count, cudaStream_t s) {
+rfd_status tl_launch(const rfd_plan *plan, const void *q, const int32_t *qscale, const int64_t *u_begin,
+                     rfd_candidate *cand, int64_t cap, int64_t *count, cudaStream_t s) {
     if (plan->tl_tiles.empty()) return RFD_OK;
     TlArgs a;
     a.tiles = (const TcTile *)plan->d_tl_tiles.p;
     a.ranges = (const int64_t *)plan->d_tl_ranges.p;
-    a.n_tb = plan->grid.n / kN;
+    a.n_tb = plan->out_len / kN;
+    a.u_begin = u_begin;
     a.taps = (const uint8_t *)plan->d_tl_taps.p;
     a.q = (const uint16_t *)q;
     a.ld = plan->ld;

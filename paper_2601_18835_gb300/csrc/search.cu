@@ -8,8 +8,8 @@
 namespace rfd {
 rfd_status filter_reference_impl(rfd_ctx *, const Grid &, const float2 *, const double *, const float2 *,
                                  int64_t, int32_t, int32_t, void *, int32_t *, cudaStream_t);
-rfd_status ratio_filter_enqueue(const rfd_plan *, const void *, const int32_t *, rfd_candidate *, int64_t,
-                                int64_t *, cudaStream_t);
+rfd_status ratio_filter_enqueue(const rfd_plan *, const void *, const int32_t *, const int64_t *, rfd_candidate *,
+                                int64_t, int64_t *, cudaStream_t);
 void add_launches(int64_t n);
 int64_t launch_count();
 }  // namespace rfd
@@ -33,6 +33,8 @@ struct rfd_search {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the ratio-filter kernel, inside the graph
     cudaEvent_t evs = nullptr, eve = nullptr;   // first and last node of the graph
     bool pinned = false;                        // holds a graphs_pin()
+    int64_t *d_ubase = nullptr;                 // window start read by the filtering kernels
+    int64_t *h_ubase = nullptr;                 // pinned staging for it
 };
 
 namespace rfd {
@@ -51,7 +53,7 @@ rfd_status enqueue_step(rfd_search *S, cudaStream_t s, bool capturing) {
                                   S->qscale, s));
     RFD_TRY_CUDA(cudaMemsetAsync(S->count, 0, sizeof(int64_t), s));
     RFD_TRY_CUDA(record(S->ev0, s, capturing));
-    RFD_TRY(ratio_filter_enqueue(p, S->qref, S->qscale, S->cand, S->cap, S->count, s));
+    RFD_TRY(ratio_filter_enqueue(p, S->qref, S->qscale, S->d_ubase, S->cand, S->cap, S->count, s));
     RFD_TRY_CUDA(record(S->ev1, s, capturing));
     RFD_TRY(find_triggers_enqueue(p->ctx, p->n_tmpl, S->cand, S->count, S->cap, S->trig, S->trig_cap, S->host, s));
     RFD_TRY_CUDA(record(S->eve, s, capturing));
@@ -71,6 +73,8 @@ void rfd_search_destroy(rfd_search *S) {
     if (S->pinned) graphs_unpin();
     if (S->graph) cudaGraphDestroy(S->graph);
     if (S->host) cudaFreeHost(S->host);
+    if (S->h_ubase) cudaFreeHost(S->h_ubase);
+    if (S->d_ubase) cudaFree(S->d_ubase);
     if (S->ev0) cudaEventDestroy(S->ev0);
     if (S->ev1) cudaEventDestroy(S->ev1);
     if (S->evs) cudaEventDestroy(S->evs);
@@ -106,8 +110,11 @@ rfd_status rfd_search_create(rfd_plan *plan, const void *dtilde_dev, const doubl
     rfd_status st = RFD_OK;
     do {
         cudaError_t e = cudaMallocHost((void **)&S->host, sizeof(TrigReadback));
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_ubase, sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_ubase, sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMemset(S->d_ubase, 0, sizeof(int64_t));
         if (e != cudaSuccess) {
-            set_error("cudaMallocHost failed: %s", cudaGetErrorString(e));
+            set_error("search allocation failed: %s", cudaGetErrorString(e));
             st = RFD_ERR_NOMEM;
             break;
         }
@@ -158,6 +165,17 @@ rfd_status rfd_search_create(rfd_plan *plan, const void *dtilde_dev, const doubl
     }
     *out = S;
     return RFD_OK;
+}
+
+rfd_status rfd_search_run_at(rfd_search *S, int64_t u_begin, void *stream, int64_t *n_trig_host) {
+    RFD_REQUIRE(S && n_trig_host, RFD_ERR_ARG, "NULL argument");
+    RFD_REQUIRE(u_begin >= 0 && u_begin < S->plan->grid.n && u_begin % 512 == 0, RFD_ERR_ARG,
+                "u_begin=%lld must be a multiple of 512 in [0, n)", (long long)u_begin);
+    RFD_TRY_CUDA(cudaSetDevice(S->plan->ctx->device));
+    *S->h_ubase = u_begin;
+    RFD_TRY_CUDA(cudaMemcpyAsync(S->d_ubase, S->h_ubase, sizeof(int64_t), cudaMemcpyHostToDevice,
+                                 (cudaStream_t)stream));
+    return rfd_search_run(S, stream, n_trig_host);
 }
 
 rfd_status rfd_search_run(rfd_search *S, void *stream, int64_t *n_trig_host) {

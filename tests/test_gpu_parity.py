@@ -599,6 +599,100 @@ def test_search_survives_scratch_growth(c1):
     plan.close()
 
 
+WINDOW_KERNELS = [("fp32", 0, {}), ("time_on_m", 1, {"long_k": 512}), ("templates_on_m", 1, {"long_k": 0}),
+                  ("block_fft", 1, {"fft_k": 0})]
+
+
+def _merge_windows(trig_list, window):
+    """Per (j, t // window) the trigger with the largest |z|^2 (ties: smallest t) over the
+    windows' trigger lists, as find_triggers merges candidates."""
+    best = {}
+    for tr in trig_list:
+        for x in tr:
+            key = (int(x["j"]), int(x["t"]) // window)
+            cur = best.get(key)
+            if cur is None or (x["snr2"], -int(x["t"])) > (cur["snr2"], -int(cur["t"])):
+                best[key] = x
+    return best
+
+
+@pytest.mark.parametrize("kernel,prec,opts", WINDOW_KERNELS)
+def test_windows_tile_the_segment(c1, kernel, prec, opts):
+    """Streaming (out_len = 2048 of n = 16384): the eight windows' candidates, merged by
+    find_triggers, give the full-segment triggers (bit for bit on the direct kernels; the
+    block-FFT kernel cuts its blocks at each window start, so there SNRs agree to 1e-5)."""
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    q, e, _ = gpu.filter_reference(halo, prec)
+    full, _ = gpu.ratio_filter(t, q, e, prec, halo, options=opts)
+    B = 2048
+    plan = rfd.Plan(gpu.ctx, gpu.grid, bank.n_ref, bank.ref_of_tmpl, t["K"], prec, cfg.window, cfg.threshold, halo,
+                    options=dict(opts, out_len=B))
+    plan.set_taps(t["taps"], t["k_stride"], t["lag"], t["sigma"])
+    cap = 1 << 16
+    parts, total = [], 0
+    u = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for w0 in range(0, cfg.n, B):
+        cand = torch.zeros(cap * 24, dtype=torch.uint8, device="cuda")
+        u.fill_(w0)
+        plan.ratio_filter_window(q, e, u, cand, cnt)
+        nc = int(cnt.item())
+        assert nc < cap
+        parts.append(cand[: nc * 24].clone())
+        total += nc
+    plan.close()
+    allc = torch.cat(parts) if total else torch.zeros(24, dtype=torch.uint8, device="cuda")
+    cnt.fill_(total)
+    tb = torch.zeros((1 << 16) * 20, dtype=torch.uint8, device="cuda")
+    nt = rfd.find_triggers(gpu.ctx, bank.n_tmpl, allc, cnt, tb)
+    got = rfd.triggers_to_numpy(tb, nt)
+    assert len(full) > 0
+    if kernel != "block_fft":
+        assert np.array_equal(got.view(np.uint8), full.view(np.uint8))
+    else:
+        a = {(int(x["j"]), int(x["t"]) // cfg.window): x for x in full}
+        b = {(int(x["j"]), int(x["t"]) // cfg.window): x for x in got}
+        assert len(set(a) ^ set(b)) <= 2
+        for key in set(a) & set(b):
+            assert abs(math.sqrt(float(a[key]["snr2"])) / math.sqrt(float(b[key]["snr2"])) - 1) < 1e-5
+
+
+def test_streaming_search_graph(c1):
+    """A captured search on a window plan, replayed at each window start (rfd_search_run_at):
+    the windows' triggers merged per (template, window) equal the full-segment search's."""
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    href = gpu.templates(bank.ref_params())
+    ld = rfd.qref_ld(cfg.n, halo)
+    stream = torch.cuda.Stream()
+    out = []
+    for out_len in (0, 2048):
+        q = torch.zeros(bank.n_ref * ld * 8, dtype=torch.uint8, device="cuda")
+        e = torch.zeros(bank.n_ref, dtype=torch.int32, device="cuda")
+        plan = rfd.Plan(gpu.ctx, gpu.grid, bank.n_ref, bank.ref_of_tmpl, t["K"], rfd.PREC_FP16X3, cfg.window,
+                        cfg.threshold, halo, options={"out_len": out_len})
+        plan.set_taps(t["taps"], t["k_stride"], t["lag"], t["sigma"])
+        cand = torch.zeros((1 << 18) * 24, dtype=torch.uint8, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        trig = torch.zeros((1 << 16) * 20, dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(stream):
+            search = rfd.Search(plan, gpu.d, gpu.psd, href, q, e, cand, cnt, trig, stream)
+        lists = []
+        for w0 in (range(0, cfg.n, out_len) if out_len else [0]):
+            nt = search.run(u_begin=w0)
+            lists.append(rfd.triggers_to_numpy(trig, nt).copy())
+        out.append(_merge_windows(lists, cfg.window))
+        search.close()
+        plan.close()
+    full, win = out
+    assert len(full) > 0 and set(full) == set(win)
+    for key in full:
+        assert full[key].tobytes() == win[key].tobytes()
+
+
 def test_autotuner_choices_give_identical_triggers(ctx, tmp_path):
     """Every tile choice the autotuner tries gives bit-identical triggers (tiles only change
     which templates share an MMA and how many zero taps pad them); the tuner caches its pick."""
@@ -643,8 +737,8 @@ def test_autotuner_choices_give_identical_triggers(ctx, tmp_path):
             assert np.array_equal(r, results[0])
             continue
         got = r.view(rfd.TRIGGER_DTYPE)
-        a = {(int(x["j"]), int(x["w"])): x for x in base}
-        b = {(int(x["j"]), int(x["w"])): x for x in got}
+        a = {(int(x["j"]), int(x["t"]) // cfg.window): x for x in base}
+        b = {(int(x["j"]), int(x["t"]) // cfg.window): x for x in got}
         diff = set(a) ^ set(b)
         assert len(diff) <= 0.01 * len(a), (c["options"], len(diff))
         for key in set(a) & set(b):
