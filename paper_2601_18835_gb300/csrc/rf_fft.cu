@@ -38,12 +38,40 @@ __device__ __forceinline__ void group_bar(int id) {
 
 // Length-2048 transform by one 128-thread group: thread t holds elements t + 128 r (r < 16) in
 // v on entry and on exit (natural order).  Passes: radix 8 (ns = 1) into tile A, radix 16
-// (ns = 8) from A into B, radix 16 (ns = 128) from B into registers.  stw: the stage twiddles
-// of length 2048 (7 + 120 + 1920 entries).  Every thread of the group calls this; bar is the
+// (ns = 8) from A into B, radix 16 (ns = 128) from B into registers.  tw: the twiddles of the
+// last two passes as built by build_twiddles (in shared memory).  Every thread of the group calls this; bar is the
 // group's named barrier.  Two calls in a row are safe: a thread writes A again only after
 // every thread of the group passed the barrier that follows its reads of A, and likewise B.
+// Thread-major, XOR-swizzled rows of 16 complex values: value r of row i is float2 index
+// 16 i + 2 ((r / 2) ^ (i & 7)) + (r & 1), so that eight threads reading the 16-byte chunk c of
+// eight consecutive rows hit eight different bank groups.
+__device__ __forceinline__ int swz(int i, int c) { return 16 * i + 2 * (c ^ (i & 7)); }
+
+// Reads row i (16 values) with eight 16-byte loads.
+__device__ __forceinline__ void load_row16(float2 (&w)[16], const float2 *base, int i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float4 q = *reinterpret_cast<const float4 *>(base + swz(i, c));
+        w[2 * c] = make_float2(q.x, q.y);
+        w[2 * c + 1] = make_float2(q.z, q.w);
+    }
+}
+
+// Twiddles of the last two passes in the swizzled row layout: rows k < 8 (pass 2, value r =
+// w_128^(r k)) then rows t < 128 (pass 3, value r = w_2048^(r t)); value 0 of each row is 1.
+// Built from the stage table (7 + 120 + 1920 entries) by the whole CTA.
+constexpr int kTwRows = 8 + kGT;
+__device__ __forceinline__ void build_twiddles(float2 *tw, const float2 *__restrict__ stage) {
+    for (int e = threadIdx.x; e < kTwRows * 16; e += blockDim.x) {
+        const int i = e >> 4, r = e & 15;
+        float2 w = make_float2(1.f, 0.f);
+        if (r > 0) w = i < 8 ? stage[7 + (r - 1) * 8 + i] : stage[127 + (r - 1) * kGT + (i - 8)];
+        tw[swz(i, r >> 1) + (r & 1)] = w;
+    }
+}
+
 template <bool INV>
-__device__ __forceinline__ void group_fft(float2 (&v)[16], float2 *A, float2 *B, const float2 *stw, int t,
+__device__ __forceinline__ void group_fft(float2 (&v)[16], float2 *A, float2 *B, const float2 *tw, int t,
                                           int bar) {
     {
         float2 a[8], b[8];
@@ -63,14 +91,12 @@ __device__ __forceinline__ void group_fft(float2 (&v)[16], float2 *A, float2 *B,
     group_bar(bar);
     {
         const int k = t & 7;
-        float2 a[16];
+        float2 a[16], w[16];
 #pragma unroll
         for (int r = 0; r < 16; ++r) a[r] = A[tpos(t + kGT * r)];
+        load_row16(w, tw, k);
 #pragma unroll
-        for (int r = 1; r < 16; ++r) {
-            const float2 w = stw[7 + (r - 1) * 8 + k];
-            a[r] = INV ? cmul(a[r], w) : cmulc(a[r], w);
-        }
+        for (int r = 1; r < 16; ++r) a[r] = INV ? cmul(a[r], w[r]) : cmulc(a[r], w[r]);
         dft_reg<float, 16, INV>(a);
         const int idx = ((t - k) << 4) + k;
 #pragma unroll
@@ -79,10 +105,11 @@ __device__ __forceinline__ void group_fft(float2 (&v)[16], float2 *A, float2 *B,
     group_bar(bar);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = B[tpos(t + kGT * r)];
+    {
+        float2 w[16];
+        load_row16(w, tw, 8 + t);
 #pragma unroll
-    for (int r = 1; r < 16; ++r) {
-        const float2 w = stw[127 + (r - 1) * kGT + t];
-        v[r] = INV ? cmul(v[r], w) : cmulc(v[r], w);
+        for (int r = 1; r < 16; ++r) v[r] = INV ? cmul(v[r], w[r]) : cmulc(v[r], w[r]);
     }
     dft_reg<float, 16, INV>(v);
 }
@@ -125,11 +152,11 @@ __global__ void __launch_bounds__(kThreads) k_block_spectra(const void *__restri
                                                             const float2 *__restrict__ stw_g,
                                                             const int64_t *__restrict__ u_begin) {
     extern __shared__ __align__(16) uint8_t sm[];
-    float2 *stw = (float2 *)sm;
-    float2 *tl = stw + kM;
+    float2 *tw = (float2 *)sm;                  // [kTwRows][16] swizzled twiddle rows
+    float2 *tl = tw + kTwRows * 16;
     const int g = threadIdx.x / kGT, t = threadIdx.x % kGT;
     float2 *TA = tl + (2 * g) * kTileLd, *TB = TA + kTileLd;
-    for (int i = threadIdx.x; i < kM - 1; i += kThreads) stw[i] = stw_g[i];
+    build_twiddles(tw, stw_g);
     __syncthreads();
     const int r = refs[blockIdx.y];
     const int b = blockIdx.x * kGroups + g;
@@ -139,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_block_spectra(const void *__restri
     float2 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = load_q<PREC>(q, r, ld, (u0 + t + kGT * i) & (n - 1), sc);
-    group_fft<false>(v, TA, TB, stw, t, 1 + g);
+    group_fft<false>(v, TA, TB, tw, t, 1 + g);
     if (bvalid) {
         float2 *dst = X + ((int64_t)r * nb + b) * kM;
 #pragma unroll
@@ -154,7 +181,7 @@ struct RfFftArgs {
     int64_t out_len;            // outputs of the window
     const int64_t *u_begin;     // first output position of the window (device), or NULL
     const float2 *X, *stw;
-    const float2 *P;            // [slot - slot0][kM]
+    const float2 *P;            // [slot - slot0][kM], row layout of swz (row t holds k = t + 128 r)
     int64_t slot0;              // first block-FFT slot
     const int32_t *perm, *off;
     int64_t n;
@@ -167,12 +194,12 @@ struct RfFftArgs {
 
 __global__ void __launch_bounds__(kThreads, 1) k_rf_fft(const RfFftArgs a) {
     extern __shared__ __align__(16) uint8_t sm[];
-    float2 *stw = (float2 *)sm;                 // [kM] stage twiddles
-    float2 *Ps = stw + kM;                      // [2][kM] template spectra, double-buffered
+    float2 *tw = (float2 *)sm;                  // [kTwRows][16] swizzled twiddle rows
+    float2 *Ps = tw + kTwRows * 16;             // [2][kM] template spectra, double-buffered
     float2 *tl = Ps + 2 * kM;                   // [kGroups][2][kTileLd]
     const int g = threadIdx.x / kGT, t = threadIdx.x % kGT;
     float2 *TA = tl + (2 * g) * kTileLd, *TB = TA + kTileLd;
-    for (int i = threadIdx.x; i < kM - 1; i += kThreads) stw[i] = a.stw[i];
+    build_twiddles(tw, a.stw);
     const int64_t it0 = a.ranges[blockIdx.x], it1 = a.ranges[blockIdx.x + 1];
     const int64_t ubase = window_base(a.u_begin, a.n);
     for (int64_t it = it0; it < it1; ++it) {
@@ -196,11 +223,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_fft(const RfFftArgs a) {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
             __syncthreads();                    // P_q visible to all; buffer (q + 1) & 1 free
             if (q + 1 < tile.count) stage_p(Ps + ((q + 1) & 1) * kM, Pt + (int64_t)(q + 1) * kM);
-            const float2 *Pq = Ps + (q & 1) * kM;
             float2 v[16];
+            load_row16(v, Ps + (q & 1) * kM, t);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[r] = cmul(x[r], Pq[t + kGT * r]);
-            group_fft<true>(v, TA, TB, stw, t, 1 + g);
+            for (int r = 0; r < 16; ++r) v[r] = cmul(x[r], v[r]);
+            group_fft<true>(v, TA, TB, tw, t, 1 + g);
             // epilogue: v[r] = z at u = u0 + t + 128 r
             // screen on the largest |z|^2 of the thread (invalid outputs included: a false
             // alarm only costs the exact pass below, which drops them)
@@ -233,7 +260,11 @@ __global__ void __launch_bounds__(kGT) k_taps_spectra(const float2 *__restrict__
                                                       const double *__restrict__ sigma, int64_t n, int64_t slot0,
                                                       int64_t s_off, float2 *__restrict__ P, int32_t *__restrict__ off,
                                                       const float2 *__restrict__ stw) {
-    __shared__ __align__(16) float2 tiles[2 * kTileLd];
+    extern __shared__ __align__(16) uint8_t sm[];
+    float2 *tw = (float2 *)sm;
+    float2 *tiles = tw + kTwRows * 16;
+    build_twiddles(tw, stw);
+    __syncthreads();
     const int64_t local = s_off + blockIdx.x;
     const int64_t slot = slot0 + local;
     const int t = threadIdx.x;
@@ -252,15 +283,17 @@ __global__ void __launch_bounds__(kGT) k_taps_spectra(const float2 *__restrict__
             v[r] = make_float2(0.f, 0.f);
         }
     }
-    group_fft<true>(v, tiles, tiles + kTileLd, stw, t, 1);
+    group_fft<true>(v, tiles, tiles + kTileLd, tw, t, 1);
     float2 *dst = P + local * kM;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) dst[t + kGT * r] = v[r];
+    for (int c = 0; c < 8; ++c)
+        *reinterpret_cast<float4 *>(dst + swz(t, c)) = make_float4(v[2 * c].x, v[2 * c].y, v[2 * c + 1].x, v[2 * c + 1].y);
     if (t == 0) off[slot] = (int32_t)((((int64_t)lag[j] + K - 1) % n + n) % n);
 }
 
-constexpr size_t kSmemSpectra = (size_t)(kM + 2 * kGroups * kTileLd) * sizeof(float2);
-constexpr size_t kSmemFilter = (size_t)(3 * kM + 2 * kGroups * kTileLd) * sizeof(float2);
+constexpr size_t kSmemSpectra = (size_t)(kTwRows * 16 + 2 * kGroups * kTileLd) * sizeof(float2);
+constexpr size_t kSmemFilter = (size_t)(kTwRows * 16 + 2 * kM + 2 * kGroups * kTileLd) * sizeof(float2);
+constexpr size_t kSmemTaps = (size_t)(kTwRows * 16 + 2 * kTileLd) * sizeof(float2);
 
 }  // namespace
 
@@ -271,9 +304,14 @@ int fft_fir_blocks_per_cta() { return kGroups; }
 rfd_status fft_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const int32_t *lag, const double *sigma,
                     cudaStream_t s) {
     if (plan->fft_nslots == 0) return RFD_OK;
+    static bool attr_set = false;
+    if (!attr_set) {
+        RFD_TRY_CUDA(cudaFuncSetAttribute(k_taps_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTaps));
+        attr_set = true;
+    }
     for (int64_t s0 = 0; s0 < plan->fft_nslots; s0 += 65535) {
         const unsigned nblk = (unsigned)std::min<int64_t>(65535, plan->fft_nslots - s0);
-        k_taps_spectra<<<nblk, kGT, 0, s>>>(taps, k_stride, (const int32_t *)plan->d_perm.p,
+        k_taps_spectra<<<nblk, kGT, kSmemTaps, s>>>(taps, k_stride, (const int32_t *)plan->d_perm.p,
                                              (const int32_t *)plan->d_kslot.p, lag, sigma, plan->grid.n,
                                              plan->fft_slot0, s0, (float2 *)plan->d_fft_P.p,
                                              (int32_t *)plan->d_off.p, plan->fft_stw);
