@@ -23,7 +23,10 @@
 // consecutive rows: conflict-free), warps 8-15 drain: a warp of lane quarter 2/3 (imaginary
 // rows) and the warp of quarter 0/1 (real rows, same templates) swap half of each 32-column
 // chunk through shared memory, and each forms z, |z|^2 and the per-window maxima of its 16
-// columns.  Every wait is bounded.
+// columns.  The MMA thread waits once per item, on a barrier of the item's buffer that the
+// epilogue (accumulator free), the builders (Y built) and the producer (first taps chunk, with
+// its bytes) all arrive on; taps chunks already in their stage are not copied again.  Every
+// wait is bounded.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -47,10 +50,10 @@ constexpr uint32_t kSpin = 1u << 22;
 enum {
     kBarAFull = 0,      // kAStages
     kBarAEmpty = 2,     // kAStages
-    kBarYFull = 4,      // 2
+    kBarGo = 4,         // 2: accumulator free + Y built + chunk 0 staged, per item buffer
     kBarYEmpty = 6,     // 2
     kBarDFull = 8,      // 2
-    kBarDEmpty = 10,    // 2
+    kBarUnused = 10,    // 2
     kBarQFull = 12,     // 2
     kBarQEmpty = 14,    // 2
     kBarDone = 16,
@@ -147,10 +150,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
             mbar_init(BAR(kBarAEmpty + s), 1);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(BAR(kBarYFull + b), 4);
+            // one phase per use of item buffer b: 8 epilogue warps (the accumulator is free),
+            // 4 builder warps (Y is built), the producer (chunk 0 of the taps, with its bytes)
+            mbar_init(BAR(kBarGo + b), 8 + 4 + 1);
             mbar_init(BAR(kBarYEmpty + b), 1);
             mbar_init(BAR(kBarDFull + b), 1);
-            mbar_init(BAR(kBarDEmpty + b), 8);
+            mbar_init(BAR(kBarUnused + b), 1);
             mbar_init(BAR(kBarQFull + b), 1);
             mbar_init(BAR(kBarQEmpty + b), 4);
         }
@@ -168,10 +173,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
         // ------------------------------------------------------------ producer: taps chunks
         if (lane == 0) {
             uint32_t ka = 0, li = 0;
-            int64_t prev = -1;
+            static_assert(kAStages == 2, "two A stages");
+            int64_t held0 = -1, held1 = -1;      // taps-image offset each A stage holds (-1: none)
+            int64_t ti = it0 / A.n_tb, tb = it0 - ti * A.n_tb, prev = -1;
             TcTile T{};
-            for (int64_t it = it0; it < it1; ++it, ++li) {
-                const int64_t ti = it / A.n_tb, tb = it - ti * A.n_tb;
+            for (int64_t it = it0; it < it1; ++it, ++li, tb = (tb + 1 == A.n_tb) ? 0 : tb + 1, ti += (tb == 0)) {
                 if (ti != prev) {
                     T = A.tiles[ti];
                     prev = ti;
@@ -192,11 +198,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(BAR(kBarAFull + st), kChunkBytes);
-                    const uint8_t *src = A.taps + T.taps_off + (int64_t)c * kChunkBytes;
-                    bulk_g2s(smem_u32(s_a + st * kChunkBytes), src, kChunkImg, BAR(kBarAFull + st));
-                    bulk_g2s(smem_u32(s_a + st * kChunkBytes) + kChunkImg, src + kChunkImg, kChunkImg,
-                             BAR(kBarAFull + st));
+                    // chunk 0 completes on the item's go barrier, later chunks on the stage's
+                    const uint32_t full = c == 0 ? BAR(kBarGo + (li & 1u)) : BAR(kBarAFull + st);
+                    const int64_t want = T.taps_off + (int64_t)c * kChunkBytes;
+                    if ((st == 0u ? held0 : held1) == want) {
+                        // the stage already holds this chunk (a tile whose chunks all fit the
+                        // stages, as at K <= 128): no copy, only the phase
+                        mbar_arrive(full);
+                        continue;
+                    }
+                    if (st == 0u)
+                        held0 = want;
+                    else
+                        held1 = want;
+                    mbar_arrive_expect_tx(full, kChunkBytes);
+                    const uint8_t *src = A.taps + want;
+                    bulk_g2s(smem_u32(s_a + st * kChunkBytes), src, kChunkImg, full);
+                    bulk_g2s(smem_u32(s_a + st * kChunkBytes) + kChunkImg, src + kChunkImg, kChunkImg, full);
                 }
                 if (!ok) break;
             }
@@ -204,33 +222,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            uint32_t ka = 0, li = 0;
+            uint32_t ka = 0, li = 0, uf0 = 0, uf1 = 0;
             const uint32_t idn = idesc_f16(128, kN, BF16, 0);
             const uint32_t a_base = smem_u32(s_a), y_base = smem_u32(s_y);
-            int64_t prev = -1;
+            int64_t ti = it0 / A.n_tb, tb = it0 - ti * A.n_tb, prev = -1;
             TcTile T{};
-            for (int64_t it = it0; it < it1; ++it, ++li) {
-                if (it / A.n_tb != prev) {
-                    prev = it / A.n_tb;
-                    T = A.tiles[prev];
+            bool go_seen = false;                 // the go barrier of this item was already waited on
+            for (int64_t it = it0; it < it1; ++it, ++li, tb = (tb + 1 == A.n_tb) ? 0 : tb + 1, ti += (tb == 0)) {
+                if (ti != prev) {
+                    prev = ti;
+                    T = A.tiles[ti];
                 }
                 const uint32_t acc = li & 1u, yb = li & 1u, use = li >> 1;
-                if (!wait_bar(BAR(kBarDEmpty + acc), (use & 1u) ^ 1u, abort_flag, A.count)) break;
-                if (!wait_bar(BAR(kBarYFull + yb), use & 1u, abort_flag, A.count)) break;
+                // one wait: the accumulator is free, Y is built and chunk 0 of the taps is staged
+                if (!go_seen && !wait_bar(BAR(kBarGo + acc), use & 1u, abort_flag, A.count)) break;
+                go_seen = false;
                 fence_after();
                 const uint32_t d = tmem + acc * (uint32_t)kN;
                 const uint32_t y0 = y_base + yb * 4u * A.ystride;
                 bool ok = true;
                 for (int c = 0; c < T.nch; ++c, ++ka) {
-                    const uint32_t st = ka % kAStages, r = ka / kAStages;
-                    if (!wait_bar(BAR(kBarAFull + st), r & 1u, abort_flag, A.count)) {
-                        ok = false;
-                        break;
+                    const uint32_t st = ka % kAStages;
+                    if (c > 0) {
+                        const uint32_t uf = st == 0u ? uf0++ : uf1++;
+                        if (!wait_bar(BAR(kBarAFull + st), uf & 1u, abort_flag, A.count)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
                     }
-                    fence_after();
                     const uint32_t ah = a_base + st * kChunkBytes, al = ah + kChunkImg;
                     const int s_end = min(4, T.nk16 - 4 * c);
                     for (int s = 0; s < s_end; ++s) {
+                        if (c == T.nch - 1 && s == s_end - 1 && it + 1 < it1) {
+                            // the next item's go barrier, waited on while this item's earlier
+                            // MMAs still run (deadlock-free: it needs only work issued before)
+                            const uint32_t nli = li + 1u;
+                            if (!wait_bar(BAR(kBarGo + (nli & 1u)), (nli >> 1) & 1u, abort_flag, A.count)) {
+                                ok = false;
+                                break;
+                            }
+                            go_seen = true;
+                        }
                         const uint32_t o = (uint32_t)s * 32u;
                         const uint64_t A2h = desc_sw128(ah + o), A2l = desc_sw128(al + o);               // [-Pi; Pr]
                         const uint64_t A1h = desc_sw128(ah + kNT * 128u + o), A1l = desc_sw128(al + kNT * 128u + o);  // [Pr; Pi]
@@ -247,11 +280,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                         mma_ss(d, A2l, Qih, idn, 1u);
                         mma_ss(d, A2h, Qil, idn, 1u);
                     }
+                    if (!ok) break;
                     mma_commit(BAR(kBarAEmpty + st));
                 }
                 if (!ok) break;
+                // one commit: the accumulator is full and Y buffer yb (= acc) is free again
                 mma_commit(BAR(kBarDFull + acc));
-                mma_commit(BAR(kBarYEmpty + yb));
             }
             // every MMA this thread issued has completed before TMEM is released
             mma_commit(BAR(kBarDone));
@@ -262,15 +296,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
         // ------------------------------------------------------------ Y builders
         const int bt = (warp - 4) * 32 + lane;          // 0..127
         uint32_t li = 0;
-        int64_t prev = -1;
         int kpad = 0;
-        for (int64_t it = it0; it < it1; ++it, ++li) {
-            if (it / A.n_tb != prev) {
-                prev = it / A.n_tb;
-                kpad = A.tiles[prev].kpad;
+        int64_t ti = it0 / A.n_tb, tb = it0 - ti * A.n_tb, prev = -1;
+        for (int64_t it = it0; it < it1; ++it, ++li, tb = (tb + 1 == A.n_tb) ? 0 : tb + 1, ti += (tb == 0)) {
+            if (ti != prev) {
+                prev = ti;
+                kpad = A.tiles[ti].kpad;
             }
             const uint32_t b2 = li & 1u, use = li >> 1;
-            bool ok = wait_bar(BAR(kBarYEmpty + b2), (use & 1u) ^ 1u, abort_flag, A.count);
+            // Y buffer b2 is free once the MMAs of the item two back completed (its accumulator is full)
+            bool ok = wait_bar(BAR(kBarDFull + b2), (use & 1u) ^ 1u, abort_flag, A.count);
             ok = ok && wait_bar(BAR(kBarQFull + b2), use & 1u, abort_flag, A.count);
             if (!__all_sync(0xffffffffu, ok)) break;
             const int rows = kN - 8 + kpad;             // Y rows 0 .. 248 + kpad - 1
@@ -297,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive(BAR(kBarYFull + b2));
+                mbar_arrive(BAR(kBarGo + b2));
                 mbar_arrive(BAR(kBarQEmpty + b2));
             }
         }
@@ -313,12 +348,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
         const int col_off = is_re ? 0 : 16;                  // this warp's 16 columns of each chunk
         const uint32_t tlane = (lq * 32u) << 16;
         uint32_t li = 0;
-        int64_t prev = -1;
         bool valid = false;
         float sc = 0.f, thr_raw = 0.f;
         int32_t j = 0, o = 0;
-        for (int64_t it = it0; it < it1; ++it, ++li) {
-            const int64_t ti = it / A.n_tb, tb = it - ti * A.n_tb;
+        // both accumulators start free: this warp's share of the first phase of each go barrier
+        if (lane == 0) {
+            mbar_arrive(BAR(kBarGo + 0));
+            mbar_arrive(BAR(kBarGo + 1));
+        }
+        int64_t ti = it0 / A.n_tb, tb = it0 - ti * A.n_tb, prev = -1;
+        for (int64_t it = it0; it < it1; ++it, ++li, tb = (tb + 1 == A.n_tb) ? 0 : tb + 1, ti += (tb == 0)) {
             if (ti != prev) {
                 // this lane's template: a = 32 (quarter & 1) + lane, the same in both warps of the pair
                 prev = ti;
@@ -343,9 +382,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                 tmem_ld32(tmem + tlane + acc * (uint32_t)kN + c0, v);
                 tmem_ld_wait();
                 if (cc == 3) {
+                    // the accumulator is free for the item two ahead
                     fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(BAR(kBarDEmpty + acc));
+                    if (lane == 0) mbar_arrive(BAR(kBarGo + acc));
                 }
                 // static register indices only (a runtime index would put v in local memory)
                 float re[16], im[16];
