@@ -155,7 +155,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------- helpers
-def roofline(prec, family, K, options, n, n_ref, secs, exec_flops, peaks, peak_kind):
+def roofline(prec, family, K, options, n, n_ref, secs, exec_flops, peaks, peak_kind, workload=None):
     """Roofline entry of one kernel family over the templates with tap counts K, one launch of
     secs seconds: the FP32 direct FIR or the block-FFT kernel against the derived FP32 ALU peak,
     the tensor-core contraction against the measured sustained bf16 peak."""
@@ -167,7 +167,8 @@ def roofline(prec, family, K, options, n, n_ref, secs, exec_flops, peaks, peak_k
         roof = {"bound": "alu", "achieved": alg / secs / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                 "peak_source": fp32_src}
     elif family == "fft":
-        kernel, src = "k_block_spectra+k_rf_fft", "rf_fft.cu"
+        # k_rf_fft dominates; the time also covers the per-segment k_block_spectra (about 2 %)
+        kernel, src = "k_rf_fft", "rf_fft.cu"
         work = block_fft_flops(K, {"fft_k": 0}, n, n_ref)
         roof = {"bound": "alu", "achieved": work / secs / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                 "peak_source": fp32_src,
@@ -190,7 +191,7 @@ def roofline(prec, family, K, options, n, n_ref, secs, exec_flops, peaks, peak_k
                 "executed_tflops": exec_flops / secs / 1e12,
                 "executed_frac": exec_flops / secs / 1e12 / peak_tf}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = recorded_traffic(kernel, src)
+    roof["traffic"] = recorded_traffic(kernel, src, workload)
     roof["kernel"] = kernel
     roof["kernel_ms"] = secs * 1e3
     roof["algorithmic_flops_per_launch"] = alg
@@ -232,13 +233,14 @@ def kernel_source_hash(name):
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def recorded_traffic(kernel, source):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+def recorded_traffic(kernel, source, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source and
+    this workload."""
     if not os.path.exists(PROFILE_TRAFFIC):
         return None
     with open(PROFILE_TRAFFIC) as fh:
         rec = json.load(fh).get(kernel)
-    if not rec or rec.get("source_sha") != kernel_source_hash(source):
+    if not rec or rec.get("source_sha") != kernel_source_hash(source) or rec.get("workload") != workload:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -785,7 +787,7 @@ def run_ours(args):
     if parts:
         dom = max(parts, key=lambda q: q["ms"])
         roof = roofline(prec, dom["family"], s.K[dom["idx"]], s.options, s.out_len, bank.n_ref, dom["ms"] / 1e3,
-                        dom["executed_flops"], peaks, peak_kind)
+                        dom["executed_flops"], peaks, peak_kind, None)
         for q in parts:
             q["frac"] = roofline(prec, q["family"], s.K[q["idx"]], s.options, s.out_len, bank.n_ref, q["ms"] / 1e3,
                                  q["executed_flops"], peaks, peak_kind)["frac"]
@@ -793,7 +795,8 @@ def run_ours(args):
     else:
         family = "fft" if fft_templates(s.K, s.options) == len(s.K) and prec != 0 else "direct"
         roof = roofline(prec, family, s.K, s.options, s.out_len, bank.n_ref, filt_s,
-                        s.plan.executed_flops() if prec != 0 else 0.0, peaks, peak_kind)
+                        s.plan.executed_flops() if prec != 0 else 0.0, peaks, peak_kind,
+                        cfg.name if s.out_len == cfg.n else None)
 
     chisq_rep = None
     if args.chisq and prec != 0:
