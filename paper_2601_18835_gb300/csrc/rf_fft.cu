@@ -25,8 +25,10 @@ namespace {
 
 constexpr int kM = 2048;                     // block transform length
 constexpr int kGT = 128;                     // threads per block transform, 16 elements each
-constexpr int kGroups = 4;                   // block transforms per CTA
+constexpr int kGroups = 4;                   // block transforms per CTA of the spectra kernel
 constexpr int kThreads = kGT * kGroups;
+constexpr int kFGroups = 3;                  // block transforms per CTA of the filter kernel
+constexpr int kFThreads = kGT * kFGroups;    // (384 threads: room for both twiddle rows in registers)
 constexpr int kTileLd = kM + kM / 16 + 2;    // padded shared-memory tile (one pad per 16)
 constexpr int kTileTemplates = 64;           // templates per tile (one reference)
 
@@ -38,8 +40,8 @@ __device__ __forceinline__ void group_bar(int id) {
 
 // Length-2048 transform by one 128-thread group: thread t holds elements t + 128 r (r < 16) in
 // v on entry and on exit (natural order).  Passes: radix 8 (ns = 1) into tile A, radix 16
-// (ns = 8) from A into B, radix 16 (ns = 128) from B into registers.  tw: the twiddles of the
-// last two passes as built by build_twiddles (in shared memory).  Every thread of the group calls this; bar is the
+// (ns = 8) from A into B, radix 16 (ns = 128) from B into registers.  w2, w3: this thread's
+// twiddles of the last two passes (load_twiddles), held in registers across transforms.  Every thread of the group calls this; bar is the
 // group's named barrier.  Two calls in a row are safe: a thread writes A again only after
 // every thread of the group passed the barrier that follows its reads of A, and likewise B.
 // Thread-major, XOR-swizzled rows of 16 complex values: value r of row i is float2 index
@@ -71,8 +73,8 @@ __device__ __forceinline__ void build_twiddles(float2 *tw, const float2 *__restr
 }
 
 template <bool INV>
-__device__ __forceinline__ void group_fft(float2 (&v)[16], float2 *A, float2 *B, const float2 *tw, int t,
-                                          int bar) {
+__device__ __forceinline__ void group_fft(float2 (&v)[16], float2 *A, float2 *B, const float2 (&w2)[16],
+                                          const float2 (&w3)[16], int t, int bar) {
     {
         float2 a[8], b[8];
 #pragma unroll
@@ -91,27 +93,27 @@ __device__ __forceinline__ void group_fft(float2 (&v)[16], float2 *A, float2 *B,
     group_bar(bar);
     {
         const int k = t & 7;
-        float2 a[16], w[16];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) a[r] = A[tpos(t + kGT * r)];
-        load_row16(w, tw, k);
+        for (int r = 0; r < 16; ++r) v[r] = A[tpos(t + kGT * r)];
 #pragma unroll
-        for (int r = 1; r < 16; ++r) a[r] = INV ? cmul(a[r], w[r]) : cmulc(a[r], w[r]);
-        dft_reg<float, 16, INV>(a);
+        for (int r = 1; r < 16; ++r) v[r] = INV ? cmul(v[r], w2[r]) : cmulc(v[r], w2[r]);
+        dft_reg<float, 16, INV>(v);
         const int idx = ((t - k) << 4) + k;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) B[tpos(idx + 8 * r)] = a[r];
+        for (int r = 0; r < 16; ++r) B[tpos(idx + 8 * r)] = v[r];
     }
     group_bar(bar);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = B[tpos(t + kGT * r)];
-    {
-        float2 w[16];
-        load_row16(w, tw, 8 + t);
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = INV ? cmul(v[r], w[r]) : cmulc(v[r], w[r]);
-    }
+    for (int r = 1; r < 16; ++r) v[r] = INV ? cmul(v[r], w3[r]) : cmulc(v[r], w3[r]);
     dft_reg<float, 16, INV>(v);
+}
+
+// Thread t's twiddle rows: pass 2 (row t mod 8) and pass 3 (row 8 + t) of the table.
+__device__ __forceinline__ void load_twiddles(float2 (&w2)[16], float2 (&w3)[16], const float2 *tw, int t) {
+    load_row16(w2, tw, t & 7);
+    load_row16(w3, tw, 8 + t);
 }
 
 __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
@@ -119,10 +121,10 @@ __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
 }
 
-// One template's P (16 KB) into shared memory: 1024 copies of 16 B, two per thread.
+// One template's P (16 KB) into shared memory: 1024 copies of 16 B spread over the filter CTA.
 __device__ __forceinline__ void stage_p(float2 *dst, const float2 *__restrict__ src) {
 #pragma unroll
-    for (int c = threadIdx.x; c < kM / 2; c += kThreads) cp_async16(dst + 2 * c, src + 2 * c);
+    for (int c = threadIdx.x; c < kM / 2; c += kFThreads) cp_async16(dst + 2 * c, src + 2 * c);
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
@@ -166,7 +168,9 @@ __global__ void __launch_bounds__(kThreads) k_block_spectra(const void *__restri
     float2 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = load_q<PREC>(q, r, ld, (u0 + t + kGT * i) & (n - 1), sc);
-    group_fft<false>(v, TA, TB, tw, t, 1 + g);
+    float2 w2[16], w3[16];
+    load_twiddles(w2, w3, tw, t);
+    group_fft<false>(v, TA, TB, w2, w3, t, 1 + g);
     if (bvalid) {
         float2 *dst = X + ((int64_t)r * nb + b) * kM;
 #pragma unroll
@@ -192,21 +196,24 @@ struct RfFftArgs {
     unsigned long long *count;
 };
 
-__global__ void __launch_bounds__(kThreads, 1) k_rf_fft(const RfFftArgs a) {
+__global__ void __launch_bounds__(kFThreads, 1) k_rf_fft(const RfFftArgs a) {
     extern __shared__ __align__(16) uint8_t sm[];
     float2 *tw = (float2 *)sm;                  // [kTwRows][16] swizzled twiddle rows
     float2 *Ps = tw + kTwRows * 16;             // [2][kM] template spectra, double-buffered
-    float2 *tl = Ps + 2 * kM;                   // [kGroups][2][kTileLd]
+    float2 *tl = Ps + 2 * kM;                   // [kFGroups][2][kTileLd]
     const int g = threadIdx.x / kGT, t = threadIdx.x % kGT;
     float2 *TA = tl + (2 * g) * kTileLd, *TB = TA + kTileLd;
     build_twiddles(tw, a.stw);
+    __syncthreads();
+    float2 w2[16], w3[16];
+    load_twiddles(w2, w3, tw, t);
     const int64_t it0 = a.ranges[blockIdx.x], it1 = a.ranges[blockIdx.x + 1];
     const int64_t ubase = window_base(a.u_begin, a.n);
     for (int64_t it = it0; it < it1; ++it) {
         const int64_t ti = it / a.nbg;
         const int bg = (int)(it - ti * a.nbg);
         const FftTile tile = a.tiles[ti];
-        const int b = bg * kGroups + g;
+        const int b = bg * kFGroups + g;
         const bool bvalid = b < a.nb;
         const int64_t u0 = ubase + (int64_t)b * a.L;
         // outputs l of this block inside the window: l < lim
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_fft(const RfFftArgs a) {
             load_row16(v, Ps + (q & 1) * kM, t);
 #pragma unroll
             for (int r = 0; r < 16; ++r) v[r] = cmul(x[r], v[r]);
-            group_fft<true>(v, TA, TB, tw, t, 1 + g);
+            group_fft<true>(v, TA, TB, w2, w3, t, 1 + g);
             // epilogue: v[r] = z at u = u0 + t + 128 r
             // screen on the largest |z|^2 of the thread (invalid outputs included: a false
             // alarm only costs the exact pass below, which drops them)
@@ -283,7 +290,9 @@ __global__ void __launch_bounds__(kGT) k_taps_spectra(const float2 *__restrict__
             v[r] = make_float2(0.f, 0.f);
         }
     }
-    group_fft<true>(v, tiles, tiles + kTileLd, tw, t, 1);
+    float2 w2[16], w3[16];
+    load_twiddles(w2, w3, tw, t);
+    group_fft<true>(v, tiles, tiles + kTileLd, w2, w3, t, 1);
     float2 *dst = P + local * kM;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
@@ -292,14 +301,14 @@ __global__ void __launch_bounds__(kGT) k_taps_spectra(const float2 *__restrict__
 }
 
 constexpr size_t kSmemSpectra = (size_t)(kTwRows * 16 + 2 * kGroups * kTileLd) * sizeof(float2);
-constexpr size_t kSmemFilter = (size_t)(kTwRows * 16 + 2 * kM + 2 * kGroups * kTileLd) * sizeof(float2);
+constexpr size_t kSmemFilter = (size_t)(kTwRows * 16 + 2 * kM + 2 * kFGroups * kTileLd) * sizeof(float2);
 constexpr size_t kSmemTaps = (size_t)(kTwRows * 16 + 2 * kTileLd) * sizeof(float2);
 
 }  // namespace
 
 int fft_fir_block_len() { return kM; }
 int fft_fir_tile_templates() { return kTileTemplates; }
-int fft_fir_blocks_per_cta() { return kGroups; }
+int fft_fir_blocks_per_cta() { return kFGroups; }
 
 rfd_status fft_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const int32_t *lag, const double *sigma,
                     cudaStream_t s) {
@@ -334,7 +343,7 @@ rfd_status fft_launch(const rfd_plan *plan, const void *q, const int32_t *qscale
         RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFilter));
         attr_set = true;
     }
-    const dim3 gs((unsigned)plan->fft_nbg, (unsigned)plan->fft_refs.size());
+    const dim3 gs((unsigned)((plan->fft_nb + kGroups - 1) / kGroups), (unsigned)plan->fft_refs.size());
     const int32_t *refs = (const int32_t *)plan->d_fft_refs.p;
     float2 *X = (float2 *)plan->d_fft_X.p;
     if (plan->precision == RFD_PREC_FP32)
@@ -370,7 +379,7 @@ rfd_status fft_launch(const rfd_plan *plan, const void *q, const int32_t *qscale
     a.cand = cand;
     a.cap = cap;
     a.count = (unsigned long long *)count;
-    k_rf_fft<<<(unsigned)plan->fft_grid, kThreads, kSmemFilter, s>>>(a);
+    k_rf_fft<<<(unsigned)plan->fft_grid, kFThreads, kSmemFilter, s>>>(a);
     RFD_LAUNCH_CHECK();
     return RFD_OK;
 }
