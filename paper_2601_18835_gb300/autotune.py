@@ -29,6 +29,7 @@ DEFAULT_CANDIDATES = [
     {"mix_k": 1, "fft_k": 256},
     {"mix_k": 1, "fft_k": 128},
     {"mix_k": 1, "fft_k": 0},
+    {"mix_k": 1, "fft_k": 128, "long_k": 0},
 ]
 
 
