@@ -395,14 +395,16 @@ rfd_status fft_c2c(rfd_ctx *ctx, int64_t n, int64_t batch, const typename Cplx<T
         RFD_TRY(get_stage_twiddles<T>(ctx, logN1, &stA, s));
         RFD_TRY(get_stage_twiddles<T>(ctx, logN2, &stB, s));
         RFD_TRY(get_twiddles<T>(ctx, n >> sh, &hi, s));
-        static bool attr_set = false;                           // one per T
-        if (!attr_set) {
+        // set once per device and T, so that calls inside a stream capture make no other runtime call
+        static bool attr_set[64] = {};
+        const int dev = ctx->device < 64 ? ctx->device : 63;
+        if (!attr_set[dev]) {
             const int mx = 200 * 1024;
             RFD_TRY_CUDA(cudaFuncSetAttribute(k_fft_cols<T, EPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
             RFD_TRY_CUDA(cudaFuncSetAttribute(k_fft_rows<T, EPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
             RFD_TRY_CUDA(cudaFuncSetAttribute(k_fft_cols<T, EPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
             RFD_TRY_CUDA(cudaFuncSetAttribute(k_fft_rows<T, EPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-            attr_set = true;
+            attr_set[dev] = true;
         }
         // the whole batch in one launch per pass (chunking the batch so that the intermediate
         // stays in L2 measured slower: the short grids lose more to wave tails)

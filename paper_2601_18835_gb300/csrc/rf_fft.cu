@@ -313,10 +313,11 @@ int fft_fir_blocks_per_cta() { return kFGroups; }
 rfd_status fft_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const int32_t *lag, const double *sigma,
                     cudaStream_t s) {
     if (plan->fft_nslots == 0) return RFD_OK;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static bool attr_set[64] = {};                      // once per device
+    const int dev = plan->ctx->device < 64 ? plan->ctx->device : 63;
+    if (!attr_set[dev]) {
         RFD_TRY_CUDA(cudaFuncSetAttribute(k_taps_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTaps));
-        attr_set = true;
+        attr_set[dev] = true;
     }
     for (int64_t s0 = 0; s0 < plan->fft_nslots; s0 += 65535) {
         const unsigned nblk = (unsigned)std::min<int64_t>(65535, plan->fft_nslots - s0);
@@ -332,8 +333,9 @@ rfd_status fft_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const 
 rfd_status fft_launch(const rfd_plan *plan, const void *q, const int32_t *qscale, const int64_t *u_begin,
                       rfd_candidate *cand, int64_t cap, int64_t *count, cudaStream_t s) {
     if (plan->fft_tiles.empty()) return RFD_OK;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static bool attr_set[64] = {};                      // once per device (none inside a capture)
+    const int dev = plan->ctx->device < 64 ? plan->ctx->device : 63;
+    if (!attr_set[dev]) {
         RFD_TRY_CUDA(cudaFuncSetAttribute(k_block_spectra<RFD_PREC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)kSmemSpectra));
         RFD_TRY_CUDA(cudaFuncSetAttribute(k_block_spectra<RFD_PREC_FP16X3>,
@@ -341,7 +343,7 @@ rfd_status fft_launch(const rfd_plan *plan, const void *q, const int32_t *qscale
         RFD_TRY_CUDA(cudaFuncSetAttribute(k_block_spectra<RFD_PREC_BF16X3>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSpectra));
         RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemFilter));
-        attr_set = true;
+        attr_set[dev] = true;
     }
     const dim3 gs((unsigned)((plan->fft_nb + kGroups - 1) / kGroups), (unsigned)plan->fft_refs.size());
     const int32_t *refs = (const int32_t *)plan->d_fft_refs.p;
