@@ -11,13 +11,16 @@
 //   z_j[(u_0 + l + off_j) mod n] = sum_k X_b[k] P_j[k] exp(+2 pi i k l / M),
 //   X_b[k] = sum_i x_b[i] exp(-2 pi i k i / M)      (per reference and block, every segment),
 //   P_j[k] = (1/M) sum_m c_j[m] exp(+2 pi i k m / M) (per template, when the taps are set).
-// A CTA holds four 128-thread groups, one block b each.  The templates of a tile stream
-// through shared memory (the next template's P_j copied with cp.async while the current one
-// is transformed); every group multiplies its X_b, kept in registers, by P_j, runs the inverse
-// transform (Stockham passes of radix 8, 16, 16 through two padded tiles) and screens |z|^2.
+// A CTA holds three 128-thread groups, one block b each.  The templates of a tile stream
+// through a two-buffer ring in shared memory (bulk copies completing on mbarriers; a buffer is
+// refilled once every group has released it, so the groups never wait for one another as a
+// whole); every group multiplies its X_b, kept in registers, by P_j, runs the inverse
+// transform (Stockham passes of radix 8, 16, 16 through two padded tiles, twiddles in
+// registers) and screens |z|^2.
 #include "epilogue.cuh"
 #include "fft_reg.cuh"
 #include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace rfd {
 
@@ -33,6 +36,7 @@ constexpr int kTileLd = kM + kM / 16 + 2;    // padded shared-memory tile (one p
 constexpr int kTileTemplates = 64;           // templates per tile (one reference)
 
 __device__ __forceinline__ int tpos(int i) { return i + (i >> 4); }
+
 
 __device__ __forceinline__ void group_bar(int id) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kGT) : "memory");
@@ -116,18 +120,6 @@ __device__ __forceinline__ void load_twiddles(float2 (&w2)[16], float2 (&w3)[16]
     load_row16(w3, tw, 8 + t);
 }
 
-__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
-    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
-}
-
-// One template's P (16 KB) into shared memory: 1024 copies of 16 B spread over the filter CTA.
-__device__ __forceinline__ void stage_p(float2 *dst, const float2 *__restrict__ src) {
-#pragma unroll
-    for (int c = threadIdx.x; c < kM / 2; c += kFThreads) cp_async16(dst + 2 * c, src + 2 * c);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
 // q_r[m] as FP32 from the stored reference series (complex64, or the four hi/lo planes of
 // the split precisions with hi + lo = q 2^e_r).
 template <int PREC>
@@ -196,19 +188,46 @@ struct RfFftArgs {
     unsigned long long *count;
 };
 
+constexpr uint32_t kFSpin = 1u << 22;
+
+// Bounded wait on an mbarrier phase.  A wait that gives up raises the CTA's abort flag and
+// bit 62 of the candidate count (reported as RFD_ERR_TIMEOUT by find_triggers); every later
+// wait then returns at once, so every thread keeps the same control flow (the group barriers
+// stay matched) and the kernel ends.
+__device__ __forceinline__ void ring_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag,
+                                          unsigned long long *count) {
+    for (uint32_t i = 0; i < kFSpin; ++i) {
+        if (tc::mbar_try_wait(bar, parity) || *abort_flag) return;
+    }
+    *abort_flag = 1u;
+    atomicOr(count, 1ull << 62);
+}
+
 __global__ void __launch_bounds__(kFThreads, 1) k_rf_fft(const RfFftArgs a) {
     extern __shared__ __align__(16) uint8_t sm[];
     float2 *tw = (float2 *)sm;                  // [kTwRows][16] swizzled twiddle rows
-    float2 *Ps = tw + kTwRows * 16;             // [2][kM] template spectra, double-buffered
+    float2 *Ps = tw + kTwRows * 16;             // [2][kM] template spectra ring
     float2 *tl = Ps + 2 * kM;                   // [kFGroups][2][kTileLd]
+    uint64_t *bars = (uint64_t *)(tl + 2 * kFGroups * kTileLd);   // full[2], empty[2]
+    volatile uint32_t *abort_flag = (volatile uint32_t *)(bars + 4);
     const int g = threadIdx.x / kGT, t = threadIdx.x % kGT;
     float2 *TA = tl + (2 * g) * kTileLd, *TB = TA + kTileLd;
+    const uint32_t full0 = tc::smem_u32(bars), empty0 = full0 + 16u;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(full0, 1);
+        tc::mbar_init(full0 + 8u, 1);
+        tc::mbar_init(empty0, kFGroups);
+        tc::mbar_init(empty0 + 8u, kFGroups);
+        *abort_flag = 0u;
+        tc::mbar_fence_init();
+    }
     build_twiddles(tw, a.stw);
     __syncthreads();
     float2 w2[16], w3[16];
     load_twiddles(w2, w3, tw, t);
     const int64_t it0 = a.ranges[blockIdx.x], it1 = a.ranges[blockIdx.x + 1];
     const int64_t ubase = window_base(a.u_begin, a.n);
+    uint32_t tq = 0;                            // templates this CTA has started (ring position)
     for (int64_t it = it0; it < it1; ++it) {
         const int64_t ti = it / a.nbg;
         const int bg = (int)(it - ti * a.nbg);
@@ -223,18 +242,32 @@ __global__ void __launch_bounds__(kFThreads, 1) k_rf_fft(const RfFftArgs a) {
         float2 x[16];
 #pragma unroll
         for (int r = 0; r < 16; ++r) x[r] = Xb[t + kGT * r];
-        __syncthreads();                        // every reader of Ps in the previous item is done
         const float2 *Pt = a.P + (tile.first - a.slot0) * kM;
-        stage_p(Ps, Pt);
-        for (int q = 0; q < tile.count; ++q) {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            __syncthreads();                    // P_q visible to all; buffer (q + 1) & 1 free
-            if (q + 1 < tile.count) stage_p(Ps + ((q + 1) & 1) * kM, Pt + (int64_t)(q + 1) * kM);
+        for (int q = 0; q < tile.count; ++q, ++tq) {
+            // template spectra stream through a ring of two buffers (template tq in buffer
+            // tq & 1): thread 0 copies the item's first template, and each next one, once
+            // every group has released the buffer's previous template; the groups do not
+            // wait for one another
+            if (threadIdx.x == 0) {
+                for (int k = (q == 0 ? 0 : 1); k < 2; ++k) {
+                    const uint32_t t2 = tq + (uint32_t)k;
+                    if (q + k >= tile.count) break;
+                    const uint32_t b2 = t2 & 1u;
+                    ring_wait(empty0 + 8u * b2, ((t2 >> 1) & 1u) ^ 1u, abort_flag, a.count);
+                    tc::mbar_arrive_expect_tx(full0 + 8u * b2, (uint32_t)(kM * sizeof(float2)));
+                    tc::bulk_g2s(tc::smem_u32(Ps + b2 * kM), Pt + (int64_t)(q + k) * kM,
+                                 (uint32_t)(kM * sizeof(float2)), full0 + 8u * b2);
+                }
+            }
+            const uint32_t bq = tq & 1u;
+            ring_wait(full0 + 8u * bq, (tq >> 1) & 1u, abort_flag, a.count);
             float2 v[16];
-            load_row16(v, Ps + (q & 1) * kM, t);
+            load_row16(v, Ps + bq * kM, t);
 #pragma unroll
             for (int r = 0; r < 16; ++r) v[r] = cmul(x[r], v[r]);
             group_fft<true>(v, TA, TB, w2, w3, t, 1 + g);
+            // the group's reads of the buffer precede its first barrier inside group_fft
+            if (t == 0) tc::mbar_arrive(empty0 + 8u * bq);
             // epilogue: v[r] = z at u = u0 + t + 128 r
             // screen on the largest |z|^2 of the thread (invalid outputs included: a false
             // alarm only costs the exact pass below, which drops them)
@@ -301,7 +334,7 @@ __global__ void __launch_bounds__(kGT) k_taps_spectra(const float2 *__restrict__
 }
 
 constexpr size_t kSmemSpectra = (size_t)(kTwRows * 16 + 2 * kGroups * kTileLd) * sizeof(float2);
-constexpr size_t kSmemFilter = (size_t)(kTwRows * 16 + 2 * kM + 2 * kFGroups * kTileLd) * sizeof(float2);
+constexpr size_t kSmemFilter = (size_t)(kTwRows * 16 + 2 * kM + 2 * kFGroups * kTileLd) * sizeof(float2) + 64;
 constexpr size_t kSmemTaps = (size_t)(kTwRows * 16 + 2 * kTileLd) * sizeof(float2);
 
 }  // namespace
