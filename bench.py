@@ -263,14 +263,29 @@ def workload_for_rank(c, rank, n_tmpl=None, n_ref=None):
 
 
 # ------------------------------------------------------------------------------- oracle arm
+def oracle_k(cfg, bank, j):
+    """Taps of template j as the bench's GPU set-up chooses them: the configured K, or for a
+    bucketed bank the smallest bucket holding 0.999 of the impulse response's energy (the
+    oracle's own rule)."""
+    if cfg.k:
+        return int(cfg.k)
+    from oracle import ratio
+    r = int(bank.ref_of_tmpl[j])
+    G = ratio.ratio_spectrum(cfg.fs, cfg.n, cfg.f_low, bank.params()[j], bank.ref_params()[r], cfg.pn_flags)
+    return int(ratio.k_bucket(ratio.impulse_response(G), list(cfg.k_buckets), 0.999))
+
+
 def oracle_sample(cfg, bank, data, n_templates):
     """Set-up for timing the FP64 oracle: one reference series and the taps of the first
-    n_templates templates assigned to it (untimed)."""
+    n_templates templates assigned to it (untimed), each with its own K."""
     from tests.oracle_pipeline import OracleRun
     ora = OracleRun(cfg, bank, data)
     r = int(bank.ref_of_tmpl[0])
-    js = [int(j) for j in np.nonzero(bank.ref_of_tmpl == r)[0][:n_templates]]
-    designs = [ora.design(j, cfg.k, with_match=False) for j in js]
+    cands = np.nonzero(bank.ref_of_tmpl == r)[0]
+    # a seeded draw from the reference's templates, so that a bucketed bank's K mix shows
+    js = sorted(int(j) for j in np.random.default_rng(0).choice(cands, size=min(n_templates, len(cands)),
+                                                                replace=False))
+    designs = [ora.design(j, oracle_k(cfg, bank, j), with_match=False) for j in js]
     return ora, js, designs
 
 
@@ -307,8 +322,9 @@ def run_reference(args):
                    "fs": cfg.fs},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "each step: one template of the bank through the FP64 oracle's direct "
-                                   "circular FIR (K=%d, n=%d) and window-max triggers, reference series and "
-                                   "taps precomputed (set-up %.1f s)" % (cfg.k, cfg.n, t_setup)},
+                                   "circular FIR (K=%s, n=%d) and window-max triggers, reference series and "
+                                   "taps precomputed (set-up %.1f s)" % (
+                                       sorted(len(d["taps"]) for d in designs), cfg.n, t_setup)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -859,8 +875,9 @@ def run_ours(args):
         el = time.perf_counter() - t0
         cpu = {"value": done * dur / el, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "one reference's FP64 matched filter plus %d template passes (8 distinct templates) "
-                         "through the oracle's direct circular FIR (K=%d, n=%d) and triggers, taps "
-                         "precomputed: %.1f s of one host core" % (done, cfg.k, cfg.n, el)}
+                         "through the oracle's direct circular FIR (K=%s, n=%d) and triggers, taps "
+                         "precomputed: %.1f s of one host core" % (done, sorted(len(d["taps"]) for d in designs),
+                                                                   cfg.n, el)}
 
     match = s.match.cpu().numpy() if s.match is not None else None
     line = {
