@@ -173,3 +173,49 @@ def test_energy_span_and_bucket():
     g[0:4] = 1.0
     assert ratio.energy_span(g, 1.0) == 10
     assert ratio.k_bucket(g, (4, 8, 16, 32), 1.0) == 16
+
+
+@pytest.mark.parametrize("K,n,s", [(64, 16384, -37), (512, 16384, 211), (3, 4096, 0), (200, 1024, -5)])
+def test_overlap_save_blocks_reproduce_the_circular_fir(rng, K, n, s):
+    """Reading of the block-FFT realisation (Table II's form): with off = (s + K - 1) mod n,
+    c[m] = rho[K-1-m], blocks of L = M - K + 1 outputs (M = 2048) starting at u0 = b L and
+    x_b[i] = q[(u0 + i) mod n], the unnormalised inverse DFT of X_b P (P = IDFT_M(c) / M)
+    gives qhat[(u0 + l + off) mod n] for l < L: every output of the direct circular FIR of
+    Eq. 3, exactly once, including blocks that run past the end of the segment (and M > n)."""
+    M = 2048
+    q = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    rho = rng.standard_normal(K) + 1j * rng.standard_normal(K)
+    direct = ratio.ratio_fir(q, rho, s)
+    off = (s + K - 1) % n
+    c = np.zeros(M, dtype=np.complex128)
+    c[:K] = rho[::-1]
+    P = np.fft.ifft(c)                       # (1/M) sum_m c[m] e^{+2 pi i k m / M}
+    L = M - K + 1
+    got = np.full(n, np.nan + 0j)
+    for b in range(-(-n // L)):
+        u0 = b * L
+        x = q[(u0 + np.arange(M)) % n]
+        y = np.fft.ifft(np.fft.fft(x) * P) * M
+        l = np.arange(min(L, n - u0))
+        got[(u0 + l + off) % n] = y[l]
+    assert not np.isnan(got).any()
+    assert np.max(np.abs(got - direct)) <= 1e-11 * np.max(np.abs(direct))
+
+
+def test_streaming_windows_tile_the_series(rng):
+    """Reading of the streaming form (Sec. VII.A): the outputs u of windows [w0, w0 + B), taken
+    with their true times (u + off) mod n, cover the direct circular FIR exactly once."""
+    n, K, s, B = 8192, 64, 17, 2048
+    q = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    rho = rng.standard_normal(K) + 1j * rng.standard_normal(K)
+    direct = ratio.ratio_fir(q, rho, s)
+    off = (s + K - 1) % n
+    seen = np.zeros(n, dtype=int)
+    for w0 in range(0, n, B):
+        u = np.arange(w0, w0 + B)
+        t = (u + off) % n
+        seen[t] += 1
+        # the window needs q[u .. u + K - 1] only (the K-sample halo)
+        win = np.array([np.sum(rho[::-1] * q[(uu + np.arange(K)) % n]) for uu in u[:8]])
+        assert np.allclose(win, direct[t[:8]], rtol=1e-12, atol=1e-12)
+    assert np.all(seen == 1)
