@@ -39,7 +39,7 @@ typedef enum {
     RFD_OK = 0,
     RFD_ERR_ARG = -1,          /* null pointer, bad enum, non-finite parameter */
     RFD_ERR_SHAPE = -2,        /* sizes inconsistent or out of the supported range */
-    RFD_ERR_UNSUPPORTED = -3,  /* valid request this build does not implement */
+    RFD_ERR_UNSUPPORTED = -3,  /* a valid request the library does not implement */
     RFD_ERR_CUDA = -4,         /* a CUDA runtime call failed (message has the CUDA error) */
     RFD_ERR_NOMEM = -5,        /* workspace allocation failed */
     RFD_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
