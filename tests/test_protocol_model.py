@@ -1,0 +1,163 @@
+"""Models of the two hand-off protocols the persistent kernels rely on, run under random
+interleavings of their parties (mbarrier semantics: a phase completes after `count` arrivals;
+a wait with parity p returns once a phase of parity p has completed, i.e. when
+completed_phases mod 2 != p).
+
+* rf_tc_long.cu: the producer (q window, taps chunks; chunk 0 completes on the item's go
+  barrier), the Y builders (released by the accumulator-full commit of the item two back), the
+  epilogue (frees the accumulator for the item two ahead; pre-arrives once per buffer) and the
+  MMA issuer (one go wait per item, waited before the last k-step of the previous item; taps
+  stage waits for later chunks; stage release per chunk).  Checked: every go phase completes
+  with the arrivals of exactly one item, the MMA reads the chunk it expects, no copy lands on a
+  stage in use, no deadlock.
+* rf_fft.cu: the two-buffer ring of template spectra: thread 0 copies template t + 1 once all
+  groups released template t - 1; groups wait for their template's buffer and release it.
+  Checked: every group reads the spectrum it expects, no copy lands on a buffer in use, no
+  deadlock.
+"""
+import random
+
+import pytest
+
+
+class Bar:
+    def __init__(self, count):
+        self.count, self.arr, self.done, self.log = count, [], 0, []
+
+    def arrive(self, tag=None):
+        self.arr.append(tag)
+        if len(self.arr) == self.count:
+            self.log.append(self.arr)
+            self.arr, self.done = [], self.done + 1
+
+    def ok(self, parity):
+        return (self.done & 1) != parity
+
+
+def _schedule(procs, rnd, limit=200000):
+    alive = [True] * len(procs)
+    steps = 0
+    while any(alive):
+        steps += 1
+        assert steps < limit, "deadlock"
+        k = rnd.choice([i for i in range(len(procs)) if alive[i]])
+        try:
+            next(procs[k])
+        except StopIteration:
+            alive[k] = False
+
+
+def _long_kernel(tiles_nch, n_tb, rnd):
+    items = [(ti, tb) for ti in range(len(tiles_nch)) for tb in range(n_tb)]
+    a = rnd.randrange(len(items))
+    rng = items[a: rnd.randrange(a, len(items)) + 1]           # one CTA's contiguous range
+    n = len(rng)
+    AF, AE = [Bar(1), Bar(1)], [Bar(1), Bar(1)]
+    GO, DF = [Bar(3), Bar(3)], [Bar(1), Bar(1)]               # go: producer, builders, epilogue
+    stage, inuse = [None, None], [0, 0]
+
+    def producer():
+        ka = 0
+        for li, (ti, tb) in enumerate(rng):
+            for c in range(tiles_nch[ti]):
+                st, r = ka % 2, ka // 2
+                while not AE[st].ok((r & 1) ^ 1):
+                    yield
+                assert inuse[st] == 0, "copy onto a stage in use"
+                stage[st] = (ti, c)
+                (GO[li & 1] if c == 0 else AF[st]).arrive(li)
+                ka += 1
+                yield
+
+    def builders():
+        for li in range(n):
+            while not DF[li & 1].ok(((li >> 1) & 1) ^ 1):
+                yield
+            yield
+            GO[li & 1].arrive(li)
+
+    def epilogue():
+        GO[0].arrive(0)
+        GO[1].arrive(1)
+        for li in range(n):
+            while not DF[li & 1].ok((li >> 1) & 1):
+                yield
+            yield
+            GO[li & 1].arrive(li + 2)
+
+    def mma():
+        ka, uf, go_seen = 0, [0, 0], False
+        for li, (ti, tb) in enumerate(rng):
+            nch = tiles_nch[ti]
+            if not go_seen:
+                while not GO[li & 1].ok((li >> 1) & 1):
+                    yield
+            go_seen = False
+            assert GO[li & 1].log[li >> 1] in ([li] * 3,), ("go phase of mixed items", li)
+            for c in range(nch):
+                st = (ka + c) % 2
+                if c > 0:
+                    u = uf[st]
+                    uf[st] += 1
+                    while not AF[st].ok(u & 1):
+                        yield
+                if c == nch - 1 and li + 1 < n:
+                    while not GO[(li + 1) & 1].ok(((li + 1) >> 1) & 1):
+                        yield
+                    go_seen = True
+                assert stage[st] == (ti, c), "MMA reads the wrong taps chunk"
+                inuse[st] = 1
+                yield
+                inuse[st] = 0
+                AE[st].arrive()
+            ka += nch
+            DF[li & 1].arrive()
+            yield
+
+    _schedule([producer(), builders(), epilogue(), mma()], rnd)
+
+
+def _fft_ring(counts, groups, rnd):
+    full, empty = [Bar(1), Bar(1)], [Bar(groups), Bar(groups)]
+    buf, readers = [None, None], [set(), set()]
+    seq = [(it, q) for it, c in enumerate(counts) for q in range(c)]
+
+    def group(g):
+        tq = 0
+        for it, c in enumerate(counts):
+            for q in range(c):
+                if g == 0:
+                    for k in (0, 1) if q == 0 else (1,):
+                        if q + k >= c:
+                            break
+                        t2 = tq + k
+                        while not empty[t2 & 1].ok(((t2 >> 1) & 1) ^ 1):
+                            yield
+                        assert not readers[t2 & 1], "copy onto a buffer in use"
+                        buf[t2 & 1] = seq[t2]
+                        full[t2 & 1].arrive()
+                b = tq & 1
+                while not full[b].ok((tq >> 1) & 1):
+                    yield
+                assert buf[b] == seq[tq], "group reads the wrong spectrum"
+                readers[b].add(g)
+                yield
+                readers[b].discard(g)
+                empty[b].arrive()
+                tq += 1
+                yield
+
+    _schedule([group(g) for g in range(groups)], rnd)
+
+
+@pytest.mark.parametrize("seed", range(0, 600, 3))
+def test_long_kernel_handoffs(seed):
+    rnd = random.Random(seed)
+    tiles = [rnd.choice([1, 2, 2, 2, 3, 4]) for _ in range(rnd.randrange(1, 5))]
+    _long_kernel(tiles, rnd.randrange(1, 12), rnd)
+
+
+@pytest.mark.parametrize("seed", range(0, 600, 3))
+def test_block_fft_spectrum_ring(seed):
+    rnd = random.Random(seed)
+    _fft_ring([rnd.randrange(1, 6) for _ in range(rnd.randrange(1, 6))], 3, rnd)
