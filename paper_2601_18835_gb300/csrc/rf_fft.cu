@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_rf_fft(const RfFftArgs a) {
     const int64_t it0 = a.ranges[blockIdx.x], it1 = a.ranges[blockIdx.x + 1];
     const int64_t ubase = window_base(a.u_begin, a.n);
     uint32_t tq = 0;                            // templates this CTA has started (ring position)
+    uint32_t last0 = 0xffffffffu, last1 = 0xffffffffu;   // thread 0: last template copied per buffer
     for (int64_t it = it0; it < it1; ++it) {
         const int64_t ti = it / a.nbg;
         const int bg = (int)(it - ti * a.nbg);
@@ -257,6 +258,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_rf_fft(const RfFftArgs a) {
                     tc::mbar_arrive_expect_tx(full0 + 8u * b2, (uint32_t)(kM * sizeof(float2)));
                     tc::bulk_g2s(tc::smem_u32(Ps + b2 * kM), Pt + (int64_t)(q + k) * kM,
                                  (uint32_t)(kM * sizeof(float2)), full0 + 8u * b2);
+                    if (b2 == 0u)
+                        last0 = t2;
+                    else
+                        last1 = t2;
                 }
             }
             const uint32_t bq = tq & 1u;
@@ -287,6 +292,16 @@ __global__ void __launch_bounds__(kFThreads, 1) k_rf_fft(const RfFftArgs a) {
                     emit_window_max(valid, (uint32_t)j, tt, v[r].x, v[r].y, a.thr, a.W, a.cand, a.cap, a.count);
                 }
             }
+        }
+    }
+    // no copy may still be landing when the CTA ends (after a wait that gave up, the groups no
+    // longer consume them): thread 0 waits, bounded, for the last copy into each buffer; in
+    // normal operation these phases completed long ago
+    if (threadIdx.x == 0) {
+        for (uint32_t i = 0; i < kFSpin && last0 != 0xffffffffu && !tc::mbar_try_wait(full0, (last0 >> 1) & 1u); ++i) {
+        }
+        for (uint32_t i = 0; i < kFSpin && last1 != 0xffffffffu &&
+                             !tc::mbar_try_wait(full0 + 8u, (last1 >> 1) & 1u); ++i) {
         }
     }
 }
