@@ -350,11 +350,14 @@ void rfd_search_destroy(rfd_search *search);
  * callers whose device memory is owned by another allocator or memory pool, and callers that
  * hold no librfd context.  The paper has no counterpart; this is a deployment variant.
  *
- * It allocates nothing.  Its scratch is one fixed array of static device memory (about 4 MB,
+ * It allocates nothing.  Its scratch is one fixed array of static device memory (4.0 MiB,
  * sized for RFD_NOALLOC_MAX_TEMPLATES templates and RFD_NOALLOC_MAX_CANDIDATES candidates)
- * that every GPU loading librfd holds until the process exits.  It runs on the calling
- * thread's current device.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * that every GPU loading librfd holds until the process exits.  It runs on
+ * the calling thread's current device.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress).  Under CUDA's lazy module loading that lookup is
+ * also what loads librfd's device code on that device and backs the array, which can
+ * synchronise the device: make the first call on each device during set-up, before any
+ * stream capture; later calls only reuse the cached address.
  * n_tmpl > RFD_NOALLOC_MAX_TEMPLATES or cand_capacity > RFD_NOALLOC_MAX_CANDIDATES is
  * rejected with RFD_ERR_SHAPE before anything runs.  Every call on a device shares the one
  * array: each call clears the counters it needs, but calls that overlap on the GPU (other
