@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32-FIR / FINDCHIRP comparison runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--extra-configs", default="3,5",
+                    help="also measure these configs (their own set-up, timed steps, e2e, roofline, oracle check) "
+                         "under 'more_configs' in a plain default run; '' for none")
+    ap.add_argument("--oracle-sample", type=int, default=0,
+                    help="templates in the oracle check (0: 128 for banks up to 8192 templates, else 256)")
     ap.add_argument("--n-tmpl", type=int, default=None, help="smaller bank (profiling cases only)")
     ap.add_argument("--n-ref", type=int, default=None, help="fewer references (profiling cases only)")
     ap.add_argument("--no-graph", action="store_true", help="separate launches instead of one CUDA graph")
@@ -155,10 +160,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------- helpers
-def roofline(prec, family, K, options, n, n_ref, secs, exec_flops, peaks, peak_kind, workload=None):
+def roofline(prec, family, K, options, n, n_ref, secs, exec_flops, peaks, peak_kind, workload=None,
+             sustained=False):
     """Roofline entry of one kernel family over the templates with tap counts K, one launch of
     secs seconds: the FP32 direct FIR or the block-FFT kernel against the derived FP32 ALU peak,
-    the tensor-core contraction against the measured sustained bf16 peak."""
+    the tensor-core contraction against the measured dense bf16 peak (fp16 has the same dense
+    rate): the burst figure when the timed steps add up to under a second, else the sustained
+    one."""
     alg = 8.0 * float(np.asarray(K, dtype=np.float64).sum()) * n
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     fp32_src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
@@ -185,9 +193,11 @@ def roofline(prec, family, K, options, n, n_ref, secs, exec_flops, peaks, peak_k
             kernel, src = "k_rf_tc", "rf_tc.cu"
         else:
             kernel, src = "k_rf_tc_long+k_rf_tc", "rf_tc_long.cu"
-        peak_tf = peaks["bf16_tflops_sustained"]
+        peak_tf = peaks["bf16_tflops_sustained"] if sustained else peaks["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": alg / secs / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
-                "peak_source": "%s bf16 dense sustained (fp16 has the same dense rate)" % peak_kind,
+                "peak_source": "%s bf16 dense %s (fp16 has the same dense rate)" % (
+                    peak_kind, "sustained" if sustained else "burst"),
+                "ceiling_frac_three_products": 1.0 / 3.0 * peaks["bf16_tflops"] / peak_tf,
                 "executed_tflops": exec_flops / secs / 1e12,
                 "executed_frac": exec_flops / secs / 1e12 / peak_tf}
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -263,6 +273,18 @@ def workload_for_rank(c, rank, n_tmpl=None, n_ref=None):
 
 
 # ------------------------------------------------------------------------------- oracle arm
+# Relative |z| error bound of each arithmetic path (the parity tests' bounds): the oracle flags
+# a window ambiguous when an error this large could decide it differently.
+EPS = {0: 2e-6, 1: 2e-5, 2: 2e-4}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def oracle_k(cfg, bank, j):
     """Taps of template j as the bench's GPU set-up chooses them: the configured K, or for a
     bucketed bank the smallest bucket holding 0.999 of the impulse response's energy (the
@@ -275,56 +297,219 @@ def oracle_k(cfg, bank, j):
     return int(ratio.k_bucket(ratio.impulse_response(G), list(cfg.k_buckets), 0.999))
 
 
-def oracle_sample(cfg, bank, data, n_templates):
-    """Set-up for timing the FP64 oracle: one reference series and the taps of the first
-    n_templates templates assigned to it (untimed), each with its own K."""
+def _oracle_worker(conn, c, n_tmpl, n_ref, rank):
+    """One host process of the FP64 oracle (started with spawn): holds the workload and answers
+    requests on its pipe.  'eval' j [K] eps: design (untimed) + Eq. 3 series and triggers (timed);
+    'prep' j: keep template j's design; 'step': one timed pass of the kept template."""
     from tests.oracle_pipeline import OracleRun
-    ora = OracleRun(cfg, bank, data)
-    r = int(bank.ref_of_tmpl[0])
-    cands = np.nonzero(bank.ref_of_tmpl == r)[0]
-    # a seeded draw from the reference's templates, so that a bucketed bank's K mix shows
-    js = sorted(int(j) for j in np.random.default_rng(0).choice(cands, size=min(n_templates, len(cands)),
-                                                                replace=False))
-    designs = [ora.design(j, oracle_k(cfg, bank, j), with_match=False) for j in js]
-    return ora, js, designs
-
-
-def oracle_step(cfg, ora, j, design):
-    """One template through the oracle's ratio path: direct circular FIR (Eq. 3) + triggers."""
     from oracle import triggers
-    z = ora.snr(j, design)
-    return triggers.window_triggers(z, cfg.window, cfg.threshold)
+    cfg, bank, data = workload_for_rank(c, rank, n_tmpl, n_ref)
+    ora = OracleRun(cfg, bank, data)
+    kept = None
+    while True:
+        msg = conn.recv()
+        try:
+            if msg[0] == "stop":
+                break
+            if msg[0] in ("eval", "prep"):
+                j = int(msg[1])
+                K = oracle_k(cfg, bank, j)
+                r = int(bank.ref_of_tmpl[j])
+                if r not in ora._q:
+                    ora._q.clear()                  # one reference series at a time
+                ora._design.clear()
+                d = ora.design(j, K, with_match=False)
+                d = {k: v for k, v in d.items() if k != "g"}
+                if msg[0] == "prep":
+                    kept = (j, d)
+                    conn.send(("ok", K))
+                    continue
+                t0 = time.perf_counter()
+                z = ora.snr(j, d)
+                tr, amb = triggers.window_triggers(z, cfg.window, cfg.threshold, tol=float(msg[2]))
+                el = time.perf_counter() - t0
+                conn.send(("eval", j, K, [(x["w"], x["t"], x["z"].real, x["z"].imag) for x in tr], amb, el,
+                           d["sigma_eff"]))
+            elif msg[0] == "step":
+                j, d = kept
+                t0 = time.perf_counter()
+                z = ora.snr(j, d)
+                triggers.window_triggers(z, cfg.window, cfg.threshold)
+                conn.send(("step", time.perf_counter() - t0))
+        except Exception as ex:                     # reported to the parent, which raises
+            conn.send(("error", repr(ex)))
+
+
+class OracleWorkers:
+    """The FP64 oracle on the host's cores: one spawned process per core, each with the same
+    seeded workload (the oracle is test infrastructure; only the CPU-baseline legs use it)."""
+
+    def __init__(self, c, n_tmpl, n_ref, rank, workers):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for _ in range(workers):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_worker, args=(b, c, n_tmpl, n_ref, rank), daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+
+    @staticmethod
+    def _get(conn):
+        r = conn.recv()
+        if r[0] == "error":
+            raise RuntimeError("oracle worker: " + r[1])
+        return r
+
+    def eval_all(self, js, eps):
+        """Oracle triggers of templates js, spread over the workers as they free up."""
+        from multiprocessing.connection import wait
+        todo = list(js)
+        busy, out = {}, {}
+        for conn in self.conns:
+            if todo:
+                conn.send(("eval", todo.pop(0), eps))
+                busy[conn] = True
+        while busy:
+            for conn in wait(list(busy)):
+                r = self._get(conn)
+                out[r[1]] = {"K": r[2], "triggers": r[3], "amb": r[4], "secs": r[5], "sigma_eff": r[6]}
+                if todo:
+                    conn.send(("eval", todo.pop(0), eps))
+                else:
+                    del busy[conn]
+        return out
+
+    def prep(self, js):
+        for conn, j in zip(self.conns, js):
+            conn.send(("prep", j))
+        return [self._get(conn)[1] for conn in self.conns[:len(js)]]
+
+    def step(self):
+        """One pass of every worker's kept template at once; returns (wall seconds, per-worker seconds)."""
+        t0 = time.perf_counter()
+        for conn in self.conns:
+            conn.send(("step",))
+        per = [self._get(conn)[1] for conn in self.conns]
+        return time.perf_counter() - t0, per
+
+    def close(self):
+        for conn in self.conns:
+            try:
+                conn.send(("stop",))
+            except (BrokenPipeError, OSError):
+                pass
+        for pr in self.procs:
+            pr.join(timeout=10)
+            if pr.is_alive():
+                pr.kill()
+
+
+def stratified_sample(cfg, bank, K, data, n_sample, seed=0):
+    """Templates for the oracle check: every (reference, K) group of the bank once, every
+    injected template, then a seeded draw up to n_sample."""
+    rng = np.random.default_rng(seed)
+    pick = set()
+    groups = {}
+    for j in range(bank.n_tmpl):
+        groups.setdefault((int(bank.ref_of_tmpl[j]), int(K[j])), []).append(j)
+    for key in sorted(groups):
+        pick.add(int(rng.choice(groups[key])))
+    pick |= {int(s) for (_, _, _, s) in data.injections}
+    rest = np.setdiff1d(np.arange(bank.n_tmpl), np.fromiter(pick, dtype=np.int64))
+    extra = max(0, n_sample - len(pick))
+    if extra and len(rest):
+        pick |= {int(j) for j in rng.choice(rest, size=min(extra, len(rest)), replace=False)}
+    return sorted(pick)
+
+
+def error_vs_oracle(ow, cfg, bank, data, K, trig, prec, n_sample):
+    """The GPU step's triggers against the FP64 oracle's on a stratified sample of templates:
+    relative |z| error at the triggers both have (same window and sample), and window counts
+    (matched, skipped as ambiguous under the path's error bound, mismatched).  A template whose
+    oracle K differs from the GPU's (a bucket boundary within rounding) is counted, not compared."""
+    eps = EPS[prec]
+    js = stratified_sample(cfg, bank, K, data, n_sample)
+    t0 = time.perf_counter()
+    ora = ow.eval_all(js, eps)
+    secs = time.perf_counter() - t0
+    errs, zerrs = [], []
+    matched = amb_skipped = mismatched = k_diff = 0
+    n_oracle = 0
+    for j in js:
+        o = ora[j]
+        if o["K"] != int(K[j]):
+            k_diff += 1
+            continue
+        n_oracle += len(o["triggers"])
+        amb = set(o["amb"])
+        ob = {w: (t, complex(zr, zi)) for (w, t, zr, zi) in o["triggers"]}
+        g = trig[trig["j"] == j]
+        gb = {int(x["t"]) // cfg.window: (int(x["t"]), float(x["snr2"]), complex(float(x["zr"]), float(x["zi"])))
+              for x in g}
+        for w in set(ob) | set(gb):
+            if w in amb:
+                amb_skipped += 1
+                continue
+            if w in ob and w in gb and ob[w][0] == gb[w][0]:
+                matched += 1
+                za = abs(ob[w][1])
+                errs.append(abs(math.sqrt(gb[w][1]) / za - 1.0))
+                zerrs.append(abs(gb[w][2] - ob[w][1]) / za)
+            else:
+                mismatched += 1
+    return {"templates": len(js), "sample": "every (reference, K) group once, every injected template, then a "
+                                            "seeded draw (seed 0)",
+            "snr_rel_err_max": max(errs) if errs else None,
+            "snr_rel_err_median": float(np.median(errs)) if errs else None,
+            "z_rel_err_max": max(zerrs) if zerrs else None,
+            "windows_oracle": n_oracle, "windows_matched": matched, "windows_ambiguous": amb_skipped,
+            "windows_mismatched": mismatched, "templates_k_differs": k_diff,
+            "ambiguity_band": "peak within 4 x %g of the threshold or runner-up within 4 x %g of the peak" % (eps, eps),
+            "tolerance": 1e-5 if prec == 0 else 1e-3, "error_bound": eps,
+            "oracle_seconds": secs, "oracle_template_seconds": [ora[j]["secs"] for j in js]}
 
 
 def run_reference(args):
+    """The FP64 oracle (the paper ships no implementation) on this host's cores: every step is
+    one pass of the Eq. 3 series and triggers of one template per core at once, reference series
+    and taps prepared beforehand (untimed)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     cfg, bank, data = workload_for_rank(args.config, 0)
+    cores = host_cores()
     t_setup = time.perf_counter()
-    ora, js, designs = oracle_sample(cfg, bank, data, 4)
-    ora.q_ref(int(bank.ref_of_tmpl[js[0]]))
-    t_setup = time.perf_counter() - t_setup
-    for i in range(args.warmup):
-        oracle_step(cfg, ora, js[i % len(js)], designs[i % len(js)])
-    times = []
-    for i in range(args.steps):
-        t0 = time.perf_counter()
-        oracle_step(cfg, ora, js[i % len(js)], designs[i % len(js)])
-        times.append(time.perf_counter() - t0)
+    ow = OracleWorkers(args.config, None, None, 0, cores)
+    try:
+        rng = np.random.default_rng(0)
+        r0 = int(bank.ref_of_tmpl[0])
+        cands = np.nonzero(bank.ref_of_tmpl == r0)[0]
+        js = [int(j) for j in rng.choice(cands, size=min(cores, len(cands)), replace=len(cands) < cores)]
+        Ks = ow.prep(js)
+        t_setup = time.perf_counter() - t_setup
+        for _ in range(args.warmup):
+            ow.step()
+        times = []
+        for _ in range(args.steps):
+            wall, _ = ow.step()
+            times.append(wall)
+    finally:
+        ow.close()
     mean = sum(times) / len(times)
-    value = cfg.duration / mean
+    value = cores * cfg.duration / mean
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": cfg.name, "n_tmpl": cfg.n_tmpl, "n_ref": cfg.n_ref, "k": cfg.k, "n": cfg.n,
                    "fs": cfg.fs},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step: one template of the bank through the FP64 oracle's direct "
-                                   "circular FIR (K=%s, n=%d) and window-max triggers, reference series and "
-                                   "taps precomputed (set-up %.1f s)" % (
-                                       sorted(len(d["taps"]) for d in designs), cfg.n, t_setup)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "each step: %d templates of the bank at once, one per host core, through the "
+                                   "FP64 oracle's direct circular FIR (Eq. 3; K=%s, n=%d) and window-max "
+                                   "triggers; reference series and taps prepared beforehand (%.1f s)" % (
+                                       len(js), sorted(set(Ks)), cfg.n, t_setup)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -640,13 +825,28 @@ class GpuSearch:
         return nt, kms
 
     def step_e2e(self):
-        """Through host buffers: H2D of the data spectrum, the step, D2H of the triggers."""
+        """One segment end to end through the C ABI's host-buffer call (rfd_search_run_host):
+        H2D of the data spectrum from pinned memory, the graph, D2H of the triggers."""
+        return self.search.run_host(self.d_host, self.trig_host)
+
+    def e2e_phases(self, nt, reps=5):
+        """Device times of the pieces of an end-to-end step on the search stream: the H2D copy
+        of the spectrum and the D2H copy of nt triggers alone (CUDA events, pinned memory)."""
         torch = self.torch
+        out = {}
         with torch.cuda.stream(self.stream):
-            self.d.copy_(self.d_host, non_blocking=True)
-            nt, _ = self.step()
-            self.trig_host[: nt * 20].copy_(self.trig[: nt * 20], non_blocking=False)
-        return nt
+            for name, dst, src in (("h2d_ms", self.d, self.d_host),
+                                   ("d2h_ms", self.trig_host[: max(nt, 1) * 20], self.trig[: max(nt, 1) * 20])):
+                ts = []
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(self.stream)
+                    dst.copy_(src, non_blocking=True)
+                    b.record(self.stream)
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b))
+                out[name] = float(np.median(ts))
+        return out
 
     def close(self):
         if self.search is not None:
@@ -702,20 +902,14 @@ def findchirp_rate(cfg, bank, data, device, steps=2, max_templates=4096):
     return bank.n_tmpl * cfg.duration / t, t, t_own, t_cufft, bank.n_tmpl
 
 
-def run_ours(args):
+def measure(args, c, prec, precision_name, ws, rank, local, primary):
+    """Set-up, warm-up, timed steps, end-to-end steps, roofline, comparisons and the oracle check
+    of one workload; returns the fields of its JSON line."""
     import torch
     import paper_2601_18835_gb300 as rfd
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        dist.init_process_group(backend)
-    torch.cuda.set_device(local)
-    precision_name = args.precision or "fp16x3"
-    prec = PREC[precision_name]
-    cfg, bank, data = workload_for_rank(args.config, rank, args.n_tmpl, args.n_ref)
-    learned = None
-    if cfg.lambda_range is not None:          # the learned-tap workload
+    cfg, bank, data = workload_for_rank(c, rank, args.n_tmpl if primary else None, args.n_ref if primary else None)
+    learned = fit = fixed = None
+    if primary and cfg.lambda_range is not None:          # the learned-tap workload
         import workload
         dense_train = None
         if args.dense_refs:
@@ -730,9 +924,9 @@ def run_ours(args):
         learned = {"n_train": args.n_train, "epochs": args.epochs, "dense_train": dense_train,
                    "spot_stride": args.spot_stride}
     tune_cache = os.path.join(ROOT, "paper_2601_18835_gb300", "_build", "autotune.json")
-    fit = {"target": args.match_target, "ridge": args.ridge} if args.taps == "fit" else None
-    fixed = None
-    if args.long_k is not None or args.fft_k is not None or args.stream_block:
+    if primary and args.taps == "fit":
+        fit = {"target": args.match_target, "ridge": args.ridge}
+    if primary and (args.long_k is not None or args.fft_k is not None or args.stream_block):
         fixed = {"mix_k": 1}
         if args.stream_block:
             fixed["out_len"] = args.stream_block
@@ -779,43 +973,55 @@ def run_ours(args):
     ms = sum(step_ms) / len(step_ms)
     ms_max = max_over_ranks(ms, ws)
     value = job_rate(ws, J, step_dur, ms_max / 1e3)
+    trig_np = rfd.triggers_to_numpy(s.trig, ntrig).copy() if s.out_len == cfg.n else None
 
-    # end to end through host buffers
-    for _ in range(2):
-        s.step_e2e()
-    torch.cuda.synchronize()
-    e2e_t = []
-    for _ in range(args.e2e_steps):
-        s.flush_l2()
+    # end to end through the C ABI's host-buffer call: H2D of the spectrum, the graph, D2H of
+    # the triggers, each step after an L2 flush (outside the timed region)
+    e2e = None
+    if s.search is not None and s.out_len == cfg.n:
+        for _ in range(2):
+            s.step_e2e()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        nt = s.step_e2e()
-        torch.cuda.synchronize()
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_value = job_rate(ws, J, step_dur, max_over_ranks(sum(e2e_t) / len(e2e_t), ws))
+        e2e_t, dev_t = [], []
+        nt = 0
+        for _ in range(args.e2e_steps):
+            s.flush_l2()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nt = s.step_e2e()
+            e2e_t.append(time.perf_counter() - t0)
+            dev_t.append(s.search.step_ms())
+        e2e_s = sum(e2e_t) / len(e2e_t)
+        ph = s.e2e_phases(nt)
+        ph["graph_device_ms"] = float(np.mean(dev_t))
+        ph["host_total_ms"] = e2e_s * 1e3
+        ph["host_overhead_ms"] = ph["host_total_ms"] - ph["graph_device_ms"] - ph["h2d_ms"] - ph["d2h_ms"]
+        e2e = {"value": job_rate(ws, J, step_dur, max_over_ranks(e2e_s, ws)), "unit": UNIT,
+               "h2d_bytes_per_step": int(s.d_host.numel() * 8), "d2h_bytes_per_step": int(nt * 20),
+               "api": "rfd_search_run_host (pinned host spectrum in, triggers out)", "phases_ms": ph}
 
     # roofline of the dominant kernel: the ratio-filter contraction (or, for a plan that sends
     # long templates to the block-FFT kernel, whichever family takes longer, timed on its own)
     peaks, peak_kind = measured_peaks()
+    sustained = ms_max * args.steps > 1000.0        # the timed steps keep the GPU busy for over a second
     filt_s = sum(kernel_ms) / len(kernel_ms) / 1e3
-    alg_flops = s.alg_flops()
     parts = s.kernel_parts() if prec != 0 else []
     if parts:
         dom = max(parts, key=lambda q: q["ms"])
         roof = roofline(prec, dom["family"], s.K[dom["idx"]], s.options, s.out_len, bank.n_ref, dom["ms"] / 1e3,
-                        dom["executed_flops"], peaks, peak_kind, None)
+                        dom["executed_flops"], peaks, peak_kind, None, sustained)
         for q in parts:
             q["frac"] = roofline(prec, q["family"], s.K[q["idx"]], s.options, s.out_len, bank.n_ref, q["ms"] / 1e3,
-                                 q["executed_flops"], peaks, peak_kind)["frac"]
+                                 q["executed_flops"], peaks, peak_kind, None, sustained)["frac"]
         roof["parts"] = [{k: v for k, v in q.items() if k not in ("idx", "executed_flops")} for q in parts]
     else:
         family = "fft" if fft_templates(s.K, s.options) == len(s.K) and prec != 0 else "direct"
         roof = roofline(prec, family, s.K, s.options, s.out_len, bank.n_ref, filt_s,
                         s.plan.executed_flops() if prec != 0 else 0.0, peaks, peak_kind,
-                        cfg.name if s.out_len == cfg.n else None)
+                        cfg.name if s.out_len == cfg.n else None, sustained)
 
     chisq_rep = None
-    if args.chisq and prec != 0:
+    if primary and args.chisq and prec != 0:
         # the sub-band chi^2 of the step's triggers: per-band reference series (once per segment)
         # and the per-trigger sub-band FIRs; the band shares are per-bank set-up
         sb = rfd.Subband(s.ctx, s.grid, s.psd, bank.ref_params(), args.chisq)
@@ -855,35 +1061,34 @@ def run_ours(args):
                 s32.step(e)
                 torch.cuda.synchronize()
                 tt.append(s32.last_step_ms)
-            comparisons["fp32_fir_step"] = {"value": J * dur / (sum(tt) / len(tt) / 1e3), "unit": UNIT,
-                                            "ms_per_step": sum(tt) / len(tt)}
+            fp32_ms = sum(tt) / len(tt)
+            comparisons["fp32_fir_step"] = {"value": J * dur / (fp32_ms / 1e3), "unit": UNIT,
+                                            "ms_per_step": fp32_ms, "ratio": (fp32_ms / ms_max)}
             s32.close()
         fc_value, fc_t, t_own, t_cufft, fc_n = findchirp_rate(cfg, bank, data, local)
         comparisons["findchirp"] = {"value": fc_value, "unit": UNIT, "ms_per_step": fc_t * 1e3,
-                                    "templates_timed": fc_n,
+                                    "templates_timed": fc_n, "ratio": value / fc_value,
                                     "ifft_us_per_row_stockham": t_own * 1e6, "ifft_us_per_row_cufft": t_cufft * 1e6}
 
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        ora, js, designs = oracle_sample(cfg, bank, data, 8)
-        t0 = time.perf_counter()
-        ora.q_ref(int(bank.ref_of_tmpl[js[0]]))
-        done = 0
-        while time.perf_counter() - t0 < 10.0:
-            oracle_step(cfg, ora, js[done % len(js)], designs[done % len(js)])
-            done += 1
-        el = time.perf_counter() - t0
-        cpu = {"value": done * dur / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one reference's FP64 matched filter plus %d template passes (8 distinct templates) "
-                         "through the oracle's direct circular FIR (K=%s, n=%d) and triggers, taps "
-                         "precomputed: %.1f s of one host core" % (done, sorted(len(d["taps"]) for d in designs),
-                                                                   cfg.n, el)}
+    cpu = err = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and s.out_len == cfg.n:
+        cores = host_cores()
+        ow = OracleWorkers(c, args.n_tmpl if primary else None, args.n_ref if primary else None, 0, cores)
+        try:
+            err = error_vs_oracle(ow, cfg, bank, data, s.K, trig_np, prec,
+                                  args.oracle_sample if args.oracle_sample else (128 if cfg.n_tmpl <= 8192 else 256))
+        finally:
+            ow.close()
+        ts = err.pop("oracle_template_seconds")
+        cpu = {"value": cores * dur / float(np.mean(ts)), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "the %d templates of the oracle check, one per host process at a time on %d cores: each "
+                         "template's FP64 direct circular FIR (Eq. 3, n=%d) and window-max triggers timed inside "
+                         "its process (designs untimed); rate = cores x segment / mean template time "
+                         "(%.2f s)" % (len(ts), cores, cfg.n, float(np.mean(ts)))}
 
     match = s.match.cpu().numpy() if s.match is not None else None
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": precision_name, "data": "synthetic",
+    out = {
+        "value": value, "ms_per_step": ms_max, "dtype": precision_name,
         "config": {"workload": cfg.name + ("_stream%d" % s.out_len if s.out_len < cfg.n else ""),
                    "n_tmpl": J, "n_ref": bank.n_ref,
                    "k": (cfg.k if (cfg.k and fit is None) else
@@ -896,10 +1101,10 @@ def run_ours(args):
                    "segment_s": dur, "window": cfg.window, "threshold": cfg.threshold,
                    "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if ws > 1 else "single"},
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s.d_host.numel() * 8),
-                "d2h_bytes_per_step": int(nt * 20 + 8 * 3)},
+        "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roof,
+        "error_vs_oracle": err,
         "cpu_baseline": cpu,
         "comparisons": comparisons,
         "breakdown_ms": {"ratio_filter_batch": filt_s * 1e3, "rest_of_step": ms - filt_s * 1e3},
@@ -912,18 +1117,48 @@ def run_ours(args):
         "triggers_per_step": int(ntrig),
     }
     if s.learned_report is not None:
-        line["learned_taps"] = s.learned_report
+        out["learned_taps"] = s.learned_report
     if chisq_rep is not None:
-        line["subband_chi2"] = chisq_rep
+        out["subband_chi2"] = chisq_rep
     if s.out_len < cfg.n:
         srt = sorted(step_ms)
-        line["streaming"] = {"block_samples": s.out_len, "block_s": step_dur,
-                             "latency_ms_median": srt[len(srt) // 2], "latency_ms_max": srt[-1],
-                             "ratio_filter_ms": filt_s * 1e3,
-                             "note": "per block: every reference's matched filter over the whole segment "
-                                     "(Eq. 1, as an overlap-save stream re-transforms it), the ratio filter "
-                                     "over the block's outputs only, and the trigger merge"}
+        out["streaming"] = {"block_samples": s.out_len, "block_s": step_dur,
+                            "latency_ms_median": srt[len(srt) // 2], "latency_ms_max": srt[-1],
+                            "ratio_filter_ms": filt_s * 1e3,
+                            "note": "per block: every reference's matched filter over the whole segment "
+                                    "(Eq. 1, as an overlap-save stream re-transforms it), the ratio filter "
+                                    "over the block's outputs only, and the trigger merge"}
     s.close()
+    del s
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    torch.cuda.set_device(local)
+    precision_name = args.precision or "fp16x3"
+    prec = PREC[precision_name]
+    head = measure(args, args.config, prec, precision_name, ws, rank, local, primary=True)
+    line = {"metric": METRIC, "value": head.pop("value"), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head.pop("ms_per_step"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": head.pop("dtype"), "data": "synthetic"}
+    line.update(head)
+    # the larger single-GPU workloads, timed the same way, under their own key (the headline
+    # stays the configured workload): only for a plain default run on one GPU
+    extra = [int(x) for x in args.extra_configs.split(",") if x.strip()] if args.extra_configs else []
+    plain = (args.config == 2 and not args.n_tmpl and not args.n_ref and not args.stream_block and args.taps ==
+             "windowed" and args.long_k is None and args.fft_k is None and not args.no_graph)
+    if ws == 1 and plain and extra:
+        line["more_configs"] = {}
+        for c in extra:
+            r = measure(args, c, prec, precision_name, ws, rank, local, primary=False)
+            line["more_configs"][r["config"]["workload"]] = r
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:

@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define RFD_VERSION 3
+#define RFD_VERSION 4
 
 typedef enum {
     RFD_OK = 0,
@@ -244,9 +244,19 @@ typedef struct {
                              multiple of 512 (n a multiple of 512 too): rfd_ratio_filter_window
                              then filters out_len positions from a start held in device memory
                              (streaming, Sec. VII.A) */
+    int32_t fft_rem;      /* per reference, the templates bound for the long-tap kernel fill
+                             tiles of 64; when they leave a last tile of at most fft_rem
+                             templates (a tile whose empty rows the MMAs still compute), those
+                             templates (the ones with the largest K) go to the block-FFT kernel
+                             instead (needs K <= 1024): 0 = never, at most 63 */
+    int32_t debug_flags;  /* testing only, 0 otherwise.  RFD_DEBUG_STALL_TAPS: the tensor-core
+                             kernels never copy the taps and give up their waits after a few
+                             thousand polls, so that rfd_find_triggers reports RFD_ERR_TIMEOUT
+                             (the test of the bounded-wait abort path) */
 } rfd_plan_options;
+#define RFD_DEBUG_STALL_TAPS 1
 /* Fills the defaults: tile_nt = {128, 64, 32}, mix_k = 1, grid_ctas = 0, long_k = 64,
- * fft_k = 4096, out_len = 0. */
+ * fft_k = 4096, out_len = 0, fft_rem = 0, debug_flags = 0. */
 void rfd_plan_options_default(rfd_plan_options *options);
 /* rfd_plan_create with explicit tile choices (NULL = defaults). */
 rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
@@ -334,6 +344,15 @@ rfd_status rfd_search_run(rfd_search *search, void *stream, int64_t *n_trig_host
  * memory the graph reads, then the graph is launched as by rfd_search_run).  A plan without a
  * window ignores it. */
 rfd_status rfd_search_run_at(rfd_search *search, int64_t u_begin, void *stream, int64_t *n_trig_host);
+/* One segment end to end from host memory: copies the data spectrum dtilde_host (complex64
+ * [n/2+1], host memory; pinned memory makes the copy asynchronous with respect to other host
+ * work) into the search's bound dtilde_dev on `stream`, replays the graph as rfd_search_run,
+ * then copies the triggers (rfd_trigger, sorted by (j, w)) into trig_host [trig_host_capacity].
+ * Returns the trigger count in *n_trig_host with the status rules of rfd_find_triggers, and
+ * RFD_ERR_OVERFLOW (with the count) when trig_host_capacity is too small; nothing is copied
+ * to trig_host then.  Synchronises the stream twice (the count decides the read-back size). */
+rfd_status rfd_search_run_host(rfd_search *search, const void *dtilde_host, rfd_trigger *trig_host,
+                               int64_t trig_host_capacity, void *stream, int64_t *n_trig_host);
 /* Kernels one run launches (they are counted in rfd_kernel_launches as they are replayed). */
 int64_t rfd_search_kernels_per_run(const rfd_search *search);
 /* Device time (ms) of the ratio-filter kernel in the last completed run (CUDA events recorded

@@ -171,7 +171,8 @@ class Plan:
     def __init__(self, ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, options=None):
         """options: dict with any of tile_nt (3 ints), mix_k (0/1), grid_ctas (int), long_k (int),
         fft_k (int: templates with fft_k < K <= 1024 use the block-FFT kernel), out_len (int: outputs per
-        call, a multiple of 512; 0 = the whole segment)."""
+        call, a multiple of 512; 0 = the whole segment), fft_rem (int: a reference's last long-kernel
+        tile of at most this many templates goes to the block-FFT kernel), debug_flags (testing only)."""
         ro, rop = _i32_host(ref_of)
         kk, kp = _i32_host(k)
         h = ctypes.c_void_p()
@@ -192,6 +193,10 @@ class Plan:
                 opt.fft_k = int(options["fft_k"])
             if "out_len" in options:
                 opt.out_len = int(options["out_len"])
+            if "fft_rem" in options:
+                opt.fft_rem = int(options["fft_rem"])
+            if "debug_flags" in options:
+                opt.debug_flags = int(options["debug_flags"])
         check(_lib().rfd_plan_create_ex(ctx.handle, ctypes.byref(g), int(n_ref), len(ro), rop, kp,
                                         int(precision), int(window), float(threshold), int(halo),
                                         ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))
@@ -268,6 +273,20 @@ class Search:
         else:
             check(_lib().rfd_search_run_at(self.handle, int(u_begin), _stream(self.stream), ctypes.byref(n)),
                   needed=n.value)
+        return int(n.value)
+
+    def run_host(self, dtilde_host, trig_host):
+        """One segment end to end from host memory (rfd_search_run_host): dtilde_host (a CPU
+        complex64 tensor of n/2+1 bins, pinned for an asynchronous copy) in, triggers out into
+        trig_host (a CPU uint8 tensor of rfd_trigger records).  Returns the number of triggers."""
+        for t in (dtilde_host, trig_host):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("expected contiguous host (CPU) tensors")
+        tcap = trig_host.numel() * trig_host.element_size() // TRIGGER_DTYPE.itemsize
+        n = ctypes.c_int64(0)
+        check(_lib().rfd_search_run_host(self.handle, ctypes.c_void_p(dtilde_host.data_ptr()),
+                                         ctypes.c_void_p(trig_host.data_ptr()), int(tcap), _stream(self.stream),
+                                         ctypes.byref(n)), needed=n.value)
         return int(n.value)
 
     def close(self):

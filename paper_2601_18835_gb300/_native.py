@@ -35,7 +35,11 @@ class Grid(ctypes.Structure):
 
 class PlanOptions(ctypes.Structure):
     _fields_ = [("tile_nt", ctypes.c_int32 * 3), ("mix_k", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
-                ("long_k", ctypes.c_int32), ("fft_k", ctypes.c_int32), ("out_len", ctypes.c_int32)]
+                ("long_k", ctypes.c_int32), ("fft_k", ctypes.c_int32), ("out_len", ctypes.c_int32),
+                ("fft_rem", ctypes.c_int32), ("debug_flags", ctypes.c_int32)]
+
+
+DEBUG_STALL_TAPS = 1
 
 
 class Params(ctypes.Structure):
@@ -80,6 +84,7 @@ SIGNATURES = {
                                  ctypes.POINTER(_vp)]),
     "rfd_search_run": (_i32, [_vp, _vp, ctypes.POINTER(_i64)]),
     "rfd_search_run_at": (_i32, [_vp, _i64, _vp, ctypes.POINTER(_i64)]),
+    "rfd_search_run_host": (_i32, [_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(_i64)]),
     "rfd_search_kernels_per_run": (_i64, [_vp]),
     "rfd_search_filter_ms": (_dbl, [_vp]),
     "rfd_search_step_ms": (_dbl, [_vp]),

@@ -4,8 +4,11 @@ The choices (rfd_plan_options): templates per tile for each K class, whether a t
 templates of different K (padding the short ones) or must split where K changes, the number
 of persistent CTAs, above which K templates go to the long-tap kernel (templates on the
 MMA's M side, time on its N side), and above which K they go to the block-FFT kernel (FP32
-overlap-save transforms on the CUDA cores, cheaper than the contraction for long taps).  Each candidate plan is built through the C ABI, given the bank's
-taps, and timed on the q_ref buffer with CUDA events; the fastest wins.  Results are cached
+overlap-save transforms on the CUDA cores, cheaper than the contraction for long taps), and
+how small a reference's last long-kernel tile may be before its templates go to the block-FFT
+kernel instead of padding a 64-template tile.  Each candidate plan is built through the C ABI,
+given the bank's taps, and timed on the q_ref buffer with CUDA events after an L2 flush; the
+fastest wins.  Results are cached
 in a JSON file keyed by the workload's signature (grid, precision, the (reference, K)
 histogram, the device), so a bank is tuned once.
 """
@@ -30,6 +33,9 @@ DEFAULT_CANDIDATES = [
     {"mix_k": 1, "fft_k": 128},
     {"mix_k": 1, "fft_k": 0},
     {"mix_k": 1, "fft_k": 128, "long_k": 0},
+    {"mix_k": 1, "fft_rem": 16},
+    {"mix_k": 1, "fft_rem": 40},
+    {"mix_k": 0, "fft_rem": 16},
 ]
 
 
@@ -45,12 +51,13 @@ def signature(g, precision, ref_of, k):
     return h.hexdigest()[:24]
 
 
-def _time_plan(plan, qref, qscale, cand, cnt, reps):
+def _time_plan(plan, qref, qscale, cand, cnt, reps, flush):
     for _ in range(2):
         plan.ratio_filter_batch(qref, qscale, cand, cnt)
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
+        flush.random_(0, 255)          # every timed call starts from a cold L2, as a search step does
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         plan.ratio_filter_batch(qref, qscale, cand, cnt)
@@ -77,11 +84,12 @@ def autotune(ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, taps,
             return cache[sig]["options"], cache[sig]
     cand = torch.zeros((1 << 22) * CANDIDATE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # larger than the 126 MB L2
     report = []
     for opts in cands:
         plan = Plan(ctx, g, n_ref, ref_of, k, precision, window, threshold, halo, options=opts)
         plan.set_taps(taps, k_stride, lag, sigma)
-        ms = _time_plan(plan, qref, qscale, cand, cnt, reps)
+        ms = _time_plan(plan, qref, qscale, cand, cnt, reps, flush)
         report.append({"options": opts, "ms": ms, "executed_tflop": plan.executed_flops() / 1e12})
         plan.close()
     best = min(report, key=lambda r: r["ms"])

@@ -605,6 +605,8 @@ void rfd_plan_options_default(rfd_plan_options *o) {
     o->grid_ctas = 0;
     o->long_k = 64;
     o->fft_k = 4096;
+    o->fft_rem = 0;
+    o->debug_flags = 0;
 }
 
 rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref, int32_t n_tmpl,
@@ -624,6 +626,8 @@ rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref,
         RFD_REQUIRE(opt.fft_k >= 0 && opt.fft_k <= 4096, RFD_ERR_ARG, "fft_k must be in [0, 4096]");
         RFD_REQUIRE(opt.out_len >= 0 && opt.out_len % 512 == 0, RFD_ERR_ARG,
                     "out_len=%d must be 0 or a positive multiple of 512", opt.out_len);
+        RFD_REQUIRE(opt.fft_rem >= 0 && opt.fft_rem < 64, RFD_ERR_ARG, "fft_rem must be in [0, 63]");
+        RFD_REQUIRE((opt.debug_flags & ~RFD_DEBUG_STALL_TAPS) == 0, RFD_ERR_ARG, "unknown debug_flags bits");
     }
     RFD_REQUIRE(ctx && out, RFD_ERR_ARG, "NULL ctx or out");
     *out = nullptr;
@@ -672,6 +676,38 @@ rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref,
     // templates with fft_k < K <= 1024 go to the block-FFT path
     std::vector<int32_t> order_fft, order_rest;
     for (int32_t j : order) (p->k_of[j] > opt.fft_k && p->k_of[j] <= 1024 ? order_fft : order_rest).push_back(j);
+    if (precision != RFD_PREC_FP32 && opt.fft_rem > 0) {
+        // per reference, the long-tap kernel's last partial tile (its largest-K templates) goes
+        // to the block-FFT kernel when it holds at most fft_rem templates
+        const int32_t nt = tl_tile_templates();
+        std::vector<int32_t> keep;
+        size_t i = 0;
+        while (i < order_rest.size()) {
+            const int32_t r = p->ref_of[order_rest[i]];
+            size_t e = i;
+            while (e < order_rest.size() && p->ref_of[order_rest[e]] == r) ++e;
+            std::vector<int32_t> lng;
+            for (size_t q = i; q < e; ++q) {
+                const int32_t j = order_rest[q];
+                if (p->k_of[j] > opt.long_k) lng.push_back(j); else keep.push_back(j);
+            }
+            const int32_t rem = (int32_t)(lng.size() % (size_t)nt);
+            const bool move = rem > 0 && rem <= opt.fft_rem && p->k_of[lng.back()] <= 1024;
+            for (size_t q = 0; q < lng.size(); ++q)
+                (move && q >= lng.size() - (size_t)rem ? order_fft : keep).push_back(lng[q]);
+            i = e;
+        }
+        order_rest.swap(keep);
+        std::stable_sort(order_rest.begin(), order_rest.end(), [&](int32_t a, int32_t b) {
+            if (p->ref_of[a] != p->ref_of[b]) return p->ref_of[a] < p->ref_of[b];
+            return p->k_of[a] < p->k_of[b];
+        });
+        std::stable_sort(order_fft.begin(), order_fft.end(), [&](int32_t a, int32_t b) {
+            if (p->ref_of[a] != p->ref_of[b]) return p->ref_of[a] < p->ref_of[b];
+            return p->k_of[a] < p->k_of[b];
+        });
+    }
+    p->debug_flags = opt.debug_flags;
     order.swap(order_rest);
     if (precision != RFD_PREC_FP32) {
         rfd_status st = plan_tc_tiles(p, order, ctx->num_sms, opt);

@@ -229,6 +229,7 @@ struct rfd_plan {
     uint32_t tc_taps_cap = 0, tc_win = 0;
     int32_t tc_grid = 0;
     double executed_flops = 0.0;     // tensor (or FMA) flops one ratio_filter_batch executes
+    int32_t debug_flags = 0;         // RFD_DEBUG_* (testing only)
     // block-FFT path (rf_fft.cu): templates with fft_k < K <= 1024
     std::vector<FftTile> fft_tiles;
     std::vector<int32_t> fft_refs;   // references with block-FFT templates

@@ -20,7 +20,10 @@
 // bulk-copied once per tile change from the image rfd_plan_set_taps pre-swizzles.  One CTA
 // per SM walks a contiguous, cost-balanced range of (tile, time block) items.  Roles: warp 0
 // bulk copies, warp 1 issues the MMAs (and owns the TMEM allocation), warps 4-7 build A,
-// warps 8-15 drain the accumulator and run the epilogue.  Every wait is bounded.
+// warps 8-15 drain the accumulator and run the epilogue.  Every wait is bounded.  Every bulk
+// copy completes on a barrier that only the producer arms, and before the CTA ends the producer
+// waits (bounded) for the last phase it armed on each: no copy is still landing in shared
+// memory when the CTA exits, also after a wait has given up.
 #include "epilogue.cuh"
 #include "internal.cuh"
 #include "tc_ptx.cuh"
@@ -37,6 +40,7 @@ constexpr int kThreads = 512;
 constexpr int kEpiWarps = 8;      // two per TMEM lane group, each half of the templates
 constexpr uint32_t kACol = 256;   // first TMEM column of the A stages (D uses 0 .. 2 NT - 1)
 constexpr uint32_t kSpin = 1u << 22;
+constexpr uint32_t kSpinStall = 1u << 12;        // RFD_DEBUG_STALL_TAPS: give up quickly
 
 enum {
     kBarTapsFull = 0,
@@ -71,11 +75,13 @@ struct TcArgs {
     unsigned long long *count;
     uint32_t taps_cap;          // bytes of the taps region
     uint32_t win;               // elements per q window plane
+    uint32_t spin;              // polls before a wait gives up
+    uint32_t stall;             // RFD_DEBUG_STALL_TAPS: never copy the taps (tests the abort path)
 };
 
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag,
-                                         unsigned long long *count) {
-    for (uint32_t i = 0; i < kSpin; ++i) {
+                                         unsigned long long *count, uint32_t spin) {
+    for (uint32_t i = 0; i < spin; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
     }
@@ -126,28 +132,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
         // ------------------------------------------------------------ producer (bulk copies)
         if (lane == 0) {
             uint32_t tchg = 0, li = 0;
+            uint32_t taps_armed = 0u, q_armed[2] = {0u, 0u};   // phases armed (for the final drain)
             int64_t prev = -1;
             for (int64_t it = it0; it < it1; ++it, ++li) {
                 const int64_t ti = it / A.n_tt, tt = it - ti * A.n_tt;
                 const TcTile T = A.tiles[ti];
                 if (ti != prev) {
-                    if (!wait_bar(BAR(kBarTapsEmpty), (tchg & 1u) ^ 1u, abort_flag, A.count)) break;
-                    mbar_arrive_expect_tx(BAR(kBarTapsFull), (uint32_t)T.taps_bytes);
-                    for (uint32_t o = 0; o < (uint32_t)T.taps_bytes; o += 32768u) {
-                        const uint32_t len = min(32768u, (uint32_t)T.taps_bytes - o);
-                        bulk_g2s(smem_u32(s_taps) + o, A.taps + T.taps_off + o, len, BAR(kBarTapsFull));
+                    if (!wait_bar(BAR(kBarTapsEmpty), (tchg & 1u) ^ 1u, abort_flag, A.count, A.spin)) break;
+                    if (!A.stall) {                // stalled: the taps barrier never completes
+                        mbar_arrive_expect_tx(BAR(kBarTapsFull), (uint32_t)T.taps_bytes);
+                        ++taps_armed;
+                        for (uint32_t o = 0; o < (uint32_t)T.taps_bytes; o += 32768u) {
+                            const uint32_t len = min(32768u, (uint32_t)T.taps_bytes - o);
+                            bulk_g2s(smem_u32(s_taps) + o, A.taps + T.taps_off + o, len, BAR(kBarTapsFull));
+                        }
                     }
                     ++tchg;
                     prev = ti;
                 }
                 const uint32_t qb = li & 1u, use = li >> 1;
-                if (!wait_bar(BAR(kBarQEmpty + qb), (use & 1u) ^ 1u, abort_flag, A.count)) break;
+                if (!wait_bar(BAR(kBarQEmpty + qb), (use & 1u) ^ 1u, abort_flag, A.count, A.spin)) break;
                 const uint32_t wbytes = (uint32_t)(kM + T.kpad) * 2u;
                 mbar_arrive_expect_tx(BAR(kBarQFull + qb), 4u * wbytes);
+                ++q_armed[qb];
                 for (int p = 0; p < 4; ++p) {
                     const uint16_t *src = A.q + (int64_t)(4 * T.ref + p) * A.ld + wrap_pos(ubase, tt * kM, A.n);
                     bulk_g2s(smem_u32(s_q + (qb * 4 + p) * A.win), src, wbytes, BAR(kBarQFull + qb));
                 }
+            }
+            // drain: the last phase armed on each copy barrier has completed before this thread
+            // reaches the CTA's final barrier (bounded, like every wait)
+            const uint32_t bars3[3] = {BAR(kBarTapsFull), BAR(kBarQFull), BAR(kBarQFull + 1)};
+            const uint32_t armed[3] = {taps_armed, q_armed[0], q_armed[1]};
+            for (int k = 0; k < 3; ++k) {
+                if (armed[k] == 0u) continue;
+                uint32_t i = 0;
+                while (i < kSpin && !mbar_try_wait(bars3[k], (armed[k] - 1u) & 1u)) ++i;
             }
         }
     } else if (warp == 1) {
@@ -160,11 +180,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
                 const int64_t ti = it / A.n_tt;
                 const TcTile T = A.tiles[ti];
                 if (ti != prev) {
-                    if (!wait_bar(BAR(kBarTapsFull), tchg & 1u, abort_flag, A.count)) break;
+                    if (!wait_bar(BAR(kBarTapsFull), tchg & 1u, abort_flag, A.count, A.spin)) break;
                     ++tchg;
                     prev = ti;
                 }
-                if (!wait_bar(BAR(kBarDEmpty), (li & 1u) ^ 1u, abort_flag, A.count)) break;
+                if (!wait_bar(BAR(kBarDEmpty), (li & 1u) ^ 1u, abort_flag, A.count, A.spin)) break;
                 fence_after();
                 const uint32_t nt = (uint32_t)T.nt;
                 const uint32_t d = tmem;
@@ -173,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
                 bool ok = true;
                 for (int s = 0; s < T.nk16; ++s, ++ka) {
                     const uint32_t st = ka % kStages, r = ka / kStages;
-                    if (!wait_bar(BAR(kBarAFull + st), r & 1u, abort_flag, A.count)) {
+                    if (!wait_bar(BAR(kBarAFull + st), r & 1u, abort_flag, A.count, A.spin)) {
                         ok = false;
                         break;
                     }
@@ -213,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
             const int64_t ti = it / A.n_tt;
             const int nk16 = A.tiles[ti].nk16;
             const uint32_t qb = li & 1u, use = li >> 1;
-            bool ok = wait_bar(BAR(kBarQFull + qb), use & 1u, abort_flag, A.count);
+            bool ok = wait_bar(BAR(kBarQFull + qb), use & 1u, abort_flag, A.count, A.spin);
             if (!__all_sync(0xffffffffu, ok)) break;
             const uint32_t *W0 = (const uint32_t *)(s_q + (qb * 4 + 0) * A.win);
             const uint32_t *W1 = (const uint32_t *)(s_q + (qb * 4 + 1) * A.win);
@@ -221,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
             const uint32_t *W3 = (const uint32_t *)(s_q + (qb * 4 + 3) * A.win);
             for (int s = 0; s < nk16; ++s, ++ka) {
                 const uint32_t st = ka % kStages, r = ka / kStages;
-                ok = wait_bar(BAR(kBarAEmpty + st), (r & 1u) ^ 1u, abort_flag, A.count);
+                ok = wait_bar(BAR(kBarAEmpty + st), (r & 1u) ^ 1u, abort_flag, A.count, A.spin);
                 if (!__all_sync(0xffffffffu, ok)) break;
                 const uint32_t e0 = row + (uint32_t)s * 16u, w0 = e0 >> 1, sh = (e0 & 1u) * 16u;
                 uint32_t v[32];
@@ -257,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
         for (int64_t it = it0; it < it1; ++it, ++li) {
             const int64_t ti = it / A.n_tt, tt = it - ti * A.n_tt;
             const TcTile T = A.tiles[ti];
-            const bool ok = wait_bar(BAR(kBarDFull), li & 1u, abort_flag, A.count);
+            const bool ok = wait_bar(BAR(kBarDFull), li & 1u, abort_flag, A.count, A.spin);
             if (!__all_sync(0xffffffffu, ok)) break;
             fence_after();
             const float esc = ldexpf(1.0f, -A.qscale[T.ref]);
@@ -470,6 +490,8 @@ rfd_status tc_launch(const rfd_plan *plan, const void *q, const int32_t *qscale,
     a.count = (unsigned long long *)count;
     a.taps_cap = plan->tc_taps_cap;
     a.win = plan->tc_win;
+    a.stall = (plan->debug_flags & RFD_DEBUG_STALL_TAPS) ? 1u : 0u;
+    a.spin = a.stall ? kSpinStall : kSpin;
     // at least 120 KB so that exactly one CTA (and one 512-column TMEM allocation) fits per SM
     const size_t shm = std::max<size_t>(tc_smem_bytes(a.taps_cap, a.win), 120 * 1024);
     const unsigned grid = (unsigned)plan->tc_grid;

@@ -24,9 +24,13 @@
 // rows) and the warp of quarter 0/1 (real rows, same templates) swap half of each 32-column
 // chunk through shared memory, and each forms z, |z|^2 and the per-window maxima of its 16
 // columns.  The MMA thread waits once per item, on a barrier of the item's buffer that the
-// epilogue (accumulator free), the builders (Y built) and the producer (first taps chunk, with
-// its bytes) all arrive on; taps chunks already in their stage are not copied again.  Every
-// wait is bounded.
+// epilogue (accumulator free), the builders (Y built) and the producer (first taps chunk
+// landed) all arrive on; taps chunks already in their stage are not copied again.  Every wait
+// is bounded.  Each bulk copy completes on a barrier that only the producer arms (the first
+// chunk of an item on a barrier of its own, which the producer waits on before it arrives on
+// the item's barrier), so before the CTA ends the producer can wait for the last phase it
+// armed on each of them: no copy is still landing in shared memory when the CTA exits, also
+// after a wait has given up.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -46,6 +50,7 @@ constexpr int kAStages = 2;
 constexpr uint32_t kChunkImg = 3u * kNT * 128u;      // one 64-tap chunk, hi or lo: 24 KB
 constexpr uint32_t kChunkBytes = 2u * kChunkImg;     // hi + lo: 48 KB
 constexpr uint32_t kSpin = 1u << 22;
+constexpr uint32_t kSpinStall = 1u << 12;            // RFD_DEBUG_STALL_TAPS: give up quickly
 
 enum {
     kBarAFull = 0,      // kAStages
@@ -57,7 +62,8 @@ enum {
     kBarQFull = 12,     // 2
     kBarQEmpty = 14,    // 2
     kBarDone = 16,
-    kNumBars = 17
+    kBarT0 = 17,        // 2: the first taps chunk of an item, per item buffer (producer only)
+    kNumBars = 19
 };
 
 struct TlArgs {
@@ -80,11 +86,13 @@ struct TlArgs {
     unsigned long long *count;
     uint32_t ystride;           // bytes per Y plane
     uint32_t qwin;              // halfs per q-window plane
+    uint32_t spin;              // polls before a wait gives up
+    uint32_t stall;             // RFD_DEBUG_STALL_TAPS: never copy the taps (tests the abort path)
 };
 
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t *abort_flag,
-                                         unsigned long long *count) {
-    for (uint32_t i = 0; i < kSpin; ++i) {
+                                         unsigned long long *count, uint32_t spin) {
+    for (uint32_t i = 0; i < spin; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
     }
@@ -158,6 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
             mbar_init(BAR(kBarUnused + b), 1);
             mbar_init(BAR(kBarQFull + b), 1);
             mbar_init(BAR(kBarQEmpty + b), 4);
+            mbar_init(BAR(kBarT0 + b), 1);
         }
         mbar_init(BAR(kBarDone), 1);
         s_misc[1] = 0u;
@@ -175,6 +184,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
             uint32_t ka = 0, li = 0;
             static_assert(kAStages == 2, "two A stages");
             int64_t held0 = -1, held1 = -1;      // taps-image offset each A stage holds (-1: none)
+            // phases armed so far on each barrier the copies complete on (for the final drain)
+            uint32_t q_armed[2] = {0u, 0u}, a_armed[2] = {0u, 0u}, t0_armed[2] = {0u, 0u};
             int64_t ti = it0 / A.n_tb, tb = it0 - ti * A.n_tb, prev = -1;
             TcTile T{};
             for (int64_t it = it0; it < it1; ++it, ++li, tb = (tb + 1 == A.n_tb) ? 0 : tb + 1, ti += (tb == 0)) {
@@ -184,39 +195,69 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                 }
                 // this item's q window, 256 + kpad samples of each plane
                 const uint32_t qb = li & 1u, use = li >> 1;
-                if (!wait_bar(BAR(kBarQEmpty + qb), (use & 1u) ^ 1u, abort_flag, A.count)) break;
+                if (!wait_bar(BAR(kBarQEmpty + qb), (use & 1u) ^ 1u, abort_flag, A.count, A.spin)) break;
                 const uint32_t wbytes = (uint32_t)(kN + T.kpad) * 2u;
                 mbar_arrive_expect_tx(BAR(kBarQFull + qb), 4u * wbytes);
+                ++q_armed[qb];
                 for (int p = 0; p < 4; ++p)
                     bulk_g2s(smem_u32(s_qw + (qb * 4u + (uint32_t)p) * A.qwin),
                              A.q + (int64_t)(4 * T.ref + p) * A.ld + wrap_pos(ubase, tb * kN, A.n), wbytes,
                              BAR(kBarQFull + qb));
+                if (A.stall) continue;            // no taps: the item's go barrier never completes
                 bool ok = true;
                 for (int c = 0; c < T.nch; ++c, ++ka) {
                     const uint32_t st = ka % kAStages, r = ka / kAStages;
-                    if (!wait_bar(BAR(kBarAEmpty + st), (r & 1u) ^ 1u, abort_flag, A.count)) {
+                    if (!wait_bar(BAR(kBarAEmpty + st), (r & 1u) ^ 1u, abort_flag, A.count, A.spin)) {
                         ok = false;
                         break;
                     }
-                    // chunk 0 completes on the item's go barrier, later chunks on the stage's
-                    const uint32_t full = c == 0 ? BAR(kBarGo + (li & 1u)) : BAR(kBarAFull + st);
+                    const uint32_t ib = li & 1u;
                     const int64_t want = T.taps_off + (int64_t)c * kChunkBytes;
                     if ((st == 0u ? held0 : held1) == want) {
                         // the stage already holds this chunk (a tile whose chunks all fit the
                         // stages, as at K <= 128): no copy, only the phase
-                        mbar_arrive(full);
+                        if (c == 0) {
+                            mbar_arrive(BAR(kBarGo + ib));
+                        } else {
+                            mbar_arrive(BAR(kBarAFull + st));
+                            ++a_armed[st];
+                        }
                         continue;
                     }
                     if (st == 0u)
                         held0 = want;
                     else
                         held1 = want;
+                    // chunk 0 completes on the item's own transaction barrier, later chunks on the stage's
+                    const uint32_t full = c == 0 ? BAR(kBarT0 + ib) : BAR(kBarAFull + st);
                     mbar_arrive_expect_tx(full, kChunkBytes);
                     const uint8_t *src = A.taps + want;
                     bulk_g2s(smem_u32(s_a + st * kChunkBytes), src, kChunkImg, full);
                     bulk_g2s(smem_u32(s_a + st * kChunkBytes) + kChunkImg, src + kChunkImg, kChunkImg, full);
+                    if (c == 0) {
+                        // landed, then the producer's share of the item's go barrier
+                        const uint32_t par = t0_armed[ib]++ & 1u;
+                        if (!wait_bar(BAR(kBarT0 + ib), par, abort_flag, A.count, A.spin)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive(BAR(kBarGo + ib));
+                    } else {
+                        ++a_armed[st];
+                    }
                 }
                 if (!ok) break;
+            }
+            // drain: the last phase armed on each copy barrier has completed (every copy landed)
+            // before this thread reaches the CTA's final barrier; bounded, like every wait
+            for (int b = 0; b < 2; ++b) {
+                const uint32_t bars3[3] = {BAR(kBarQFull + b), BAR(kBarAFull + b), BAR(kBarT0 + b)};
+                const uint32_t armed[3] = {q_armed[b], a_armed[b], t0_armed[b]};
+                for (int k = 0; k < 3; ++k) {
+                    if (armed[k] == 0u) continue;
+                    uint32_t i = 0;
+                    while (i < kSpin && !mbar_try_wait(bars3[k], (armed[k] - 1u) & 1u)) ++i;
+                }
             }
         }
     } else if (warp == 1) {
@@ -235,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                 }
                 const uint32_t acc = li & 1u, yb = li & 1u, use = li >> 1;
                 // one wait: the accumulator is free, Y is built and chunk 0 of the taps is staged
-                if (!go_seen && !wait_bar(BAR(kBarGo + acc), use & 1u, abort_flag, A.count)) break;
+                if (!go_seen && !wait_bar(BAR(kBarGo + acc), use & 1u, abort_flag, A.count, A.spin)) break;
                 go_seen = false;
                 fence_after();
                 const uint32_t d = tmem + acc * (uint32_t)kN;
@@ -245,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                     const uint32_t st = ka % kAStages;
                     if (c > 0) {
                         const uint32_t uf = st == 0u ? uf0++ : uf1++;
-                        if (!wait_bar(BAR(kBarAFull + st), uf & 1u, abort_flag, A.count)) {
+                        if (!wait_bar(BAR(kBarAFull + st), uf & 1u, abort_flag, A.count, A.spin)) {
                             ok = false;
                             break;
                         }
@@ -258,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                             // the next item's go barrier, waited on while this item's earlier
                             // MMAs still run (deadlock-free: it needs only work issued before)
                             const uint32_t nli = li + 1u;
-                            if (!wait_bar(BAR(kBarGo + (nli & 1u)), (nli >> 1) & 1u, abort_flag, A.count)) {
+                            if (!wait_bar(BAR(kBarGo + (nli & 1u)), (nli >> 1) & 1u, abort_flag, A.count, A.spin)) {
                                 ok = false;
                                 break;
                             }
@@ -305,8 +346,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
             }
             const uint32_t b2 = li & 1u, use = li >> 1;
             // Y buffer b2 is free once the MMAs of the item two back completed (its accumulator is full)
-            bool ok = wait_bar(BAR(kBarDFull + b2), (use & 1u) ^ 1u, abort_flag, A.count);
-            ok = ok && wait_bar(BAR(kBarQFull + b2), use & 1u, abort_flag, A.count);
+            bool ok = wait_bar(BAR(kBarDFull + b2), (use & 1u) ^ 1u, abort_flag, A.count, A.spin);
+            ok = ok && wait_bar(BAR(kBarQFull + b2), use & 1u, abort_flag, A.count, A.spin);
             if (!__all_sync(0xffffffffu, ok)) break;
             const int rows = kN - 8 + kpad;             // Y rows 0 .. 248 + kpad - 1
             uint8_t *y0 = s_y + b2 * 4u * A.ystride;
@@ -373,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                 thr_raw = valid ? A.thr / (sc * sc) * (1.0f - 0.0009765625f) : 0.f;
             }
             const uint32_t acc = li & 1u, use = li >> 1;
-            const bool ok = wait_bar(BAR(kBarDFull + acc), use & 1u, abort_flag, A.count);
+            const bool ok = wait_bar(BAR(kBarDFull + acc), use & 1u, abort_flag, A.count, A.spin);
             if (!__all_sync(0xffffffffu, ok)) break;
             fence_after();
             for (int cc = 0; cc < 4; ++cc) {
@@ -601,6 +642,8 @@ rfd_status tl_launch(const rfd_plan *plan, const void *q, const int32_t *qscale,
     a.count = (unsigned long long *)count;
     a.ystride = plan->tl_ystride;
     a.qwin = plan->tl_qwin;
+    a.stall = (plan->debug_flags & RFD_DEBUG_STALL_TAPS) ? 1u : 0u;
+    a.spin = a.stall ? kSpinStall : kSpin;
     const size_t shm = tl_smem_bytes(a.ystride, a.qwin);
     const unsigned grid = (unsigned)plan->tl_grid;
     static size_t smem_set[64][2] = {};

@@ -188,6 +188,30 @@ rfd_status rfd_search_run(rfd_search *S, void *stream, int64_t *n_trig_host) {
     return find_triggers_check(*S->host, S->plan->n_tmpl, S->cap, S->trig_cap, n_trig_host);
 }
 
+rfd_status rfd_search_run_host(rfd_search *S, const void *dtilde_host, rfd_trigger *trig_host,
+                               int64_t trig_host_capacity, void *stream, int64_t *n_trig_host) {
+    RFD_REQUIRE(S && dtilde_host && n_trig_host && (trig_host || trig_host_capacity == 0), RFD_ERR_ARG,
+                "NULL argument");
+    RFD_REQUIRE(trig_host_capacity >= 0, RFD_ERR_SHAPE, "negative trigger capacity");
+    RFD_TRY_CUDA(cudaSetDevice(S->plan->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t in_bytes = (size_t)S->plan->grid.nf * sizeof(float2);
+    RFD_TRY_CUDA(cudaMemcpyAsync((void *)S->d, dtilde_host, in_bytes, cudaMemcpyHostToDevice, s));
+    RFD_TRY_CUDA(cudaGraphLaunch(S->exec, s));
+    add_launches(S->kernels_per_run);
+    RFD_TRY_CUDA(cudaStreamSynchronize(s));
+    int64_t n = 0;
+    RFD_TRY(find_triggers_check(*S->host, S->plan->n_tmpl, S->cap, S->trig_cap, &n));
+    *n_trig_host = n;
+    RFD_REQUIRE(n <= trig_host_capacity, RFD_ERR_OVERFLOW, "search_run_host: %lld triggers, host capacity %lld",
+                (long long)n, (long long)trig_host_capacity);
+    if (n > 0) {
+        RFD_TRY_CUDA(cudaMemcpyAsync(trig_host, S->trig, (size_t)n * sizeof(rfd_trigger), cudaMemcpyDeviceToHost, s));
+        RFD_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    return RFD_OK;
+}
+
 int64_t rfd_search_kernels_per_run(const rfd_search *S) { return S ? S->kernels_per_run : 0; }
 
 static double elapsed(cudaEvent_t a, cudaEvent_t b) {

@@ -44,17 +44,35 @@ class GpuRun:
         torch.cuda.synchronize()
         return q, e, ld
 
-    def ratio_filter(self, taps, q, e, precision, halo, cand_cap=1 << 20, trig_cap=1 << 18, options=None):
+    def ratio_filter(self, taps, q, e, precision, halo, cand_cap=1 << 20, trig_cap=1 << 18, options=None,
+                     window=None, threshold=None):
         idx = taps["idx"]
+        W = self.cfg.window if window is None else window
+        thr = self.cfg.threshold if threshold is None else threshold
         plan = rfd.Plan(self.ctx, self.grid, self.bank.n_ref, self.bank.ref_of_tmpl[idx], taps["K"], precision,
-                        self.cfg.window, self.cfg.threshold, halo, options=options)
-        plan.set_taps(taps["taps"], taps["k_stride"], taps["lag"], taps["sigma"])
-        cand = torch.zeros(cand_cap * 24, dtype=torch.uint8, device="cuda")
-        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-        plan.ratio_filter_batch(q, e, cand, cnt)
-        trig = torch.zeros(trig_cap * 20, dtype=torch.uint8, device="cuda")
-        nt = rfd.find_triggers(self.ctx, len(idx), cand, cnt, trig)
-        out = rfd.triggers_to_numpy(trig, nt).copy()
-        ncand = int(cnt.item())
-        plan.close()
+                        W, thr, halo, options=options)
+        try:
+            plan.set_taps(taps["taps"], taps["k_stride"], taps["lag"], taps["sigma"])
+            cand = torch.zeros(cand_cap * 24, dtype=torch.uint8, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            plan.ratio_filter_batch(q, e, cand, cnt)
+            trig = torch.zeros(trig_cap * 20, dtype=torch.uint8, device="cuda")
+            nt = rfd.find_triggers(self.ctx, len(idx), cand, cnt, trig)
+            out = rfd.triggers_to_numpy(trig, nt).copy()
+            ncand = int(cnt.item())
+        finally:
+            plan.close()
         return out, ncand
+
+    def series(self, taps, q, e, precision, halo, options=None):
+        """The whole SNR series of every template through the production kernels: window 1 and
+        threshold 0 make every sample with |z|^2 > 0 its own trigger.  Returns complex z[J, n]
+        (zero where nothing was emitted) and the number of (j, t) emitted."""
+        J = len(taps["idx"])
+        cap = J * self.n + 1024
+        trig, ncand = self.ratio_filter(taps, q, e, precision, halo, cand_cap=cap, trig_cap=cap, options=options,
+                                        window=1, threshold=0.0)
+        z = np.zeros((J, self.n), dtype=np.complex128)
+        z[trig["j"].astype(np.int64), trig["t"].astype(np.int64)] = trig["zr"].astype(np.float64) + \
+            1j * trig["zi"].astype(np.float64)
+        return z, len(trig)

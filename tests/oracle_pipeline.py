@@ -20,6 +20,7 @@ class OracleRun:
         self.d = data32(data)
         self.psd = data.psd
         self._q = {}
+        self._design = {}
 
     def q_ref(self, r):
         if r not in self._q:
@@ -28,9 +29,13 @@ class OracleRun:
         return self._q[r]
 
     def design(self, j, K, with_match=True):
-        r = int(self.bank.ref_of_tmpl[j])
-        return ratio.design(self.cfg.fs, self.n, self.cfg.f_low, self.bank.params()[j], self.bank.ref_params()[r],
-                            self.psd, K, self.cfg.tukey_alpha, self.cfg.pn_flags, with_match=with_match)
+        key = (int(j), int(K), bool(with_match))
+        if key not in self._design:
+            r = int(self.bank.ref_of_tmpl[j])
+            self._design[key] = ratio.design(self.cfg.fs, self.n, self.cfg.f_low, self.bank.params()[j],
+                                             self.bank.ref_params()[r], self.psd, K, self.cfg.tukey_alpha,
+                                             self.cfg.pn_flags, with_match=with_match)
+        return self._design[key]
 
     def snr(self, j, out):
         r = int(self.bank.ref_of_tmpl[j])

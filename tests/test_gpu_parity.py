@@ -1,9 +1,15 @@
 """GPU parity: every C-ABI step against the FP64 oracle on the same seeded inputs.
 
-Tolerances (stated by the method's precision targets): SNR |z| within 1e-5 relative for the
-FP32 path; trigger (j, t) bit-exact except in windows the oracle marks ambiguous under that
-tolerance; lags bit-exact; sigma_eff and match within 1e-9 (FP64 on both sides); taps within
-the complex64 rounding of their FP64 values.
+Tolerances.  The method's targets: SNR |z| within 1e-3 relative on the tensor-core path and
+1e-5 on the FP32 path (TOL_TC, TOL_FP32).  Each arithmetic path also has a much tighter error
+bound EPS[precision] (relative |z| error at trigger samples; the full-series tests below
+measure the largest error over every sample of every template, relative to rms |z|, and the
+bounds sit about 2x above those measurements).  Every parity test asserts its triggers' |z|
+within EPS, and trigger (j, w, t) bit-exact except in windows the oracle flags ambiguous under
+EPS (a peak within 4 EPS of the threshold, or a runner-up within 4 EPS of the peak: the only
+windows an error within EPS can decide differently); at most 1 % of the oracle's trigger
+windows may be skipped that way.  Lags bit-exact; sigma_eff and match within 1e-9 (FP64 on
+both sides); taps within the complex64 rounding of their FP64 values.
 """
 import math
 
@@ -23,6 +29,19 @@ import paper_2601_18835_gb300 as rfd  # noqa: E402
 from tests.gpu_pipeline import GpuRun  # noqa: E402
 
 TOL_FP32 = 1e-5
+TOL_TC = 1e-3
+# error bounds of the arithmetic paths (relative |z| error), per plan precision
+EPS = {rfd.PREC_FP32: 2e-6, rfd.PREC_FP16X3: 2e-5, rfd.PREC_BF16X3: 2e-4}
+# full-series bounds: max |z_gpu - z_oracle| over a template's series / rms |z_oracle|.  Measured
+# on GB300 over C1 and the ragged bank (the largest over the kernels of each precision): FP32
+# 3.2e-6 (direct FIR) / 2.6e-6 (block FFT); FP16x3 5.3e-6; BF16x3 1.8e-4 (its hi + lo split keeps
+# about 16 significant bits, so it is the precision whose band is widest)
+EPS_SERIES = {rfd.PREC_FP32: 8e-6, rfd.PREC_FP16X3: 1.2e-5, rfd.PREC_BF16X3: 4e-4}
+
+
+def amb_cap(n_or):
+    """Ambiguous windows allowed: 1 % of the oracle's trigger windows, rounded up."""
+    return int(math.ceil(0.01 * n_or))
 
 
 @pytest.fixture(scope="module")
@@ -35,9 +54,10 @@ def ctx():
 
 
 def compare_triggers(gpu_trig, oracle_sets, tol, js, W):
-    """gpu_trig: structured array (j, t, snr2, zr, zi); oracle_sets: {j: (triggers, ambiguous)}.
-    Every non-ambiguous window must agree in (j, w, t) and in |z| within tol.  Returns the
-    number of ambiguous windows skipped."""
+    """gpu_trig: structured array (j, t, snr2, zr, zi); oracle_sets: {j: (triggers, ambiguous)}
+    with the ambiguity flags taken under the path's error bound.  Every non-ambiguous window
+    must agree in (j, w, t) and in |z| within tol.  Returns the number of ambiguous windows
+    skipped."""
     n_amb = 0
     for j in js:
         ot, amb = oracle_sets[j]
@@ -170,9 +190,10 @@ def test_c1_triggers_fp32(c1):
     sets = {}
     for j in range(bank.n_tmpl):
         o = ora.design(j, cfg.k, with_match=False)
-        sets[j] = ora.triggers(ora.snr(j, o), TOL_FP32)
+        sets[j] = ora.triggers(ora.snr(j, o), EPS[rfd.PREC_FP32])
     n_amb = compare_triggers(trig, sets, TOL_FP32, range(bank.n_tmpl), cfg.window)
-    assert n_amb <= 2
+    assert n_amb <= amb_cap(n_oracle(sets, range(bank.n_tmpl)))
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < EPS[rfd.PREC_FP32]
     # the injected template fires at the injected sample
     m0, snr, phi, slot = data.injections[0]
     hit = trig[(trig["j"] == slot)]
@@ -189,8 +210,10 @@ def test_c1_findchirp_matches_oracle(c1):
     trig = torch.zeros(cap * 20, dtype=torch.uint8, device="cuda")
     nt = rfd.find_triggers(gpu.ctx, bank.n_tmpl, cand, cnt, trig)
     tr = rfd.triggers_to_numpy(trig, nt)
-    sets = {j: ora.triggers(ora.findchirp(j), TOL_FP32) for j in range(bank.n_tmpl)}
-    assert compare_triggers(tr, sets, TOL_FP32, range(bank.n_tmpl), cfg.window) <= 2
+    sets = {j: ora.triggers(ora.findchirp(j), EPS[rfd.PREC_FP32]) for j in range(bank.n_tmpl)}
+    assert compare_triggers(tr, sets, TOL_FP32, range(bank.n_tmpl), cfg.window) <= amb_cap(
+        n_oracle(sets, range(bank.n_tmpl)))
+    assert snr_errors(tr, sets, range(bank.n_tmpl)) < EPS[rfd.PREC_FP32]
 
 
 def test_ratio_peak_within_one_percent_of_findchirp_gpu(c1):
@@ -230,10 +253,12 @@ def test_ragged_bank_uneven_taps_and_window(ctx):
     for j in range(bank.n_tmpl):
         o = ora.design(j, int(K[j]), with_match=False)
         assert lag[j] == o["lag"]
-        sets[j] = ora.triggers(ora.snr(j, o), TOL_FP32)
-    assert sum(len(s[0]) for s in sets.values()) > 1000
+        sets[j] = ora.triggers(ora.snr(j, o), EPS[rfd.PREC_FP32])
+    n_or = n_oracle(sets, range(bank.n_tmpl))
+    assert n_or > 1000
     n_amb = compare_triggers(trig, sets, TOL_FP32, range(bank.n_tmpl), cfg.window)
-    assert n_amb <= 10
+    assert n_amb <= amb_cap(n_or)
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < EPS[rfd.PREC_FP32]
 
 
 def test_candidate_overflow_is_reported(c1):
@@ -280,16 +305,15 @@ def test_c2_full_size_fp32_sampled(ctx):
         assert abs(sig[j] / o["sigma_eff"] - 1) < 1e-9
         assert abs(mat[j] - o["match"]) < 1e-8
         z = ora.snr(j, o)
-        sets[j] = ora.triggers(z, TOL_FP32)
+        sets[j] = ora.triggers(z, EPS[rfd.PREC_FP32])
         g = trig[trig["j"] == j]
         if len(g):
             zo = ora.snr_at(j, o, g["t"].astype(np.int64))
-            assert np.max(np.abs(np.sqrt(g["snr2"]) - np.abs(zo)) / np.abs(zo)) < TOL_FP32
-    assert compare_triggers(trig, sets, TOL_FP32, sample, cfg.window) <= 2
+            assert np.max(np.abs(np.sqrt(g["snr2"]) - np.abs(zo)) / np.abs(zo)) < EPS[rfd.PREC_FP32]
+    assert compare_triggers(trig, sets, TOL_FP32, sample, cfg.window) <= amb_cap(n_oracle(sets, sample))
 
 
 # --------------------------------------------------------------------------- tensor-core path
-TOL_TC = 1e-3
 TC_PRECISIONS = [("fp16x3", 1), ("bf16x3", 2)]
 # the two tensor-core kernels: time on M with templates on N (K <= 64 by default), and
 # templates on M with time on N (the long-tap kernel, K > 64 by default), each forced for all;
@@ -298,15 +322,22 @@ TC_KERNELS = [("time_on_m", {"long_k": 512}), ("templates_on_m", {"long_k": 0}),
 
 
 def snr_errors(trig, sets, js):
-    """Largest relative |z| error over the GPU triggers that the oracle also has (same t)."""
+    """Largest relative error over the GPU triggers that the oracle also has (same t): of |z|,
+    and of the complex z."""
     worst = 0.0
     for j in js:
         o_by_t = {x["t"]: x for x in sets[j][0]}
         for r in trig[trig["j"] == j]:
             x = o_by_t.get(int(r["t"]))
             if x is not None:
-                worst = max(worst, abs(math.sqrt(float(r["snr2"])) / abs(x["z"]) - 1.0))
+                za = abs(x["z"])
+                zg = complex(float(r["zr"]), float(r["zi"]))
+                worst = max(worst, abs(math.sqrt(float(r["snr2"])) / za - 1.0), 0.5 * abs(zg - x["z"]) / za)
     return worst
+
+
+def n_oracle(sets, js):
+    return sum(len(sets[j][0]) for j in js)
 
 
 @pytest.mark.parametrize("kernel,opts", TC_KERNELS)
@@ -320,10 +351,10 @@ def test_c1_triggers_tensor_core(c1, name, prec, kernel, opts):
     sets = {}
     for j in range(bank.n_tmpl):
         o = ora.design(j, cfg.k, with_match=False)
-        sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
+        sets[j] = ora.triggers(ora.snr(j, o), EPS[prec])
     n_amb = compare_triggers(trig, sets, TOL_TC, range(bank.n_tmpl), cfg.window)
-    assert n_amb <= 4
-    assert snr_errors(trig, sets, range(bank.n_tmpl)) < (2e-5 if prec == 1 else 2e-4)
+    assert n_amb <= amb_cap(n_oracle(sets, range(bank.n_tmpl)))
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < EPS[prec]
 
 
 @pytest.mark.parametrize("kernel,opts", TC_KERNELS)
@@ -342,12 +373,11 @@ def test_ragged_bank_tensor_core(ctx, name, prec, kernel, opts):
     sets = {}
     for j in range(bank.n_tmpl):
         o = ora.design(j, int(K[j]), with_match=False)
-        sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
-    n_or = sum(len(s[0]) for s in sets.values())
+        sets[j] = ora.triggers(ora.snr(j, o), EPS[prec])
+    n_or = n_oracle(sets, range(bank.n_tmpl))
     assert n_or > 1000
-    # at threshold 6 many windows sit within the 4 tol band; every other window must agree
-    assert compare_triggers(trig, sets, TOL_TC, range(bank.n_tmpl), cfg.window) <= 0.05 * n_or
-    assert snr_errors(trig, sets, range(bank.n_tmpl)) < (2e-5 if prec == 1 else 2e-4)
+    assert compare_triggers(trig, sets, TOL_TC, range(bank.n_tmpl), cfg.window) <= amb_cap(n_or)
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < EPS[prec]
 
 
 @pytest.mark.parametrize("name,prec", TC_PRECISIONS[:1])
@@ -366,11 +396,11 @@ def test_long_taps_tensor_core(ctx, name, prec):
     sets = {}
     for j in js:
         o = ora.design(j, int(K[j]), with_match=False)
-        sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
-    n_or = sum(len(sets[j][0]) for j in js)
+        sets[j] = ora.triggers(ora.snr(j, o), EPS[prec])
+    n_or = n_oracle(sets, js)
     assert n_or > 100
-    assert compare_triggers(trig, sets, TOL_TC, js, cfg.window) <= 0.05 * n_or
-    assert snr_errors(trig, sets, js) < 2e-5
+    assert compare_triggers(trig, sets, TOL_TC, js, cfg.window) <= amb_cap(n_or)
+    assert snr_errors(trig, sets, js) < EPS[prec]
 
 
 def test_block_fft_fp32_c1_and_ragged(ctx, c1):
@@ -381,10 +411,11 @@ def test_block_fft_fp32_c1_and_ragged(ctx, c1):
     halo = cfg.k - 1
     q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP32)
     trig, _ = gpu.ratio_filter(t, q, e, rfd.PREC_FP32, halo, options={"fft_k": 0})
-    sets = {j: ora.triggers(ora.snr(j, ora.design(j, cfg.k, with_match=False)), TOL_FP32)
+    sets = {j: ora.triggers(ora.snr(j, ora.design(j, cfg.k, with_match=False)), EPS[rfd.PREC_FP32])
             for j in range(bank.n_tmpl)}
-    assert compare_triggers(trig, sets, TOL_FP32, range(bank.n_tmpl), cfg.window) <= 2
-    assert snr_errors(trig, sets, range(bank.n_tmpl)) < 2e-6
+    assert compare_triggers(trig, sets, TOL_FP32, range(bank.n_tmpl), cfg.window) <= amb_cap(
+        n_oracle(sets, range(bank.n_tmpl)))
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < EPS[rfd.PREC_FP32]
     cfg = workload.small_config(1, n_tmpl=37, window=37, threshold=6.0)
     bank, data = workload.make_workload(cfg)
     rng = np.random.default_rng(7)
@@ -394,12 +425,12 @@ def test_block_fft_fp32_c1_and_ragged(ctx, c1):
     halo = int(K.max()) - 1
     q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP32)
     trig, _ = gpu.ratio_filter(t, q, e, rfd.PREC_FP32, halo, cand_cap=1 << 22, options={"fft_k": 0})
-    sets = {j: ora.triggers(ora.snr(j, ora.design(j, int(K[j]), with_match=False)), TOL_FP32)
+    sets = {j: ora.triggers(ora.snr(j, ora.design(j, int(K[j]), with_match=False)), EPS[rfd.PREC_FP32])
             for j in range(bank.n_tmpl)}
-    n_or = sum(len(s[0]) for s in sets.values())
+    n_or = n_oracle(sets, range(bank.n_tmpl))
     assert n_or > 1000
-    assert compare_triggers(trig, sets, TOL_FP32, range(bank.n_tmpl), cfg.window) <= 0.01 * n_or
-    assert snr_errors(trig, sets, range(bank.n_tmpl)) < 2e-6
+    assert compare_triggers(trig, sets, TOL_FP32, range(bank.n_tmpl), cfg.window) <= amb_cap(n_or)
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < EPS[rfd.PREC_FP32]
 
 
 def test_block_fft_next_to_tensor_cores(ctx):
@@ -415,11 +446,40 @@ def test_block_fft_next_to_tensor_cores(ctx):
     q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP16X3)
     trig, _ = gpu.ratio_filter(t, q, e, rfd.PREC_FP16X3, halo, cand_cap=1 << 22, options={"fft_k": 256})
     js = list(range(0, bank.n_tmpl, 4))
-    sets = {j: ora.triggers(ora.snr(j, ora.design(j, int(K[j]), with_match=False)), TOL_TC) for j in js}
-    n_or = sum(len(sets[j][0]) for j in js)
+    sets = {j: ora.triggers(ora.snr(j, ora.design(j, int(K[j]), with_match=False)), EPS[rfd.PREC_FP16X3])
+            for j in js}
+    n_or = n_oracle(sets, js)
     assert n_or > 100
-    assert compare_triggers(trig, sets, TOL_TC, js, cfg.window) <= 0.05 * n_or
-    assert snr_errors(trig, sets, js) < 2e-5
+    assert compare_triggers(trig, sets, TOL_TC, js, cfg.window) <= amb_cap(n_or)
+    assert snr_errors(trig, sets, js) < EPS[rfd.PREC_FP16X3]
+
+
+@pytest.mark.parametrize("name,prec", TC_PRECISIONS)
+def test_last_partial_tile_on_block_fft(ctx, name, prec):
+    """fft_rem: 75 templates of one reference fill one 64-template tile of the long-tap kernel
+    and leave 11, which go to the block-FFT kernel (fft_rem = 16) instead of a padded tile; both
+    parts of the call match the oracle, and the plan keeps every template exactly once."""
+    cfg = workload.small_config(1, n_tmpl=75, threshold=9.0)
+    bank, data = workload.make_workload(cfg)
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    q, e, _ = gpu.filter_reference(halo, prec)
+    trig, _ = gpu.ratio_filter(t, q, e, prec, halo, options={"long_k": 0, "fft_rem": 16})
+    sets = {j: ora.triggers(ora.snr(j, ora.design(j, cfg.k, with_match=False)), EPS[prec])
+            for j in range(bank.n_tmpl)}
+    n_or = n_oracle(sets, range(bank.n_tmpl))
+    assert n_or > 20
+    assert compare_triggers(trig, sets, TOL_TC, range(bank.n_tmpl), cfg.window) <= amb_cap(n_or)
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < EPS[prec]
+    # the last 11 templates of the (stable, equal-K) order, 64..74, ran on the block-FFT kernel:
+    # their values (FP32 transforms) differ from the tensor cores' in the last bits; every other
+    # template's triggers are bit-identical to the plan without fft_rem
+    trig_tc, _ = gpu.ratio_filter(t, q, e, prec, halo, options={"long_k": 0})
+    a = {(int(x["j"]), int(x["t"]) // cfg.window): x for x in trig}
+    b = {(int(x["j"]), int(x["t"]) // cfg.window): x for x in trig_tc}
+    diff_j = {key[0] for key in set(a) | set(b) if key not in a or key not in b or a[key].tobytes() != b[key].tobytes()}
+    assert diff_j and diff_j <= set(range(64, 75))
 
 
 @pytest.mark.slow
@@ -439,12 +499,12 @@ def test_c2_full_size_tensor_core_sampled(ctx, name, prec):
     sets = {}
     for j in sample:
         o = ora.design(j, cfg.k, with_match=False)
-        sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
+        sets[j] = ora.triggers(ora.snr(j, o), EPS[prec])
         g = trig[trig["j"] == j]
         if len(g):
             zo = ora.snr_at(j, o, g["t"].astype(np.int64))
-            assert np.max(np.abs(np.sqrt(g["snr2"]) - np.abs(zo)) / np.abs(zo)) < TOL_TC
-    assert compare_triggers(trig, sets, TOL_TC, sample, cfg.window) <= 4
+            assert np.max(np.abs(np.sqrt(g["snr2"]) - np.abs(zo)) / np.abs(zo)) < EPS[prec]
+    assert compare_triggers(trig, sets, TOL_TC, sample, cfg.window) <= amb_cap(n_oracle(sets, sample))
 
 
 @pytest.mark.slow
@@ -466,14 +526,14 @@ def test_c5_grid_long_taps_sampled(ctx):
     checked = 0
     for j in sample:
         o = ora.design(j, cfg.k, with_match=False)
-        sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
+        sets[j] = ora.triggers(ora.snr(j, o), EPS[rfd.PREC_FP16X3])
         g = trig[trig["j"] == j]
         if len(g):
             zo = ora.snr_at(j, o, g["t"].astype(np.int64))
-            assert np.max(np.abs(np.sqrt(g["snr2"]) - np.abs(zo)) / np.abs(zo)) < TOL_TC
+            assert np.max(np.abs(np.sqrt(g["snr2"]) - np.abs(zo)) / np.abs(zo)) < EPS[rfd.PREC_FP16X3]
             checked += len(g)
     assert checked > 0
-    assert compare_triggers(trig, sets, TOL_TC, sample, cfg.window) <= 4
+    assert compare_triggers(trig, sets, TOL_TC, sample, cfg.window) <= amb_cap(n_oracle(sets, sample))
 
 
 # --------------------------------------------------------------------------- bucketed K (C3 shape)
@@ -506,17 +566,96 @@ def test_bucketed_taps_and_uneven_k_tensor_core(ctx):
         o = ora.design(j, int(K[j]), with_match=False)
         assert lag_h[j] == o["lag"], (j, lag_h[j], o["lag"])
         assert abs(sig_h[j] / o["sigma_eff"] - 1) < 1e-9
-        sets[j] = ora.triggers(ora.snr(j, o), TOL_TC)
+        sets[j] = ora.triggers(ora.snr(j, o), EPS[rfd.PREC_FP16X3])
     assert len(set(K.tolist())) >= 2                     # the bank really is uneven
     t = {"taps": taps, "lag": lag, "sigma": sig, "K": K.astype(np.int32), "k_stride": 512, "idx": np.arange(J)}
     q, e, _ = gpu.filter_reference(511, rfd.PREC_FP16X3)
     trig, ncand = gpu.ratio_filter(t, q, e, rfd.PREC_FP16X3, 511, cand_cap=1 << 22)
-    n_or = sum(len(s[0]) for s in sets.values())
+    n_or = n_oracle(sets, range(J))
     assert n_or > 50
-    # heavy templates sample slowly varying |z|: many peaks have a runner-up within 4 tol, and
-    # those windows are ambiguous by the rule; every other window must agree exactly
-    assert compare_triggers(trig, sets, TOL_TC, range(J), cfg.window) <= 0.5 * n_or
-    assert snr_errors(trig, sets, range(J)) < 2e-5
+    assert compare_triggers(trig, sets, TOL_TC, range(J), cfg.window) <= amb_cap(n_or)
+    assert snr_errors(trig, sets, range(J)) < EPS[rfd.PREC_FP16X3]
+
+
+# --------------------------------------------------------------------------- bounded waits
+@pytest.mark.parametrize("kernel,opts", [("templates_on_m", {"long_k": 0}), ("time_on_m", {"long_k": 512})])
+def test_bounded_wait_gives_up_and_the_context_stays_usable(c1, kernel, opts):
+    """RFD_DEBUG_STALL_TAPS makes the tensor-core kernel never copy its taps, so the MMA
+    thread's wait for them runs out (a short limit): the call reports RFD_ERR_TIMEOUT, every
+    copy the producer did issue has landed before the CTAs end, and a normal call on the same
+    context then succeeds and matches the oracle."""
+    from paper_2601_18835_gb300 import _native
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP16X3)
+    for _ in range(2):
+        with pytest.raises(rfd.RfdError) as ei:
+            gpu.ratio_filter(t, q, e, rfd.PREC_FP16X3, halo, options=dict(opts, debug_flags=_native.DEBUG_STALL_TAPS))
+        assert ei.value.status == _native.RFD_ERR_TIMEOUT
+    torch.cuda.synchronize()
+    trig, _ = gpu.ratio_filter(t, q, e, rfd.PREC_FP16X3, halo, options=opts)
+    sets = {j: ora.triggers(ora.snr(j, ora.design(j, cfg.k, with_match=False)), EPS[rfd.PREC_FP16X3])
+            for j in range(bank.n_tmpl)}
+    assert n_oracle(sets, range(bank.n_tmpl)) > 0
+    assert compare_triggers(trig, sets, TOL_TC, range(bank.n_tmpl), cfg.window) <= amb_cap(
+        n_oracle(sets, range(bank.n_tmpl)))
+    assert snr_errors(trig, sets, range(bank.n_tmpl)) < EPS[rfd.PREC_FP16X3]
+
+
+# --------------------------------------------------------------------------- full series (Eq. 3)
+# every kernel family in every precision: the FP32 CUDA-core FIR and the block-FFT kernel on an
+# FP32 plan, and the three split-precision kernels (time on M, templates on M, block FFT)
+SERIES_CASES = ([("fp32_direct", rfd.PREC_FP32, {}), ("fp32_block_fft", rfd.PREC_FP32, {"fft_k": 0})]
+                + [("%s_%s" % (k, n), p, o) for (k, o) in TC_KERNELS for (n, p) in TC_PRECISIONS])
+
+
+def series_error(ora, gpu, t, K, prec, opts, halo):
+    """The GPU's whole SNR series (window 1, threshold 0: every sample is emitted) against the
+    oracle's Eq. 3 series, template by template.  Returns the largest
+    max_t |z_gpu[t] - z_oracle[t]| / rms_t |z_oracle|."""
+    q, e, _ = gpu.filter_reference(halo, prec)
+    zg, count = gpu.series(t, q, e, prec, halo, options=opts)
+    worst, n_valid = 0.0, 0
+    for j in range(len(K)):
+        o = ora.design(j, int(K[j]), with_match=False)
+        if o["sigma_eff"] == 0:
+            assert not np.any(zg[j]), j          # all-zero taps (a 2-tap Tukey window): no output
+            continue
+        n_valid += 1
+        zo = ora.snr(j, o)
+        rms = np.sqrt(np.mean(np.abs(zo) ** 2))
+        worst = max(worst, float(np.max(np.abs(zg[j] - zo)) / rms))
+    assert count == n_valid * gpu.n              # every sample of every template, once
+    return worst
+
+
+@pytest.mark.parametrize("label,prec,opts", SERIES_CASES)
+def test_full_series_c1(c1, label, prec, opts):
+    """C1 (64 templates, K = 64): the whole series of every template."""
+    cfg, bank, data, ora, gpu = c1
+    t = gpu.make_taps(cfg.k, match=False)
+    worst = series_error(ora, gpu, t, t["K"], prec, opts, cfg.k - 1)
+    print("full series C1 %s: max |dz| / rms |z| = %.3g" % (label, worst))
+    assert worst <= (TOL_FP32 if prec == rfd.PREC_FP32 else TOL_TC)
+    assert worst <= EPS_SERIES[prec]
+
+
+@pytest.mark.parametrize("label,prec,opts", SERIES_CASES)
+def test_full_series_ragged(ctx, label, prec, opts):
+    """37 templates (a ragged last tile), K from 2 to 96 (tiles padded to 16-tap steps; K = 2
+    has all-zero Tukey taps): the whole series of every template."""
+    cfg = workload.small_config(1, n_tmpl=37, window=37, threshold=6.0)
+    bank, data = workload.make_workload(cfg)
+    rng = np.random.default_rng(7)
+    K = (2 * rng.integers(1, 49, size=bank.n_tmpl)).astype(np.int32)
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(K, k_stride=128, match=False)
+    halo = int(((K.max() + 15) // 16) * 16) - 1
+    worst = series_error(ora, gpu, t, K, prec, opts, halo)
+    print("full series ragged %s: max |dz| / rms |z| = %.3g" % (label, worst))
+    assert worst <= (TOL_FP32 if prec == rfd.PREC_FP32 else TOL_TC)
+    assert worst <= EPS_SERIES[prec]
 
 
 # --------------------------------------------------------------------------- graph and autotuner
@@ -733,7 +872,7 @@ def test_autotuner_choices_give_identical_triggers(ctx, tmp_path):
     # and samples, |z| within the tensor-core tolerance
     base = results[0].view(rfd.TRIGGER_DTYPE)
     for c, r in zip(rep["candidates"][1:], results[1:]):
-        if "fft_k" not in c["options"]:
+        if "fft_k" not in c["options"] and "fft_rem" not in c["options"]:
             assert np.array_equal(r, results[0])
             continue
         got = r.view(rfd.TRIGGER_DTYPE)

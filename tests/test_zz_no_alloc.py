@@ -74,3 +74,40 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
     with pytest.raises(rfd.RfdError) as ei:
         rfd.find_triggers_noalloc(4, big, cnt, trig)
     assert ei.value.status == _native.RFD_ERR_SHAPE
+
+
+def test_noalloc_allocates_nothing_and_leaves_no_stale_state():
+    """After a first call has loaded the module (set-up), a further call changes the device's
+    free memory by nothing; and a call with fewer templates and candidates than the call
+    before it (so the static array still holds the larger call's words past its own) equals
+    the allocating entry point on the same list."""
+    from tests.test_gpu_triggers import synthetic_candidates
+    ctx = rfd.Context(0)
+    W = 37
+    outs = []
+    for seed, n_tmpl in ((5, 60), (6, 12)):
+        rng = np.random.default_rng(seed)
+        recs = synthetic_candidates(rng, n_tmpl, W)
+        cand = np.zeros(len(recs), dtype=rfd.CANDIDATE_DTYPE)
+        for i, (j, t, p) in enumerate(recs):
+            cand[i]["key"] = (int(np.float32(p).view(np.uint32)) << 32) | (0xFFFFFFFF - t)
+            cand[i]["j"], cand[i]["w"], cand[i]["zr"], cand[i]["zi"] = j, t // W, np.sqrt(p), t
+        cd = torch.from_numpy(cand.view(np.uint8).copy()).cuda()
+        cnt = torch.tensor([len(recs)], dtype=torch.int64, device="cuda")
+        ref_buf = torch.zeros((1 << 16) * 20, dtype=torch.uint8, device="cuda")
+        n_ref = rfd.find_triggers(ctx, n_tmpl, cd, cnt, ref_buf)
+        na_buf = torch.full(((1 << 16) * 20,), 0xAB, dtype=torch.uint8, device="cuda")
+        n_first = rfd.find_triggers_noalloc(n_tmpl, cd, cnt, na_buf)     # right after the other list
+        assert n_first == n_ref
+        assert np.array_equal(ref_buf[: n_ref * 20].cpu().numpy(), na_buf[: n_first * 20].cpu().numpy())
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        na_buf.fill_(0xAB)
+        n_na = rfd.find_triggers_noalloc(n_tmpl, cd, cnt, na_buf)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert n_na == n_ref
+        assert np.array_equal(ref_buf[: n_ref * 20].cpu().numpy(), na_buf[: n_na * 20].cpu().numpy())
+        outs.append(n_ref)
+    assert outs[1] < outs[0]
+    ctx.close()
