@@ -156,15 +156,15 @@ def ratio_fir_at(q_ref, rho, s, t):
 # ---------------------------------------------------------------- normalisation (Eqs. 5-6)
 def autocorrelation(h_ref, psd, df, n, max_lag):
     """C_r[l] for l = -max_lag .. max_lag (index l + max_lag): the reference's
-    autocorrelation (h_ref|h_ref)(t) of Eq. 6 on the sample grid."""
+    autocorrelation (h_ref|h_ref)(t) of Eq. 6 on the sample grid,
+    C_r[l] = sum_k w_k exp(+2 pi i k l / n), w_k = 4 df |h_ref,k|^2 / S_k, which is n times
+    the inverse DFT of w at l (numpy's FFT as the library step)."""
+    w = np.zeros(n, dtype=np.complex128)
     nz = np.nonzero(h_ref)[0]
-    wgt = 4.0 * df * np.abs(h_ref[nz]) ** 2 / psd[nz]
+    w[nz] = 4.0 * df * np.abs(h_ref[nz]) ** 2 / psd[nz]
+    full = np.fft.ifft(w) * n
     lags = np.arange(-max_lag, max_lag + 1)
-    out = np.empty(len(lags), dtype=np.complex128)
-    for i0 in range(0, len(lags), 16):          # a few lags at a time bounds the memory
-        ph = np.exp(2j * math.pi * np.outer(lags[i0:i0 + 16], nz) / n)
-        out[i0:i0 + 16] = ph @ wgt
-    return out
+    return full[lags % n]
 
 
 def sigma_eff_sq_parseval(rho, C):

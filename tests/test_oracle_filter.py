@@ -219,3 +219,20 @@ def test_streaming_windows_tile_the_series(rng):
         win = np.array([np.sum(rho[::-1] * q[(uu + np.arange(K)) % n]) for uu in u[:8]])
         assert np.allclose(win, direct[t[:8]], rtol=1e-12, atol=1e-12)
     assert np.all(seen == 1)
+
+
+def test_autocorrelation_equals_its_defining_sum(rng):
+    """C_r[l] = sum_k 4 df |h_k|^2 / S_k exp(+2 pi i k l / n) (Eq. 6 on the sample grid),
+    summed term by term for every lag, against the oracle's inverse-FFT evaluation."""
+    from oracle import ratio, waveform as wf
+    fs, n, f_low = 1024.0, 4096, 30.0
+    df = fs / n
+    h = wf.template(fs, n, f_low, (1.4, 1.3, 0, 0, 0))
+    f = np.arange(n // 2 + 1) * df
+    psd = 1.0 + (f / 200.0) ** 2 + rng.uniform(0.0, 0.1, len(f))
+    C = ratio.autocorrelation(h, psd, df, n, 100)
+    k = np.nonzero(h)[0]
+    wgt = 4.0 * df * np.abs(h[k]) ** 2 / psd[k]
+    for i, l in enumerate(range(-100, 101)):
+        direct = np.sum(wgt * np.exp(2j * np.pi * k * l / n))
+        assert abs(C[i] - direct) <= 1e-12 * np.sum(wgt)
