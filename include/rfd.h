@@ -205,7 +205,10 @@ rfd_status rfd_make_taps_at_lag(rfd_ctx *ctx, const rfd_grid *grid, const double
  *     element offset (4 r + p) ld, p = 0 re_hi, 1 im_hi, 2 re_lo, 3 im_lo, with
  *     hi = round(x 2^e_r), lo = round(x 2^e_r - hi).
  * qscale_dev int32 [n_ref] receives e_r (0 for FP32); e_r puts the rms of the scaled series
- *   near 2^8.  Deterministic: no atomics in any floating-point reduction. */
+ *   near 2^8, lowered where needed so that the largest component of the scaled series is at
+ *   most 2^14 (a very loud sample cannot overflow the FP16 hi part).  Deterministic: the
+ *   floating-point reductions run in a fixed order (the largest component is an integer
+ *   maximum over float bits, exact in any order). */
 rfd_status rfd_filter_reference(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev,
                                 const double *psd_dev, const void *href_dev, int32_t n_ref,
                                 int32_t halo, int32_t precision, void *qref_dev,
@@ -304,6 +307,14 @@ rfd_status rfd_ratio_filter_window(rfd_plan *plan, const void *qref_dev, const i
 
 /* Tensor-core (or FMA) flops one rfd_ratio_filter_batch call of this plan executes. */
 double rfd_plan_executed_flops(const rfd_plan *plan);
+/* Which kernel filters each template of the plan: kernel_host int32 [n_tmpl] receives
+ * RFD_KERNEL_FP32 (CUDA-core direct FIR), RFD_KERNEL_TC_TIME_ON_M / _TC_TEMPLATES_ON_M (the
+ * two tensor-core contractions) or RFD_KERNEL_BLOCK_FFT (overlap-save blocks).  Host only. */
+#define RFD_KERNEL_FP32 0
+#define RFD_KERNEL_TC_TIME_ON_M 1
+#define RFD_KERNEL_TC_TEMPLATES_ON_M 2
+#define RFD_KERNEL_BLOCK_FFT 3
+rfd_status rfd_plan_template_kernels(const rfd_plan *plan, int32_t *kernel_host);
 
 /* ------------------------------------------------------------------ find_triggers
  * Merges candidates into triggers: per (j, w) the maximum key (the largest |z|^2, ties to the
@@ -394,7 +405,11 @@ rfd_status rfd_find_triggers_noalloc(int32_t n_tmpl, const rfd_candidate *cand_d
  * per template, c = 4 df d conj(h_j) / S, an n-point FP32 Stockham inverse FFT,
  * z = q / sigma(h_j), and the same threshold / window reduction into candidates as
  * rfd_ratio_filter_batch.  h_dev complex64 [n_tmpl][n/2+1] holds the templates (written by
- * rfd_gen_templates once per bank).  The comparison path for the ratio filter. */
+ * rfd_gen_templates once per bank).  The comparison path for the ratio filter.  Two kernels
+ * per batch of templates: the product 4 df d conj(h_j) / S is formed inside the first pass
+ * of the two-pass inverse FFT (the zero upper half of the spectrum is never read) and the
+ * threshold / window maximum runs inside the last pass (the series is never stored);
+ * n in [2^12, 2^22]. */
 rfd_status rfd_findchirp(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev,
                          const double *psd_dev, const void *h_dev, int32_t n_tmpl,
                          int32_t window, float threshold, rfd_candidate *cand_dev,
@@ -512,6 +527,18 @@ rfd_status rfd_mlp_grads(rfd_mlp *mlp, const void *feat_dev, const void *target_
  * gave up a bounded wait. */
 rfd_status rfd_mlp_state(rfd_mlp *mlp, float *loss_host, int32_t *step_host,
                          float *loss_scale_host, void *stream);
+/* Checkpoint of the networks' training state (the paper has no training code to resume;
+ * this makes training restartable): rfd_mlp_save writes, after the stream's work, the FP32
+ * master weights, Adam's moments, the normalisation, the lags, the optimiser state (Adam step,
+ * dynamic loss scale and its clean-step count) and the references' autocorrelations to
+ * `path`: an 8-byte magic, a little-endian uint64 header length, a JSON header naming each
+ * section (dtype, shape, offset, bytes), then the raw sections, 64-byte aligned.
+ * rfd_mlp_load reads such a file into a network object created for the same grid, PSD and
+ * references (checked: the grid, the counts and the autocorrelations bit for bit, else
+ * RFD_ERR_ARG / RFD_ERR_SHAPE) and rebuilds the FP16 operand copies from the masters, so that
+ * training continues exactly as it would have without the save.  Both synchronise. */
+rfd_status rfd_mlp_save(rfd_mlp *mlp, const char *path, void *stream);
+rfd_status rfd_mlp_load(rfd_mlp *mlp, const char *path, void *stream);
 /* Surrogate taps of n templates: taps_dev complex64 [n][k_stride] (k_stride >= 128, taps
  * 128.. zero), lag_dev int32 [n] (the network's lag), sigma_dev float64 [n] (sigma_eff of
  * the stored taps, Eqs. 5-6).  The outputs are what rfd_plan_set_taps takes.  Synchronises

@@ -205,6 +205,13 @@ class Plan:
         self.ctx = ctx
         self.n_tmpl = len(ro)
 
+    def template_kernels(self):
+        """Per template, the kernel that filters it: 0 FP32 direct FIR, 1 tensor cores with time
+        on M, 2 tensor cores with templates on M, 3 block FFT (rfd_plan_template_kernels)."""
+        out = np.empty(self.n_tmpl, dtype=np.int32)
+        check(_lib().rfd_plan_template_kernels(self.handle, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
     def set_taps(self, taps, k_stride, lag, sigma, stream=None):
         check(_lib().rfd_plan_set_taps(self.handle, _ptr(taps), int(k_stride), _ptr(lag), _ptr(sigma),
                                        _stream(stream)))
@@ -426,6 +433,15 @@ class Mlp:
         check(_lib().rfd_mlp_state(self.handle, loss.ctypes.data_as(ctypes.c_void_p), ctypes.byref(step),
                                    ctypes.byref(scale), _stream(stream)))
         return loss, int(step.value), float(scale.value)
+
+    def save(self, path, stream=None):
+        """Checkpoint of the training state (weights, Adam moments, normalisation, lags,
+        optimiser state) to `path` (rfd_mlp_save)."""
+        check(_lib().rfd_mlp_save(self.handle, str(path).encode(), _stream(stream)))
+
+    def load(self, path, stream=None):
+        """Restores a checkpoint written for the same grid, PSD and references (rfd_mlp_load)."""
+        check(_lib().rfd_mlp_load(self.handle, str(path).encode(), _stream(stream)))
 
     def infer(self, params, net_of, taps, lag, sigma, k_stride=None, stream=None):
         pa, n = _params(params)

@@ -77,6 +77,7 @@ SIGNATURES = {
     "rfd_plan_destroy": (None, [_vp]),
     "rfd_plan_set_taps": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
     "rfd_plan_executed_flops": (_dbl, [_vp]),
+    "rfd_plan_template_kernels": (_i32, [_vp, _vp]),
     "rfd_plan_options_default": (None, [_vp]),
     "rfd_plan_create_ex": (_i32, [_vp, ctypes.POINTER(Grid), _i32, _i32, _vp, _vp, _i32, _i32, _flt, _i32, _vp,
                                   ctypes.POINTER(_vp)]),
@@ -118,6 +119,8 @@ SIGNATURES = {
     "rfd_mlp_train_step": (_i32, [_vp, _vp, _vp, _i32, _vp, _i32, _flt, _vp]),
     "rfd_mlp_grads": (_i32, [_vp, _vp, _vp, _i32, _vp, _i32, _vp, _vp, _vp]),
     "rfd_mlp_state": (_i32, [_vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_flt), _vp]),
+    "rfd_mlp_save": (_i32, [_vp, ctypes.c_char_p, _vp]),
+    "rfd_mlp_load": (_i32, [_vp, ctypes.c_char_p, _vp]),
     "rfd_mlp_infer": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp]),
     "rfd_mlp_cross_match": (_i32, [_vp, _vp, _i32, _vp, _i64, _vp, _i64, _vp, _vp]),
     "rfd_learned_taps": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _dbl, _i32, _dbl, _vp, _vp, _vp, _vp, _vp, _vp,

@@ -878,6 +878,21 @@ rfd_status rfd_ratio_filter_window(rfd_plan *plan, const void *qref_dev, const i
 
 double rfd_plan_executed_flops(const rfd_plan *plan) { return plan ? plan->executed_flops : 0.0; }
 
+rfd_status rfd_plan_template_kernels(const rfd_plan *plan, int32_t *kernel_host) {
+    RFD_REQUIRE(plan && kernel_host, RFD_ERR_ARG, "NULL argument");
+    for (int32_t j = 0; j < plan->n_tmpl; ++j) kernel_host[j] = -1;
+    auto mark = [&](int32_t first, int32_t count, int32_t kind) {
+        for (int32_t a = 0; a < count; ++a) kernel_host[plan->perm[first + a]] = kind;
+    };
+    for (const RfdTile &t : plan->tiles) mark(t.first, t.count, RFD_KERNEL_FP32);
+    for (const TcTile &t : plan->tc_tiles) mark(t.first, t.count, RFD_KERNEL_TC_TIME_ON_M);
+    for (const TcTile &t : plan->tl_tiles) mark(t.first, t.count, RFD_KERNEL_TC_TEMPLATES_ON_M);
+    for (const FftTile &t : plan->fft_tiles) mark(t.first, t.count, RFD_KERNEL_BLOCK_FFT);
+    for (int32_t j = 0; j < plan->n_tmpl; ++j)
+        RFD_REQUIRE(kernel_host[j] >= 0, RFD_ERR_ARG, "template %d is in no tile (internal error)", j);
+    return RFD_OK;
+}
+
 rfd_status rfd_find_triggers(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand_dev,
                              const int64_t *cand_count_dev, int64_t cand_capacity, rfd_trigger *trig_dev,
                              int64_t trig_capacity, int64_t *n_trig_host, void *stream) {

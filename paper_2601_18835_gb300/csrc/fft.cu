@@ -18,6 +18,7 @@
 // pass reads global memory directly (every load of a thread issued at once), middle passes
 // run in place in a padded shared-memory tile, and the last pass writes global memory.
 // Other lengths take one kernel per Stockham pass over global memory.
+#include "epilogue.cuh"
 #include "fft_reg.cuh"
 #include "internal.cuh"
 
@@ -226,6 +227,22 @@ __device__ __forceinline__ void last_pass(const typename Cplx<T>::type *S, int l
     }
 }
 
+// The middle passes of a block's transforms, after a first pass of radix R0 (whose output is
+// in the tile); returns the last pass's stage twiddles.
+template <typename T, int EPT, bool INV>
+__device__ __forceinline__ const typename Cplx<T>::type *mid_passes(typename Cplx<T>::type *S, int logL, int LP,
+                                                                   const typename Cplx<T>::type *stw, int R0) {
+    stw += R0 - 1;
+    int ns = R0;
+    const int npass = ((logL & 3) ? 1 : 0) + logL / 4;
+    for (int p = 1; p + 1 < npass; ++p) {
+        mid_pass<T, 16, EPT, INV>(S, logL, LP, ns, stw);
+        stw += 15 * ns;
+        ns *= 16;
+    }
+    return stw;
+}
+
 // The C transforms of a block, global to global: first pass from g_in, middle passes in the
 // tile, last pass to g_out.  logL >= 6, so there are two or three passes.
 template <typename T, int EPT, bool INV, bool IN_CFAST, bool OUTER>
@@ -243,14 +260,7 @@ __device__ __forceinline__ void block_fft(typename Cplx<T>::type *S, int logL, i
     else if (R0 == 8) first_pass<T, 8, EPT, INV, IN_CFAST>(S, logL, LP, logC, g_in, in_ld, in_cs);
     else first_pass<T, 16, EPT, INV, IN_CFAST>(S, logL, LP, logC, g_in, in_ld, in_cs);
     __syncthreads();                 // also covers the tables the caller copied
-    stw += R0 - 1;
-    int ns = R0;
-    const int npass = (first ? 1 : 0) + logL / 4;
-    for (int p = 1; p + 1 < npass; ++p) {
-        mid_pass<T, 16, EPT, INV>(S, logL, LP, ns, stw);
-        stw += 15 * ns;
-        ns *= 16;
-    }
+    stw = mid_passes<T, EPT, INV>(S, logL, LP, stw, R0);
     last_pass<T, 16, EPT, INV, OUTER>(S, logL, LP, logC, stw, g_out, out_ld, c0, sh, lo, hi);
 }
 
@@ -302,6 +312,148 @@ __global__ void __launch_bounds__(512) k_fft_rows(const typename Cplx<T>::type *
     const int r0 = blockIdx.x * C;
     block_fft<T, EPT, INV, false, false>(S, logN2, logC, stw, y + b * y_stride + (int64_t)r0 * N2, 1, N2,
                                          out + b * out_stride + r0, N1, 0, 0, nullptr, nullptr);
+}
+
+// ------------------------------------------------------------------ fused FINDCHIRP (Eq. 1)
+// The inverse transform of c_j[k] = G[k] conj(h_j[k]) (G = 4 df d / S, zero outside the data
+// band and for k >= n/2), z_j = q_j / sigma_j, in the two passes above with the pointwise
+// product folded into pass A's first radix pass (elements with k >= n/2 are zero and never
+// loaded) and the |z|^2 threshold / window maximum folded into pass B's last radix pass (q is
+// never written).  Pass A also forms each block's share of sigma_j^2 = sum_k Wt[k] |h_j[k]|^2
+// (Wt = 4 df / S), summed per template in a fixed order afterwards.
+
+// First pass of pass A (ns = 1): element n1 of column c is k = n1 N2 + c0 + c.
+template <int R, int EPT>
+__device__ __forceinline__ void fc_first_pass(float2 *S, int logL, int LP, int logC, const float2 *__restrict__ G,
+                                              const float *__restrict__ Wt, const float2 *__restrict__ h,
+                                              int64_t half, int64_t N2, int c0, float &psum) {
+    constexpr int NB = EPT / R, LOGR = Log2R<R>::v;
+    const int loglr = logL - LOGR, lr = 1 << loglr;
+    float2 v[NB][R];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        int c, j;
+        butterfly_of<true>(threadIdx.x + q * blockDim.x, loglr, logC, c, j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t k = (int64_t)(j + r * lr) * N2 + c0 + c;
+            float2 x = make_float2(0.f, 0.f);
+            if (k < half) {
+                const float2 hv = h[k];
+                const float2 g = G[k];
+                // g conj(h)
+                x = make_float2(g.x * hv.x + g.y * hv.y, g.y * hv.x - g.x * hv.y);
+                psum += Wt[k] * (hv.x * hv.x + hv.y * hv.y);
+            }
+            v[q][r] = x;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        int c, j;
+        butterfly_of<true>(threadIdx.x + q * blockDim.x, loglr, logC, c, j);
+        dft_reg<float, R, true>(v[q]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) S[tile_pos(c, (j << LOGR) + r, LP)] = v[q][r];
+    }
+}
+
+// Pass A of FINDCHIRP: template b's spectrum formed on the fly; y[k1 N2 + n2]; sigma^2 partials.
+template <int EPT>
+__global__ void __launch_bounds__(256) k_fc_cols(const float2 *__restrict__ G, const float *__restrict__ Wt,
+                                                 const float2 *__restrict__ h, int64_t nf, float2 *__restrict__ y,
+                                                 int logN1, int logN2, int logC, int sh,
+                                                 const float2 *__restrict__ stage, const float2 *__restrict__ tw_lo,
+                                                 const float2 *__restrict__ tw_hi, double *__restrict__ part) {
+    extern __shared__ __align__(16) uint8_t fsm[];
+    __shared__ float red[16];
+    const int N1 = 1 << logN1, N2 = 1 << logN2, C = 1 << logC;
+    const int nlo = 1 << sh, nhi = 1 << (logN1 + logN2 - sh);
+    float2 *S = (float2 *)fsm;
+    float2 *stw = S + C * tile_ld(N1);
+    float2 *lo = stw + N1;
+    float2 *hi = lo + nlo;
+    copy_table(stw, stage, N1 - 1);
+    copy_table(lo, tw_lo, nlo);
+    copy_table(hi, tw_hi, nhi);
+    const int64_t b = blockIdx.y;
+    const int c0 = blockIdx.x * C;
+    const int64_t n = (int64_t)N1 * N2;
+    const int LP = tile_ld(N1);
+    const int R0 = (logN1 & 3) ? (1 << (logN1 & 3)) : 16;
+    float psum = 0.f;
+    const float2 *hb = h + b * nf;
+    if (R0 == 2) fc_first_pass<2, EPT>(S, logN1, LP, logC, G, Wt, hb, n / 2, N2, c0, psum);
+    else if (R0 == 4) fc_first_pass<4, EPT>(S, logN1, LP, logC, G, Wt, hb, n / 2, N2, c0, psum);
+    else if (R0 == 8) fc_first_pass<8, EPT>(S, logN1, LP, logC, G, Wt, hb, n / 2, N2, c0, psum);
+    else fc_first_pass<16, EPT>(S, logN1, LP, logC, G, Wt, hb, n / 2, N2, c0, psum);
+    __syncthreads();
+    const float2 *st = mid_passes<float, EPT, true>(S, logN1, LP, stw, R0);
+    last_pass<float, 16, EPT, true, true>(S, logN1, LP, logC, st, y + b * n + c0, N2, c0, sh, lo, hi);
+    // the block's share of sigma^2, fixed order
+    for (int o = 16; o > 0; o >>= 1) psum += __shfl_down_sync(0xffffffffu, psum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = psum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)red[w];
+        part[b * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// Pass B of FINDCHIRP: rows k1 of y; the last radix pass hands every output q[k1 + N1 k2]
+// straight to the trigger epilogue (z = q / sigma, |z|^2 > thr, one candidate per window and
+// warp), lanes on adjacent k1.
+template <int EPT>
+__global__ void __launch_bounds__(256) k_fc_rows(const float2 *__restrict__ y, int logN1, int logN2, int logC,
+                                                 const float2 *__restrict__ stage, const double *__restrict__ sig2,
+                                                 int32_t j0, float thr, uint32_t W, rfd_candidate *__restrict__ cand,
+                                                 int64_t cap, unsigned long long *__restrict__ count) {
+    extern __shared__ __align__(16) uint8_t fsm[];
+    const int N1 = 1 << logN1, N2 = 1 << logN2, C = 1 << logC;
+    float2 *S = (float2 *)fsm;
+    float2 *stw = S + C * tile_ld(N2);
+    copy_table(stw, stage, N2 - 1);
+    const int64_t b = blockIdx.y;
+    const int r0 = blockIdx.x * C;
+    const int64_t n = (int64_t)N1 * N2;
+    const int LP = tile_ld(N2);
+    const float2 *g = y + b * n + (int64_t)r0 * N2;
+    const int R0 = (logN2 & 3) ? (1 << (logN2 & 3)) : 16;
+    if (R0 == 2) first_pass<float, 2, EPT, true, false>(S, logN2, LP, logC, g, 1, N2);
+    else if (R0 == 4) first_pass<float, 4, EPT, true, false>(S, logN2, LP, logC, g, 1, N2);
+    else if (R0 == 8) first_pass<float, 8, EPT, true, false>(S, logN2, LP, logC, g, 1, N2);
+    else first_pass<float, 16, EPT, true, false>(S, logN2, LP, logC, g, 1, N2);
+    __syncthreads();
+    const float2 *st = mid_passes<float, EPT, true>(S, logN2, LP, stw, R0);
+    // last pass (ns = N2 / 16, k = j): outputs j + r ns of column c are q[r0 + c + N1 (j + r ns)]
+    const float inv = (float)(1.0 / sqrt(sig2[b]));
+    constexpr int NB = EPT / 16;
+    const int loglr = logN2 - 4, ns = 1 << loglr;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        int c, j;
+        butterfly_of<true>(threadIdx.x + q * blockDim.x, loglr, logC, c, j);
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = S[tile_pos(c, j + r * ns, LP)];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], st[(r - 1) * ns + j]);
+        dft_reg<float, 16, true>(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const uint32_t t = (uint32_t)(r0 + c) + (uint32_t)N1 * (uint32_t)(j + r * ns);
+            emit_window_max(true, (uint32_t)(j0 + b), t, v[r].x * inv, v[r].y * inv, thr, W, cand, cap, count);
+        }
+    }
+}
+
+// sig2[row] = the row's pass-A partials summed in index order (one thread: a few hundred terms).
+__global__ void k_fc_sum(const double *__restrict__ part, int64_t nparts, double *__restrict__ sig2) {
+    if (threadIdx.x != 0) return;
+    double t = 0.0;
+    for (int64_t i = 0; i < nparts; ++i) t += part[blockIdx.x * nparts + i];
+    sig2[blockIdx.x] = t;
 }
 
 template <typename T>
@@ -459,6 +611,51 @@ rfd_status fft_c2c(rfd_ctx *ctx, int64_t n, int64_t batch, const typename Cplx<T
         ns *= R;
         src = dst;
         src_stride = dst_stride;
+    }
+    return RFD_OK;
+}
+
+// FINDCHIRP over templates h (complex64 [J][nf]) with the weights G, Wt (length n/2): pass A
+// into tmp (J n complex64), sigma^2 per template, pass B with the trigger epilogue.  n must be
+// in [2^12, 2^22].
+rfd_status findchirp_fused(rfd_ctx *ctx, int64_t n, int64_t J, const float2 *G, const float *Wt, const float2 *h,
+                           int64_t nf, int32_t j0, float thr, int32_t W, float2 *tmp, double *part,
+                           double *sig2, rfd_candidate *cand, int64_t cap, int64_t *count, cudaStream_t s) {
+    int log2n = 0;
+    while ((int64_t(1) << log2n) < n) ++log2n;
+    RFD_REQUIRE(log2n >= 12 && log2n <= 22, RFD_ERR_SHAPE, "findchirp: n=%lld outside [2^12, 2^22]", (long long)n);
+    constexpr int EPT = 32;
+    const int logN1 = (log2n + 1) / 2, logN2 = log2n - logN1;
+    const int N1 = 1 << logN1, N2 = 1 << logN2;
+    auto pick_c = [&](int logL, int logOther) { return std::min(std::max(2, 12 - logL), logOther); };
+    const int logCA = pick_c(logN1, logN2), logCB = pick_c(logN2, logN1);
+    const int sh = (log2n + 1) / 2;
+    const unsigned thA = (unsigned)((N1 << logCA) / EPT), thB = (unsigned)((N2 << logCB) / EPT);
+    const size_t shA = ((size_t)(tile_ld(N1) << logCA) + N1 + ((size_t)1 << sh) + ((size_t)1 << (log2n - sh))) *
+                       sizeof(float2);
+    const size_t shB = ((size_t)(tile_ld(N2) << logCB) + N2) * sizeof(float2);
+    const float2 *tw = nullptr, *stA = nullptr, *stB = nullptr, *hi = nullptr;
+    RFD_TRY(get_twiddles<float>(ctx, n, &tw, s));
+    RFD_TRY(get_stage_twiddles<float>(ctx, logN1, &stA, s));
+    RFD_TRY(get_stage_twiddles<float>(ctx, logN2, &stB, s));
+    RFD_TRY(get_twiddles<float>(ctx, n >> sh, &hi, s));
+    static bool attr_set[64] = {};
+    const int dev = ctx->device < 64 ? ctx->device : 63;
+    if (!attr_set[dev]) {
+        RFD_TRY_CUDA(cudaFuncSetAttribute(k_fc_cols<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        RFD_TRY_CUDA(cudaFuncSetAttribute(k_fc_rows<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set[dev] = true;
+    }
+    for (int64_t b0 = 0; b0 < J; b0 += 65535) {
+        const int64_t nb = std::min<int64_t>(65535, J - b0);
+        const dim3 gA((unsigned)(N2 >> logCA), (unsigned)nb), gB((unsigned)(N1 >> logCB), (unsigned)nb);
+        k_fc_cols<EPT><<<gA, thA, shA, s>>>(G, Wt, h + b0 * nf, nf, tmp, logN1, logN2, logCA, sh, stA, tw, hi, part);
+        RFD_LAUNCH_CHECK();
+        k_fc_sum<<<(unsigned)nb, 32, 0, s>>>(part, (int64_t)gA.x, sig2);
+        RFD_LAUNCH_CHECK();
+        k_fc_rows<EPT><<<gB, thB, shB, s>>>(tmp, logN1, logN2, logCB, stB, sig2, (int32_t)(j0 + b0), thr, (uint32_t)W,
+                                            cand, cap, (unsigned long long *)count);
+        RFD_LAUNCH_CHECK();
     }
     return RFD_OK;
 }

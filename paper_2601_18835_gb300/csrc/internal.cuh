@@ -126,6 +126,13 @@ rfd_status fft_c2c(rfd_ctx *ctx, int64_t n, int64_t batch, const typename Cplx<T
 // ns = product of the earlier radices holds exp(+2 pi i r k / (ns R)) at
 // base_p + (r - 1) ns + k), FP32, cached in the context.
 rfd_status fft_stage_twiddles32(rfd_ctx *ctx, int logL, const float2 **out, cudaStream_t s);
+// FINDCHIRP (Eq. 1) for J templates h (complex64 [J][nf]) in two fused passes (fft.cu): the
+// spectrum G[k] conj(h[k]) (G = 4 df d / S on the data band, Wt = 4 df / S, both of length
+// n/2) formed inside the first FFT pass, z = q / sigma with the trigger epilogue inside the
+// last.  tmp: J n complex64; part: J x 2048 doubles; sig2: J doubles (sigma^2 per template).
+rfd_status findchirp_fused(rfd_ctx *ctx, int64_t n, int64_t J, const float2 *G, const float *Wt, const float2 *h,
+                           int64_t nf, int32_t j0, float thr, int32_t W, float2 *tmp, double *part,
+                           double *sig2, rfd_candidate *cand, int64_t cap, int64_t *count, cudaStream_t s);
 
 // ------------------------------------------------------------------ taps (taps.cu)
 // lag_in empty: the lag is searched (Sec. V placement); otherwise it is taken from lag_in.

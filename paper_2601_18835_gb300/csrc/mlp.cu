@@ -1257,3 +1257,182 @@ rfd_status rfd_learned_taps(rfd_mlp *P, const double *psd_dev, const rfd_params 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ checkpoint
+// File: 8-byte magic "RFDMLP" 0x00 0x01, uint64 (little endian) length of a JSON header, the
+// header (ASCII), then the sections it lists, each at its offset from the end of the header
+// (64-byte aligned): FP32 master weights, Adam first and second moments, the per-network
+// normalisation (double [R][kNorm]: mu[4], sd[4], out_scale), the lags, the optimiser state
+// (Adam step, dynamic loss scale and its clean-step count) and the references'
+// autocorrelations C_r, which identify the grid, PSD and references the networks belong to.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+namespace rfd {
+namespace {
+
+constexpr char kCkptMagic[8] = {'R', 'F', 'D', 'M', 'L', 'P', 0, 1};
+
+struct CkptSection {
+    const char *name;
+    const char *dtype;
+    int64_t rows, cols;
+    size_t bytes;
+};
+
+// The sections of a checkpoint of P, in file order.
+std::vector<CkptSection> ckpt_sections(const rfd_mlp *P) {
+    const int64_t R = P->R;
+    return {{"weights", "f32", R, kP, (size_t)(R * kP * 4)},
+            {"adam_m", "f32", R, kP, (size_t)(R * kP * 4)},
+            {"adam_v", "f32", R, kP, (size_t)(R * kP * 4)},
+            {"norm", "f64", R, kNorm, (size_t)(R * kNorm * 8)},
+            {"lag", "i32", R, 1, (size_t)(R * 4)},
+            {"optimizer", "raw", 1, (int64_t)sizeof(MlpState), sizeof(MlpState)},
+            {"autocorr", "c128", R, kCw, (size_t)(R * kCw * 16)}};
+}
+
+size_t align64(size_t x) { return (x + 63) / 64 * 64; }
+
+// Value of a number-valued key of the header ("key": number), or false when absent.
+bool header_number(const std::string &h, const char *key, double *out) {
+    const std::string k = std::string("\"") + key + "\":";
+    const size_t at = h.find(k);
+    if (at == std::string::npos) return false;
+    char *end = nullptr;
+    *out = std::strtod(h.c_str() + at + k.size(), &end);
+    return end != h.c_str() + at + k.size();
+}
+
+}  // namespace
+}  // namespace rfd
+
+extern "C" {
+
+rfd_status rfd_mlp_save(rfd_mlp *P, const char *path, void *stream) {
+    using namespace rfd;
+    RFD_REQUIRE(P && path, RFD_ERR_ARG, "NULL argument");
+    RFD_TRY_CUDA(cudaSetDevice(P->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    RFD_TRY(check_status(P, s));
+    RFD_TRY_CUDA(cudaDeviceSynchronize());
+    const std::vector<CkptSection> secs = ckpt_sections(P);
+    std::vector<std::vector<char>> data(secs.size());
+    for (size_t i = 0; i < secs.size(); ++i) data[i].resize(secs[i].bytes);
+    const int64_t R = P->R;
+    RFD_TRY_CUDA(cudaMemcpy(data[0].data(), P->d_params.p, secs[0].bytes, cudaMemcpyDeviceToHost));
+    RFD_TRY_CUDA(cudaMemcpy(data[1].data(), P->d_m.p, secs[1].bytes, cudaMemcpyDeviceToHost));
+    RFD_TRY_CUDA(cudaMemcpy(data[2].data(), P->d_v.p, secs[2].bytes, cudaMemcpyDeviceToHost));
+    std::memcpy(data[3].data(), P->norm.data(), secs[3].bytes);
+    std::memcpy(data[4].data(), P->lag.data(), secs[4].bytes);
+    MlpState st{};
+    RFD_TRY_CUDA(cudaMemcpy(&st, P->d_state.p, sizeof(st), cudaMemcpyDeviceToHost));
+    std::memcpy(data[5].data(), &st, sizeof(st));
+    RFD_TRY_CUDA(cudaMemcpy(data[6].data(), P->d_C.p, secs[6].bytes, cudaMemcpyDeviceToHost));
+    char buf[512];
+    std::string h = "{\"format\": \"librfd learned-tap networks\", \"version\": 1";
+    std::snprintf(buf, sizeof(buf),
+                  ", \"n_ref\": %lld, \"param_count\": %lld, \"taps\": %d, \"inputs\": %d"
+                  ", \"grid\": {\"fs\": %.17g, \"n\": %lld, \"f_low\": %.17g, \"pn_flags\": %d}"
+                  ", \"adam_step\": %d, \"loss_scale\": %.9g, \"clean_steps\": %d, \"sections\": [",
+                  (long long)R, (long long)kP, kT, kIn, P->grid.fs, (long long)P->grid.n, P->grid.f_low,
+                  P->grid.pn_flags, st.t, (double)st.loss_scale, st.good);
+    h += buf;
+    size_t off = 0;
+    for (size_t i = 0; i < secs.size(); ++i) {
+        std::snprintf(buf, sizeof(buf), "%s{\"name\": \"%s\", \"dtype\": \"%s\", \"shape\": [%lld, %lld], "
+                      "\"offset\": %zu, \"bytes\": %zu}", i ? ", " : "", secs[i].name, secs[i].dtype,
+                      (long long)secs[i].rows, (long long)secs[i].cols, off, secs[i].bytes);
+        h += buf;
+        off = align64(off + secs[i].bytes);
+    }
+    h += "]}\n";
+    FILE *f = std::fopen(path, "wb");
+    RFD_REQUIRE(f, RFD_ERR_ARG, "mlp_save: cannot open %s for writing", path);
+    const uint64_t hl = h.size();
+    bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(&hl, 8, 1, f) == 1 &&
+              std::fwrite(h.data(), 1, h.size(), f) == h.size();
+    const std::vector<char> zeros(64, 0);
+    off = 0;
+    for (size_t i = 0; ok && i < secs.size(); ++i) {
+        ok = std::fwrite(data[i].data(), 1, secs[i].bytes, f) == secs[i].bytes;
+        const size_t pad = align64(off + secs[i].bytes) - (off + secs[i].bytes);
+        ok = ok && (pad == 0 || std::fwrite(zeros.data(), 1, pad, f) == pad);
+        off = align64(off + secs[i].bytes);
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    RFD_REQUIRE(ok, RFD_ERR_ARG, "mlp_save: writing %s failed", path);
+    return RFD_OK;
+}
+
+rfd_status rfd_mlp_load(rfd_mlp *P, const char *path, void *stream) {
+    using namespace rfd;
+    RFD_REQUIRE(P && path, RFD_ERR_ARG, "NULL argument");
+    FILE *f = std::fopen(path, "rb");
+    RFD_REQUIRE(f, RFD_ERR_ARG, "mlp_load: cannot open %s", path);
+    char magic[8];
+    uint64_t hl = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+              std::fread(&hl, 8, 1, f) == 1 && hl > 0 && hl < (1u << 20);
+    std::string h;
+    if (ok) {
+        h.resize(hl);
+        ok = std::fread(&h[0], 1, hl, f) == hl;
+    }
+    const std::vector<CkptSection> secs = ckpt_sections(P);
+    std::vector<std::vector<char>> data(secs.size());
+    size_t off = 0;
+    for (size_t i = 0; ok && i < secs.size(); ++i) {
+        data[i].resize(secs[i].bytes);
+        ok = std::fread(data[i].data(), 1, secs[i].bytes, f) == secs[i].bytes;
+        const size_t pad = align64(off + secs[i].bytes) - (off + secs[i].bytes);
+        char skip[64];
+        ok = ok && (pad == 0 || std::fread(skip, 1, pad, f) == pad);
+        off = align64(off + secs[i].bytes);
+    }
+    std::fclose(f);
+    RFD_REQUIRE(ok, RFD_ERR_ARG, "mlp_load: %s is not a complete librfd network checkpoint", path);
+    double v = 0;
+    RFD_REQUIRE(header_number(h, "n_ref", &v) && (int64_t)v == P->R, RFD_ERR_SHAPE,
+                "mlp_load: the checkpoint holds %g networks, this object %d", v, P->R);
+    RFD_REQUIRE(header_number(h, "param_count", &v) && (int64_t)v == kP, RFD_ERR_SHAPE,
+                "mlp_load: parameter count %g, expected %lld", v, (long long)kP);
+    double fs = 0, n = 0, fl = 0, pf = 0;
+    RFD_REQUIRE(header_number(h, "fs", &fs) && header_number(h, "n", &n) && header_number(h, "f_low", &fl) &&
+                    header_number(h, "pn_flags", &pf) && fs == P->grid.fs && (int64_t)n == P->grid.n &&
+                    fl == P->grid.f_low && (int32_t)pf == P->grid.pn_flags,
+                RFD_ERR_ARG, "mlp_load: the checkpoint's grid differs from this object's");
+    RFD_TRY_CUDA(cudaSetDevice(P->ctx->device));
+    RFD_TRY_CUDA(cudaDeviceSynchronize());
+    // the references' autocorrelations must be the same to the bit: same PSD, grid and references
+    std::vector<char> C(secs[6].bytes);
+    RFD_TRY_CUDA(cudaMemcpy(C.data(), P->d_C.p, C.size(), cudaMemcpyDeviceToHost));
+    RFD_REQUIRE(std::memcmp(C.data(), data[6].data(), C.size()) == 0, RFD_ERR_ARG,
+                "mlp_load: the checkpoint was trained for other references or another PSD");
+    const int64_t R = P->R;
+    const float *w = (const float *)data[0].data();
+    for (int64_t i = 0; i < R * kP; ++i)
+        RFD_REQUIRE(std::isfinite(w[i]), RFD_ERR_ARG, "mlp_load: weight %lld is not finite", (long long)i);
+    MlpState st{};
+    std::memcpy(&st, data[5].data(), sizeof(st));
+    st.inf = 0;
+    st.err = 0;
+    std::memcpy(P->norm.data(), data[3].data(), secs[3].bytes);
+    std::memcpy(P->lag.data(), data[4].data(), secs[4].bytes);
+    RFD_TRY_CUDA(cudaMemcpy(P->d_params.p, data[0].data(), secs[0].bytes, cudaMemcpyHostToDevice));
+    RFD_TRY_CUDA(cudaMemcpy(P->d_m.p, data[1].data(), secs[1].bytes, cudaMemcpyHostToDevice));
+    RFD_TRY_CUDA(cudaMemcpy(P->d_v.p, data[2].data(), secs[2].bytes, cudaMemcpyHostToDevice));
+    RFD_TRY_CUDA(cudaMemcpy(P->d_norm.p, P->norm.data(), secs[3].bytes, cudaMemcpyHostToDevice));
+    RFD_TRY_CUDA(cudaMemcpy(P->d_lag.p, P->lag.data(), secs[4].bytes, cudaMemcpyHostToDevice));
+    RFD_TRY_CUDA(cudaMemcpy(P->d_state.p, &st, sizeof(st), cudaMemcpyHostToDevice));
+    // the FP16 operand copies follow from the masters by the same rounding every step uses
+    const int64_t nparam = R * kP;
+    k_mlp_sync_half<<<(unsigned)((nparam + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        (const float *)P->d_params.p, (__half *)P->d_wh.p, nparam);
+    RFD_LAUNCH_CHECK();
+    RFD_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return RFD_OK;
+}
+
+}  // extern "C"

@@ -99,16 +99,34 @@ __global__ void k_sum_rows(const double *__restrict__ part, int64_t nparts, doub
     if (threadIdx.x == 0) out[row] = v;
 }
 
+// Largest |Re q| or |Im q| of each reference's series (float bits of a non-negative value
+// order like the values, so an integer maximum is exact); qmax zeroed beforehand.
+__global__ void k_qmax(const float2 *__restrict__ q, int64_t n, uint32_t *__restrict__ qmax) {
+    const int64_t r = blockIdx.y;
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = q[r * n + i];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&qmax[r], __float_as_uint(m));
+}
+
 // Per-reference power-of-two scale: the rms of q is sqrt(sum_k |c_k|^2) for the unnormalised
-// inverse transform; e_r puts it near 2^8 so the fp16 hi part keeps >= 8 bits of headroom.
-__global__ void k_qscale(const double *__restrict__ pow_c, int n_ref, int precision,
-                         int32_t *__restrict__ e) {
+// inverse transform; e_r puts it near 2^8 so the fp16 hi part keeps >= 8 bits of headroom, and
+// no lower than needed to keep the largest component of the series at or below 2^14 (fp16's
+// largest finite value is 65504), so that a very loud sample (a glitch or a strong signal,
+// more than 64 times the rms) cannot overflow the hi part.
+__global__ void k_qscale(const double *__restrict__ pow_c, const uint32_t *__restrict__ qmax, int n_ref,
+                         int precision, int32_t *__restrict__ e) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_ref) return;
     int v = 0;
     if (precision != RFD_PREC_FP32 && pow_c[r] > 0.0) {
         const double rms = sqrt(pow_c[r]);
         v = (int)nearbyint(8.0 - log2(rms));
+        const double mx = (double)__uint_as_float(qmax[r]);
+        if (mx > 0.0) v = min(v, (int)floor(14.0 - log2(mx)));
         v = max(-120, min(120, v));
     }
     e[r] = v;
@@ -155,17 +173,20 @@ __global__ void k_finalize_split(const float2 *__restrict__ q, int64_t n, int64_
     base[3 * ld + m] = il;
 }
 
-// FINDCHIRP epilogue: z = q / sigma, threshold and window maximum, lanes = consecutive t.
-__global__ void __launch_bounds__(256) k_findchirp_epilogue(
-    const float2 *__restrict__ q, int64_t n, const double *__restrict__ sig2, int32_t j0,
-    float thr, uint32_t W, rfd_candidate *__restrict__ cand, int64_t cap,
-    unsigned long long *__restrict__ count) {
-    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // n multiple of 256
-    const int64_t row = blockIdx.y;
-    const float inv = (float)(1.0 / sqrt(sig2[row]));
-    const float2 x = q[row * n + m];
-    emit_window_max(true, (uint32_t)(j0 + row), (uint32_t)m, x.x * inv, x.y * inv, thr, W, cand,
-                    cap, count);
+// FINDCHIRP weights, k < n/2: Wt = 4 df / S and G = Wt d on the data band [k_lo, n/2), 0 elsewhere.
+__global__ void k_fc_weights(const float2 *__restrict__ d, const double *__restrict__ psd, double df, int64_t k_lo,
+                             int64_t half, float2 *__restrict__ G, float *__restrict__ Wt) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= half) return;
+    float w = 0.f;
+    float2 g = make_float2(0.f, 0.f);
+    if (k >= k_lo) {
+        w = (float)(4.0 * df) / (float)psd[k];
+        const float2 dv = d[k];
+        g = make_float2(w * dv.x, w * dv.y);
+    }
+    G[k] = g;
+    Wt[k] = w;
 }
 
 }  // namespace
@@ -200,10 +221,11 @@ rfd_status filter_reference_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, c
     RFD_TRY(ensure(ctx->ws[2], R * n * sizeof(float2)));
     RFD_TRY(ensure(ctx->ws[3], R * n * sizeof(float2)));
     RFD_TRY(ensure(ctx->ws[4], 2 * R * nblk * sizeof(double)));
-    RFD_TRY(ensure(ctx->ws[5], 2 * R * sizeof(double)));
+    RFD_TRY(ensure(ctx->ws[5], 2 * R * sizeof(double) + R * sizeof(uint32_t)));
     float2 *c = (float2 *)ctx->ws[1].p;
     double *part = (double *)ctx->ws[4].p;
     double *sums = (double *)ctx->ws[5].p;
+    uint32_t *qmax = (uint32_t *)(sums + 2 * R);
     for (int64_t r0 = 0; r0 < R; r0 += 65535) {
         const unsigned gy = (unsigned)std::min<int64_t>(65535, R - r0);
         k_spectrum_stored<<<dim3(nblk, gy), 256, 0, s>>>(d, psd, href + r0 * g.nf, g.nf, g.df, n, c + r0 * n, n,
@@ -212,10 +234,19 @@ rfd_status filter_reference_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, c
     }
     k_sum_rows<<<(unsigned)R, 256, 0, s>>>(part, nblk, sums);
     RFD_LAUNCH_CHECK();
-    k_qscale<<<(unsigned)((R + 127) / 128), 128, 0, s>>>(sums, (int)R, precision, qscale);
-    RFD_LAUNCH_CHECK();
     float2 *q = (float2 *)ctx->ws[2].p;
     RFD_TRY(fft_c2c<float>(ctx, n, R, c, n, q, n, (float2 *)ctx->ws[3].p, true, s));
+    if (precision != RFD_PREC_FP32) {
+        RFD_TRY_CUDA(cudaMemsetAsync(qmax, 0, R * sizeof(uint32_t), s));
+        for (int64_t r0 = 0; r0 < R; r0 += 65535) {
+            const unsigned gy = (unsigned)std::min<int64_t>(65535, R - r0);
+            k_qmax<<<dim3((unsigned)std::min<int64_t>(64, (n + 255) / 256), gy), 256, 0, s>>>(q + r0 * n, n,
+                                                                                            qmax + r0);
+            RFD_LAUNCH_CHECK();
+        }
+    }
+    k_qscale<<<(unsigned)((R + 127) / 128), 128, 0, s>>>(sums, qmax, (int)R, precision, qscale);
+    RFD_LAUNCH_CHECK();
     const int64_t keep = n + halo;
     for (int64_t r0 = 0; r0 < R; r0 += 65535) {
         const unsigned gy = (unsigned)std::min<int64_t>(65535, R - r0);
@@ -234,35 +265,27 @@ rfd_status filter_reference_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, c
     return RFD_OK;
 }
 
-// FINDCHIRP over all templates in batches from stored templates; candidates as in the
-// ratio-filter epilogue.
+// FINDCHIRP over all templates in batches from stored templates, two fused kernels per batch
+// (fft.cu: findchirp_fused); candidates as in the ratio-filter epilogue.  Batches keep the
+// intermediate array near 128 MB so that it stays mostly in the 126 MB L2 between the passes.
 rfd_status findchirp_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, const double *psd, const float2 *h,
                           int64_t J, int32_t W, float thr, rfd_candidate *cand, int64_t cap, int64_t *count,
                           cudaStream_t s) {
-    const int64_t n = g.n;
-    const unsigned nblk = (unsigned)(n / 256);
-    // batch so that three complex64 work arrays stay near 3 GB
-    int64_t B = std::max<int64_t>(1, ((int64_t)1 << 30) / (n * (int64_t)sizeof(float2)));
-    B = std::min<int64_t>(std::min<int64_t>(B, J), 65535);
-    RFD_TRY(ensure(ctx->ws[1], B * n * sizeof(float2)));
-    RFD_TRY(ensure(ctx->ws[2], B * n * sizeof(float2)));
-    RFD_TRY(ensure(ctx->ws[3], B * n * sizeof(float2)));
-    RFD_TRY(ensure(ctx->ws[4], 2 * B * nblk * sizeof(double)));
-    RFD_TRY(ensure(ctx->ws[5], 2 * B * sizeof(double)));
+    const int64_t n = g.n, half = n / 2;
+    const int64_t B = std::max<int64_t>(1, std::min<int64_t>(J, ((int64_t)128 << 20) / (n * (int64_t)sizeof(float2))));
+    RFD_TRY(ensure(ctx->ws[1], (size_t)half * (sizeof(float2) + sizeof(float))));
+    RFD_TRY(ensure(ctx->ws[2], (size_t)B * n * sizeof(float2)));
+    RFD_TRY(ensure(ctx->ws[4], (size_t)B * 2048 * sizeof(double)));
+    RFD_TRY(ensure(ctx->ws[5], (size_t)B * sizeof(double)));
+    float2 *G = (float2 *)ctx->ws[1].p;
+    float *Wt = (float *)(G + half);
     RFD_TRY_CUDA(cudaMemsetAsync(count, 0, sizeof(int64_t), s));
-    float2 *c = (float2 *)ctx->ws[1].p, *q = (float2 *)ctx->ws[2].p;
-    double *part = (double *)ctx->ws[4].p, *sums = (double *)ctx->ws[5].p;
+    k_fc_weights<<<(unsigned)((half + 255) / 256), 256, 0, s>>>(d, psd, g.df, g.k_lo, half, G, Wt);
+    RFD_LAUNCH_CHECK();
     for (int64_t j0 = 0; j0 < J; j0 += B) {
         const int64_t b = std::min<int64_t>(B, J - j0);
-        k_spectrum_stored<<<dim3(nblk, (unsigned)b), 256, 0, s>>>(d, psd, h + j0 * g.nf, g.nf, g.df, n, c, n, part,
-                                                                 part + B * nblk);
-        RFD_LAUNCH_CHECK();
-        k_sum_rows<<<(unsigned)b, 256, 0, s>>>(part + B * nblk, nblk, sums);
-        RFD_LAUNCH_CHECK();
-        RFD_TRY(fft_c2c<float>(ctx, n, b, c, n, q, n, (float2 *)ctx->ws[3].p, true, s));
-        k_findchirp_epilogue<<<dim3(nblk, (unsigned)b), 256, 0, s>>>(
-            q, n, sums, (int32_t)j0, thr, (uint32_t)W, cand, cap, (unsigned long long *)count);
-        RFD_LAUNCH_CHECK();
+        RFD_TRY(findchirp_fused(ctx, n, b, G, Wt, h + j0 * g.nf, g.nf, (int32_t)j0, thr, W, (float2 *)ctx->ws[2].p,
+                                (double *)ctx->ws[4].p, (double *)ctx->ws[5].p, cand, cap, count, s));
     }
     return RFD_OK;
 }

@@ -265,3 +265,63 @@ def test_training_reaches_target_and_learned_taps_gain(env, dense):
     extractions = stats["spot_checked"] + stats["exact"]
     print("learned taps: %s; exact extractions %d of %d" % (stats, extractions, len(P)))
     assert extractions < 0.5 * len(P)
+
+
+def test_checkpoint_resume_is_bit_exact(env, dense, tmp_path):
+    """rfd_mlp_save / rfd_mlp_load: N optimiser steps, a checkpoint, a fresh network object
+    that loads it, M more steps gives the same master weights, Adam state and loss scale, bit
+    for bit, as N + M steps without the interruption.  A checkpoint made for other
+    references is refused."""
+    from paper_2601_18835_gb300 import _native
+    _set_norm(env, dense)
+    w0 = omd.init_weights(len(REFS), seed=21)
+    feat, tgt, _ = _train_tensors(env, dense)
+    B, n1, n2 = 128, 12, 9
+    rng = np.random.default_rng(22)
+    idx = torch.from_numpy(np.stack([np.stack([rng.permutation(N_TRAIN)[:B] for _ in REFS])
+                                     for _ in range(n1 + n2)]).astype(np.int32)).cuda()
+    lrs = [3e-3 * (0.9 ** s) for s in range(n1 + n2)]
+
+    def run(net, steps):
+        for s in steps:
+            net.train_step(feat, tgt, N_TRAIN, idx[s].contiguous(), B, lrs[s])
+        torch.cuda.synchronize()
+
+    ref = env["mlp"]
+    ref.set_weights(w0)
+    run(ref, range(n1 + n2))
+    w_ref = ref.get_weights()
+    _, step_ref, scale_ref = ref.state()
+    path = tmp_path / "ckpt.rfdmlp"
+    ref.set_weights(w0)
+    run(ref, range(n1))
+    ref.save(path)
+    ref.set_weights(omd.init_weights(len(REFS), seed=99))           # the state is gone from ref
+    fresh = rfd.Mlp(env["ctx"], env["g"], env["psd"], REFS)
+    fresh.load(path)
+    run(fresh, range(n1, n1 + n2))
+    w_res = fresh.get_weights()
+    _, step_res, scale_res = fresh.state()
+    assert step_res == step_ref == n1 + n2
+    assert scale_res == scale_ref
+    assert np.array_equal(w_res.view(np.uint32), w_ref.view(np.uint32))
+    # inference from the loaded network equals the original's on the same inputs
+    P, ro = dense["held"].params()[:64], dense["held"].ref_of_tmpl[:64]
+    outs = []
+    for net in (fresh, ref):
+        if net is ref:
+            ref.load(path)
+            run(ref, range(n1, n1 + n2))
+        taps = torch.zeros((len(P), K), dtype=torch.complex64, device="cuda")
+        lag = torch.zeros(len(P), dtype=torch.int32, device="cuda")
+        sig = torch.zeros(len(P), dtype=torch.float64, device="cuda")
+        net.infer(P, ro, taps, lag, sig)
+        outs.append(taps.cpu().numpy())
+    assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
+    # a network object for other references refuses the checkpoint
+    other = rfd.Mlp(env["ctx"], env["g"], env["psd"], REFS[::-1].copy())
+    with pytest.raises(rfd.RfdError) as ei:
+        other.load(path)
+    assert ei.value.status == _native.RFD_ERR_ARG
+    other.close()
+    fresh.close()

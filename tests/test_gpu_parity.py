@@ -480,6 +480,12 @@ def test_last_partial_tile_on_block_fft(ctx, name, prec):
     b = {(int(x["j"]), int(x["t"]) // cfg.window): x for x in trig_tc}
     diff_j = {key[0] for key in set(a) | set(b) if key not in a or key not in b or a[key].tobytes() != b[key].tobytes()}
     assert diff_j and diff_j <= set(range(64, 75))
+    # the plan reports the same assignment
+    plan = rfd.Plan(gpu.ctx, gpu.grid, bank.n_ref, bank.ref_of_tmpl, t["K"], prec, cfg.window, cfg.threshold, halo,
+                    options={"long_k": 0, "fft_rem": 16})
+    kern = plan.template_kernels()
+    plan.close()
+    assert np.array_equal(kern, np.where(np.arange(bank.n_tmpl) >= 64, 3, 2))
 
 
 @pytest.mark.slow
@@ -575,6 +581,34 @@ def test_bucketed_taps_and_uneven_k_tensor_core(ctx):
     assert n_or > 50
     assert compare_triggers(trig, sets, TOL_TC, range(J), cfg.window) <= amb_cap(n_or)
     assert snr_errors(trig, sets, range(J)) < EPS[rfd.PREC_FP16X3]
+
+
+# --------------------------------------------------------------------------- a very loud signal
+@pytest.mark.parametrize("kernel,opts", TC_KERNELS)
+def test_very_loud_injection_does_not_overflow_the_split(ctx, kernel, opts):
+    """A 1024 s segment (n = 2^20 at 1024 Hz) with an injection at SNR 10^5 (standing for a
+    very loud glitch or signal): its real part peaks 355 times above the rms of q_ref, past
+    the FP16 range of a series scaled to an rms of 2^8 (65504 / 256 = 256 rms).  The split's
+    scale is capped by the largest sample, so every trigger stays finite and matches the
+    oracle within the FP16x3 bound (the many windows the loud chirp lights up included)."""
+    cfg = workload.small_config(1, n=1 << 20, inj_snr=(1e5, 1e5))
+    bank, data = workload.make_workload(cfg)
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(cfg.k, match=False)
+    halo = cfg.k - 1
+    q, e, _ = gpu.filter_reference(halo, rfd.PREC_FP16X3)
+    qo = ora.q_ref(0)
+    rms = np.sqrt(np.mean(np.abs(qo) ** 2))
+    assert max(np.max(np.abs(qo.real)), np.max(np.abs(qo.imag))) > 300 * rms
+    assert int(e.item()) < 8 - int(np.log2(rms))           # the cap lowered the exponent
+    trig, _ = gpu.ratio_filter(t, q, e, rfd.PREC_FP16X3, halo, cand_cap=1 << 22, options=opts)
+    assert np.all(np.isfinite(trig["snr2"])) and np.all(np.isfinite(trig["zr"])) and np.all(np.isfinite(trig["zi"]))
+    js = [0, 1, 2, 3, 17, 40]
+    sets = {j: ora.triggers(ora.snr(j, ora.design(j, cfg.k, with_match=False)), EPS[rfd.PREC_FP16X3]) for j in js}
+    n_or = n_oracle(sets, js)
+    assert n_or > 20
+    assert compare_triggers(trig, sets, TOL_TC, js, cfg.window) <= amb_cap(n_or)
+    assert snr_errors(trig, sets, js) < EPS[rfd.PREC_FP16X3]
 
 
 # --------------------------------------------------------------------------- bounded waits

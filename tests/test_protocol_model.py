@@ -3,7 +3,8 @@ interleavings of their parties (mbarrier semantics: a phase completes after `cou
 a wait with parity p returns once a phase of parity p has completed, i.e. when
 completed_phases mod 2 != p).
 
-* rf_tc_long.cu: the producer (q window, taps chunks; chunk 0 completes on the item's go
+* rf_tc_long.cu: the producer (q window, taps chunks; chunk 0 completes on a transaction
+  barrier of its own, which the producer waits on before it arrives on the item's go
   barrier), the Y builders (released by the accumulator-full commit of the item two back), the
   epilogue (frees the accumulator for the item two ahead; pre-arrives once per buffer) and the
   MMA issuer (one go wait per item, waited before the last k-step of the previous item; taps
@@ -54,10 +55,11 @@ def _long_kernel(tiles_nch, n_tb, rnd):
     n = len(rng)
     AF, AE = [Bar(1), Bar(1)], [Bar(1), Bar(1)]
     GO, DF = [Bar(3), Bar(3)], [Bar(1), Bar(1)]               # go: producer, builders, epilogue
+    T0 = [Bar(1), Bar(1)]                                     # chunk 0's own transaction barrier
     stage, inuse = [None, None], [0, 0]
 
     def producer():
-        ka = 0
+        ka, t0u = 0, [0, 0]
         for li, (ti, tb) in enumerate(rng):
             for c in range(tiles_nch[ti]):
                 st, r = ka % 2, ka // 2
@@ -65,9 +67,19 @@ def _long_kernel(tiles_nch, n_tb, rnd):
                     yield
                 assert inuse[st] == 0, "copy onto a stage in use"
                 stage[st] = (ti, c)
-                (GO[li & 1] if c == 0 else AF[st]).arrive(li)
+                if c == 0:
+                    b = li & 1
+                    T0[b].arrive(li)                          # the copy lands
+                    while not T0[b].ok(t0u[b] & 1):
+                        yield
+                    t0u[b] += 1
+                    GO[b].arrive(li)
+                else:
+                    AF[st].arrive(li)
                 ka += 1
                 yield
+        # drain: the last phase armed on every copy barrier has completed
+        assert all(T0[b].done == t0u[b] for b in range(2))
 
     def builders():
         for li in range(n):
