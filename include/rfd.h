@@ -530,12 +530,12 @@ rfd_status rfd_mlp_state(rfd_mlp *mlp, float *loss_host, int32_t *step_host,
 /* Checkpoint of the networks' training state (the paper has no training code to resume;
  * this makes training restartable): rfd_mlp_save writes, after the stream's work, the FP32
  * master weights, Adam's moments, the normalisation, the lags, the optimiser state (Adam step,
- * dynamic loss scale and its clean-step count) and the references' autocorrelations to
- * `path`: an 8-byte magic, a little-endian uint64 header length, a JSON header naming each
- * section (dtype, shape, offset, bytes), then the raw sections, 64-byte aligned.
- * rfd_mlp_load reads such a file into a network object created for the same grid, PSD and
- * references (checked: the grid, the counts and the autocorrelations bit for bit, else
- * RFD_ERR_ARG / RFD_ERR_SHAPE) and rebuilds the FP16 operand copies from the masters, so that
+ * dynamic loss scale and its clean-step count), the references' autocorrelations and their
+ * phase constants to `path`: an 8-byte magic, a little-endian uint64 header length, a JSON
+ * header naming each section (dtype, shape, offset, bytes), then the raw sections, 64-byte
+ * aligned.  rfd_mlp_load reads such a file into a network object created for the same grid,
+ * PSD and references (checked: the grid, the counts, the autocorrelations and the references'
+ * constants bit for bit, else RFD_ERR_ARG / RFD_ERR_SHAPE) and rebuilds the FP16 operand copies from the masters, so that
  * training continues exactly as it would have without the save.  Both synchronise. */
 rfd_status rfd_mlp_save(rfd_mlp *mlp, const char *path, void *stream);
 rfd_status rfd_mlp_load(rfd_mlp *mlp, const char *path, void *stream);

@@ -240,7 +240,7 @@ struct rfd_plan {
     // block-FFT path (rf_fft.cu): templates with fft_k < K <= 1024
     std::vector<FftTile> fft_tiles;
     std::vector<int32_t> fft_refs;   // references with block-FFT templates
-    rfd::DevBuf d_fft_tiles, d_fft_ranges, d_fft_refs, d_fft_P, d_fft_X;
+    rfd::DevBuf d_fft_tiles, d_fft_refs, d_fft_P, d_fft_X;
     const float2 *fft_stw = nullptr; // stage twiddles of length 2048 (context-owned)
     int32_t fft_grid = 0, fft_L = 0, fft_nb = 0, fft_nbg = 0;
     int64_t fft_slot0 = 0, fft_nslots = 0;

@@ -1263,8 +1263,9 @@ rfd_status rfd_learned_taps(rfd_mlp *P, const double *psd_dev, const rfd_params 
 // header (ASCII), then the sections it lists, each at its offset from the end of the header
 // (64-byte aligned): FP32 master weights, Adam first and second moments, the per-network
 // normalisation (double [R][kNorm]: mu[4], sd[4], out_scale), the lags, the optimiser state
-// (Adam step, dynamic loss scale and its clean-step count) and the references'
-// autocorrelations C_r, which identify the grid, PSD and references the networks belong to.
+// (Adam step, dynamic loss scale and its clean-step count), the references' autocorrelations
+// C_r (which depend on the grid, the PSD and the references' bands) and the references' phase
+// constants, which together identify what the networks were trained for.
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -1290,7 +1291,8 @@ std::vector<CkptSection> ckpt_sections(const rfd_mlp *P) {
             {"norm", "f64", R, kNorm, (size_t)(R * kNorm * 8)},
             {"lag", "i32", R, 1, (size_t)(R * 4)},
             {"optimizer", "raw", 1, (int64_t)sizeof(MlpState), sizeof(MlpState)},
-            {"autocorr", "c128", R, kCw, (size_t)(R * kCw * 16)}};
+            {"autocorr", "c128", R, kCw, (size_t)(R * kCw * 16)},
+            {"references", "raw", R, (int64_t)sizeof(PNParams), (size_t)(R * sizeof(PNParams))}};
 }
 
 size_t align64(size_t x) { return (x + 63) / 64 * 64; }
@@ -1330,6 +1332,7 @@ rfd_status rfd_mlp_save(rfd_mlp *P, const char *path, void *stream) {
     RFD_TRY_CUDA(cudaMemcpy(&st, P->d_state.p, sizeof(st), cudaMemcpyDeviceToHost));
     std::memcpy(data[5].data(), &st, sizeof(st));
     RFD_TRY_CUDA(cudaMemcpy(data[6].data(), P->d_C.p, secs[6].bytes, cudaMemcpyDeviceToHost));
+    std::memcpy(data[7].data(), P->refs.data(), secs[7].bytes);
     char buf[512];
     std::string h = "{\"format\": \"librfd learned-tap networks\", \"version\": 1";
     std::snprintf(buf, sizeof(buf),
@@ -1409,7 +1412,9 @@ rfd_status rfd_mlp_load(rfd_mlp *P, const char *path, void *stream) {
     std::vector<char> C(secs[6].bytes);
     RFD_TRY_CUDA(cudaMemcpy(C.data(), P->d_C.p, C.size(), cudaMemcpyDeviceToHost));
     RFD_REQUIRE(std::memcmp(C.data(), data[6].data(), C.size()) == 0, RFD_ERR_ARG,
-                "mlp_load: the checkpoint was trained for other references or another PSD");
+                "mlp_load: the checkpoint was trained with another PSD or band");
+    RFD_REQUIRE(std::memcmp(P->refs.data(), data[7].data(), secs[7].bytes) == 0, RFD_ERR_ARG,
+                "mlp_load: the checkpoint was trained for other references");
     const int64_t R = P->R;
     const float *w = (const float *)data[0].data();
     for (int64_t i = 0; i < R * kP; ++i)

@@ -590,7 +590,10 @@ def test_very_loud_injection_does_not_overflow_the_split(ctx, kernel, opts):
     very loud glitch or signal): its real part peaks 355 times above the rms of q_ref, past
     the FP16 range of a series scaled to an rms of 2^8 (65504 / 256 = 256 rms).  The split's
     scale is capped by the largest sample, so every trigger stays finite and matches the
-    oracle within the FP16x3 bound (the many windows the loud chirp lights up included)."""
+    oracle (the many windows the loud chirp lights up included).  Rounding in FP32 (the
+    reference's FFT, the accumulators) is relative to the largest values in flight, so here the
+    error at each trigger is bounded by EPS times the template's peak |z|, and by the 1e-3
+    target relative to the trigger's own |z|."""
     cfg = workload.small_config(1, n=1 << 20, inj_snr=(1e5, 1e5))
     bank, data = workload.make_workload(cfg)
     ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
@@ -608,7 +611,14 @@ def test_very_loud_injection_does_not_overflow_the_split(ctx, kernel, opts):
     n_or = n_oracle(sets, js)
     assert n_or > 20
     assert compare_triggers(trig, sets, TOL_TC, js, cfg.window) <= amb_cap(n_or)
-    assert snr_errors(trig, sets, js) < EPS[rfd.PREC_FP16X3]
+    assert snr_errors(trig, sets, js) < TOL_TC
+    for j in js:
+        ot = {x["t"]: x["z"] for x in sets[j][0]}
+        peak = max(abs(v) for v in ot.values())
+        for r in trig[trig["j"] == j]:
+            if int(r["t"]) in ot:
+                zg = complex(float(r["zr"]), float(r["zi"]))
+                assert abs(zg - ot[int(r["t"])]) <= EPS[rfd.PREC_FP16X3] * peak, (j, int(r["t"]))
 
 
 # --------------------------------------------------------------------------- bounded waits
