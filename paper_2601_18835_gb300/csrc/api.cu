@@ -128,7 +128,8 @@ static rfd_status plan_tl_tiles(rfd_plan *p, const std::vector<int32_t> &order, 
 }
 
 // Block-FFT tiles: per reference, up to 64 templates (order: by reference, then K), appended
-// to the plan's slot order.  Blocks of L = 2048 - K_max + 1 outputs, three per CTA item.
+// to the plan's slot order.  Blocks of L = 2048 - K_max + 1 outputs, four per CTA item; item
+// ranges per persistent CTA balance the templates transformed.
 static rfd_status plan_fft_tiles(rfd_plan *p, const std::vector<int32_t> &order, int num_sms,
                                  const rfd_plan_options &opt) {
     if (order.empty()) return RFD_OK;
@@ -158,12 +159,16 @@ static rfd_status plan_fft_tiles(rfd_plan *p, const std::vector<int32_t> &order,
     p->fft_flops = (double)p->fft_nslots * p->fft_nb * M * (6.0 + 5.0 * log2m) +
                    (double)p->fft_refs.size() * p->fft_nb * M * 5.0 * log2m;
     const int64_t ntiles = (int64_t)p->fft_tiles.size();
-    // persistent CTAs, one per SM; items are dealt out interleaved (see rf_fft.cu)
+    std::vector<double> cost(ntiles);
+    for (int64_t t = 0; t < ntiles; ++t) cost[t] = (double)p->fft_tiles[t].count + 0.5;
     const int64_t G = std::max<int64_t>(1, std::min<int64_t>(opt.grid_ctas > 0 ? opt.grid_ctas : num_sms,
                                                            ntiles * p->fft_nbg));
+    const std::vector<int64_t> ranges = balanced_ranges(cost, p->fft_nbg, G);
     p->fft_grid = (int32_t)G;
     RFD_TRY(fft_stage_twiddles32(p->ctx, 11, &p->fft_stw, 0));
     RFD_TRY_CUDA(cudaStreamSynchronize(0));
+    RFD_TRY(ensure(p->d_fft_ranges, (G + 1) * sizeof(int64_t)));
+    RFD_TRY_CUDA(cudaMemcpy(p->d_fft_ranges.p, ranges.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
     RFD_TRY(ensure(p->d_fft_tiles, ntiles * sizeof(FftTile)));
     RFD_TRY_CUDA(
         cudaMemcpy(p->d_fft_tiles.p, p->fft_tiles.data(), ntiles * sizeof(FftTile), cudaMemcpyHostToDevice));
@@ -799,6 +804,7 @@ void rfd_plan_destroy(rfd_plan *plan) {
     release(plan->d_tl_ranges);
     release(plan->d_tl_taps);
     release(plan->d_fft_tiles);
+    release(plan->d_fft_ranges);
     release(plan->d_fft_refs);
     release(plan->d_fft_P);
     release(plan->d_fft_X);

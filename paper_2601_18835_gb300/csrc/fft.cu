@@ -322,45 +322,53 @@ __global__ void __launch_bounds__(512) k_fft_rows(const typename Cplx<T>::type *
 // never written).  Pass A also forms each block's share of sigma_j^2 = sum_k Wt[k] |h_j[k]|^2
 // (Wt = 4 df / S), summed per template in a fixed order afterwards.
 
-// First pass of pass A (ns = 1): element n1 of column c is k = n1 N2 + c0 + c.
+// First pass of pass A (ns = 1): element n1 = j + r lr of column c is k = n1 N2 + c0 + c, and
+// k < n/2 exactly when r < R/2 (j < lr = N1 / R), so the upper half of every butterfly is zero
+// and never loaded.  GW[k] = (Re G, Im G, Wt, 0).  Every load of the thread is issued before
+// any product is formed.
 template <int R, int EPT>
-__device__ __forceinline__ void fc_first_pass(float2 *S, int logL, int LP, int logC, const float2 *__restrict__ G,
-                                              const float *__restrict__ Wt, const float2 *__restrict__ h,
-                                              int64_t half, int64_t N2, int c0, float &psum) {
-    constexpr int NB = EPT / R, LOGR = Log2R<R>::v;
+__device__ __forceinline__ void fc_first_pass(float2 *S, int logL, int LP, int logC, const float4 *__restrict__ GW,
+                                              const float2 *__restrict__ h, int64_t N2, int c0, float &psum) {
+    constexpr int NB = EPT / R, LOGR = Log2R<R>::v, RH = R / 2;
     const int loglr = logL - LOGR, lr = 1 << loglr;
-    float2 v[NB][R];
+    float2 hv[NB][RH];
+    float4 gw[NB][RH];
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
         int c, j;
         butterfly_of<true>(threadIdx.x + q * blockDim.x, loglr, logC, c, j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < RH; ++r) {
             const int64_t k = (int64_t)(j + r * lr) * N2 + c0 + c;
-            float2 x = make_float2(0.f, 0.f);
-            if (k < half) {
-                const float2 hv = h[k];
-                const float2 g = G[k];
-                // g conj(h)
-                x = make_float2(g.x * hv.x + g.y * hv.y, g.y * hv.x - g.x * hv.y);
-                psum += Wt[k] * (hv.x * hv.x + hv.y * hv.y);
-            }
-            v[q][r] = x;
+            hv[q][r] = h[k];
+            gw[q][r] = GW[k];
         }
     }
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
         int c, j;
         butterfly_of<true>(threadIdx.x + q * blockDim.x, loglr, logC, c, j);
-        dft_reg<float, R, true>(v[q]);
+        float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) S[tile_pos(c, (j << LOGR) + r, LP)] = v[q][r];
+        for (int r = 0; r < R; ++r) {
+            if (r < RH) {
+                const float2 x = hv[q][r];
+                const float4 g = gw[q][r];
+                psum += g.z * (x.x * x.x + x.y * x.y);
+                v[r] = make_float2(g.x * x.x + g.y * x.y, g.y * x.x - g.x * x.y);   // g conj(h)
+            } else {
+                v[r] = make_float2(0.f, 0.f);
+            }
+        }
+        dft_reg<float, R, true>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) S[tile_pos(c, (j << LOGR) + r, LP)] = v[r];
     }
 }
 
 // Pass A of FINDCHIRP: template b's spectrum formed on the fly; y[k1 N2 + n2]; sigma^2 partials.
 template <int EPT>
-__global__ void __launch_bounds__(256) k_fc_cols(const float2 *__restrict__ G, const float *__restrict__ Wt,
+__global__ void __launch_bounds__(256) k_fc_cols(const float4 *__restrict__ GW,
                                                  const float2 *__restrict__ h, int64_t nf, float2 *__restrict__ y,
                                                  int logN1, int logN2, int logC, int sh,
                                                  const float2 *__restrict__ stage, const float2 *__restrict__ tw_lo,
@@ -383,10 +391,10 @@ __global__ void __launch_bounds__(256) k_fc_cols(const float2 *__restrict__ G, c
     const int R0 = (logN1 & 3) ? (1 << (logN1 & 3)) : 16;
     float psum = 0.f;
     const float2 *hb = h + b * nf;
-    if (R0 == 2) fc_first_pass<2, EPT>(S, logN1, LP, logC, G, Wt, hb, n / 2, N2, c0, psum);
-    else if (R0 == 4) fc_first_pass<4, EPT>(S, logN1, LP, logC, G, Wt, hb, n / 2, N2, c0, psum);
-    else if (R0 == 8) fc_first_pass<8, EPT>(S, logN1, LP, logC, G, Wt, hb, n / 2, N2, c0, psum);
-    else fc_first_pass<16, EPT>(S, logN1, LP, logC, G, Wt, hb, n / 2, N2, c0, psum);
+    if (R0 == 2) fc_first_pass<2, EPT>(S, logN1, LP, logC, GW, hb, N2, c0, psum);
+    else if (R0 == 4) fc_first_pass<4, EPT>(S, logN1, LP, logC, GW, hb, N2, c0, psum);
+    else if (R0 == 8) fc_first_pass<8, EPT>(S, logN1, LP, logC, GW, hb, N2, c0, psum);
+    else fc_first_pass<16, EPT>(S, logN1, LP, logC, GW, hb, N2, c0, psum);
     __syncthreads();
     const float2 *st = mid_passes<float, EPT, true>(S, logN1, LP, stw, R0);
     last_pass<float, 16, EPT, true, true>(S, logN1, LP, logC, st, y + b * n + c0, N2, c0, sh, lo, hi);
@@ -448,12 +456,14 @@ __global__ void __launch_bounds__(256) k_fc_rows(const float2 *__restrict__ y, i
     }
 }
 
-// sig2[row] = the row's pass-A partials summed in index order (one thread: a few hundred terms).
+// sig2[row] = the row's pass-A partials summed in a fixed order: one warp per row, lane l sums
+// the partials l, l + 32, ..., then a fixed shuffle tree.
 __global__ void k_fc_sum(const double *__restrict__ part, int64_t nparts, double *__restrict__ sig2) {
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
     double t = 0.0;
-    for (int64_t i = 0; i < nparts; ++i) t += part[blockIdx.x * nparts + i];
-    sig2[blockIdx.x] = t;
+    for (int64_t i = lane; i < nparts; i += 32) t += part[blockIdx.x * nparts + i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sig2[blockIdx.x] = t;
 }
 
 template <typename T>
@@ -615,10 +625,10 @@ rfd_status fft_c2c(rfd_ctx *ctx, int64_t n, int64_t batch, const typename Cplx<T
     return RFD_OK;
 }
 
-// FINDCHIRP over templates h (complex64 [J][nf]) with the weights G, Wt (length n/2): pass A
+// FINDCHIRP over templates h (complex64 [J][nf]) with the weights GW (length n/2): pass A
 // into tmp (J n complex64), sigma^2 per template, pass B with the trigger epilogue.  n must be
 // in [2^12, 2^22].
-rfd_status findchirp_fused(rfd_ctx *ctx, int64_t n, int64_t J, const float2 *G, const float *Wt, const float2 *h,
+rfd_status findchirp_fused(rfd_ctx *ctx, int64_t n, int64_t J, const float4 *GW, const float2 *h,
                            int64_t nf, int32_t j0, float thr, int32_t W, float2 *tmp, double *part,
                            double *sig2, rfd_candidate *cand, int64_t cap, int64_t *count, cudaStream_t s) {
     int log2n = 0;
@@ -649,7 +659,7 @@ rfd_status findchirp_fused(rfd_ctx *ctx, int64_t n, int64_t J, const float2 *G, 
     for (int64_t b0 = 0; b0 < J; b0 += 65535) {
         const int64_t nb = std::min<int64_t>(65535, J - b0);
         const dim3 gA((unsigned)(N2 >> logCA), (unsigned)nb), gB((unsigned)(N1 >> logCB), (unsigned)nb);
-        k_fc_cols<EPT><<<gA, thA, shA, s>>>(G, Wt, h + b0 * nf, nf, tmp, logN1, logN2, logCA, sh, stA, tw, hi, part);
+        k_fc_cols<EPT><<<gA, thA, shA, s>>>(GW, h + b0 * nf, nf, tmp, logN1, logN2, logCA, sh, stA, tw, hi, part);
         RFD_LAUNCH_CHECK();
         k_fc_sum<<<(unsigned)nb, 32, 0, s>>>(part, (int64_t)gA.x, sig2);
         RFD_LAUNCH_CHECK();

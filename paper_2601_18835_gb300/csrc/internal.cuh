@@ -127,10 +127,10 @@ rfd_status fft_c2c(rfd_ctx *ctx, int64_t n, int64_t batch, const typename Cplx<T
 // base_p + (r - 1) ns + k), FP32, cached in the context.
 rfd_status fft_stage_twiddles32(rfd_ctx *ctx, int logL, const float2 **out, cudaStream_t s);
 // FINDCHIRP (Eq. 1) for J templates h (complex64 [J][nf]) in two fused passes (fft.cu): the
-// spectrum G[k] conj(h[k]) (G = 4 df d / S on the data band, Wt = 4 df / S, both of length
-// n/2) formed inside the first FFT pass, z = q / sigma with the trigger epilogue inside the
-// last.  tmp: J n complex64; part: J x 2048 doubles; sig2: J doubles (sigma^2 per template).
-rfd_status findchirp_fused(rfd_ctx *ctx, int64_t n, int64_t J, const float2 *G, const float *Wt, const float2 *h,
+// spectrum G[k] conj(h[k]) formed inside the first FFT pass from GW[k] = (Re G, Im G, Wt, 0),
+// G = 4 df d / S on the data band and Wt = 4 df / S (length n/2), z = q / sigma with the trigger
+// epilogue inside the last.  tmp: J n complex64; part: J x 2048 doubles; sig2: J doubles.
+rfd_status findchirp_fused(rfd_ctx *ctx, int64_t n, int64_t J, const float4 *GW, const float2 *h,
                            int64_t nf, int32_t j0, float thr, int32_t W, float2 *tmp, double *part,
                            double *sig2, rfd_candidate *cand, int64_t cap, int64_t *count, cudaStream_t s);
 
@@ -240,7 +240,7 @@ struct rfd_plan {
     // block-FFT path (rf_fft.cu): templates with fft_k < K <= 1024
     std::vector<FftTile> fft_tiles;
     std::vector<int32_t> fft_refs;   // references with block-FFT templates
-    rfd::DevBuf d_fft_tiles, d_fft_refs, d_fft_P, d_fft_X;
+    rfd::DevBuf d_fft_tiles, d_fft_ranges, d_fft_refs, d_fft_P, d_fft_X;
     const float2 *fft_stw = nullptr; // stage twiddles of length 2048 (context-owned)
     int32_t fft_grid = 0, fft_L = 0, fft_nb = 0, fft_nbg = 0;
     int64_t fft_slot0 = 0, fft_nslots = 0;

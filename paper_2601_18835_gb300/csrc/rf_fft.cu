@@ -11,9 +11,7 @@
 //   z_j[(u_0 + l + off_j) mod n] = sum_k X_b[k] P_j[k] exp(+2 pi i k l / M),
 //   X_b[k] = sum_i x_b[i] exp(-2 pi i k i / M)      (per reference and block, every segment),
 //   P_j[k] = (1/M) sum_m c_j[m] exp(+2 pi i k m / M) (per template, when the taps are set).
-// A CTA holds three 128-thread groups, one block b each; CTA g of G takes the items (tile,
-// group of three blocks) g, g + G, g + 2G, ... so that the CTAs in flight share a tile and
-// its template spectra come from L2.  The templates of a tile stream
+// A CTA holds three 128-thread groups, one block b each.  The templates of a tile stream
 // through a two-buffer ring in shared memory (bulk copies completing on mbarriers; a buffer is
 // refilled once every group has released it, so the groups never wait for one another as a
 // whole); every group multiplies its X_b, kept in registers, by P_j, runs the inverse
@@ -174,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_block_spectra(const void *__restri
 
 struct RfFftArgs {
     const FftTile *tiles;
-    int64_t n_items;            // item = tile * nbg + block group; CTA g takes items g, g + G, ...
+    const int64_t *ranges;      // item ranges per CTA; item = tile * nbg + block group
     int32_t nbg, nb, L;
     int64_t out_len;            // outputs of the window
     const int64_t *u_begin;     // first output position of the window (device), or NULL
@@ -227,12 +225,11 @@ __global__ void __launch_bounds__(kFThreads, 1) k_rf_fft(const RfFftArgs a) {
     __syncthreads();
     float2 w2[16], w3[16];
     load_twiddles(w2, w3, tw, t);
+    const int64_t it0 = a.ranges[blockIdx.x], it1 = a.ranges[blockIdx.x + 1];
     const int64_t ubase = window_base(a.u_begin, a.n);
     uint32_t tq = 0;                            // templates this CTA has started (ring position)
     uint32_t last0 = 0xffffffffu, last1 = 0xffffffffu;   // thread 0: last template copied per buffer
-    // interleaved items: at any time the CTAs work on neighbouring block groups of the same
-    // tile, so a tile's template spectra are read from DRAM once and then served by L2
-    for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    for (int64_t it = it0; it < it1; ++it) {
         const int64_t ti = it / a.nbg;
         const int bg = (int)(it - ti * a.nbg);
         const FftTile tile = a.tiles[ti];
@@ -414,7 +411,7 @@ rfd_status fft_launch(const rfd_plan *plan, const void *q, const int32_t *qscale
     RFD_LAUNCH_CHECK();
     RfFftArgs a;
     a.tiles = (const FftTile *)plan->d_fft_tiles.p;
-    a.n_items = (int64_t)plan->fft_tiles.size() * plan->fft_nbg;
+    a.ranges = (const int64_t *)plan->d_fft_ranges.p;
     a.nbg = plan->fft_nbg;
     a.nb = plan->fft_nb;
     a.L = plan->fft_L;

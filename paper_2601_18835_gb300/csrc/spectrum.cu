@@ -173,20 +173,19 @@ __global__ void k_finalize_split(const float2 *__restrict__ q, int64_t n, int64_
     base[3 * ld + m] = il;
 }
 
-// FINDCHIRP weights, k < n/2: Wt = 4 df / S and G = Wt d on the data band [k_lo, n/2), 0 elsewhere.
+// FINDCHIRP weights, k < n/2: GW[k] = (Re G, Im G, Wt, 0) with Wt = 4 df / S and G = Wt d on the
+// data band [k_lo, n/2), 0 elsewhere.
 __global__ void k_fc_weights(const float2 *__restrict__ d, const double *__restrict__ psd, double df, int64_t k_lo,
-                             int64_t half, float2 *__restrict__ G, float *__restrict__ Wt) {
+                             int64_t half, float4 *__restrict__ GW) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= half) return;
-    float w = 0.f;
-    float2 g = make_float2(0.f, 0.f);
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
     if (k >= k_lo) {
-        w = (float)(4.0 * df) / (float)psd[k];
+        const float w = (float)(4.0 * df) / (float)psd[k];
         const float2 dv = d[k];
-        g = make_float2(w * dv.x, w * dv.y);
+        out = make_float4(w * dv.x, w * dv.y, w, 0.f);
     }
-    G[k] = g;
-    Wt[k] = w;
+    GW[k] = out;
 }
 
 }  // namespace
@@ -267,24 +266,23 @@ rfd_status filter_reference_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, c
 
 // FINDCHIRP over all templates in batches from stored templates, two fused kernels per batch
 // (fft.cu: findchirp_fused); candidates as in the ratio-filter epilogue.  Batches keep the
-// intermediate array near 128 MB so that it stays mostly in the 126 MB L2 between the passes.
+// intermediate array near 64 MB so that it stays in the 126 MB L2 between the passes.
 rfd_status findchirp_impl(rfd_ctx *ctx, const Grid &g, const float2 *d, const double *psd, const float2 *h,
                           int64_t J, int32_t W, float thr, rfd_candidate *cand, int64_t cap, int64_t *count,
                           cudaStream_t s) {
     const int64_t n = g.n, half = n / 2;
-    const int64_t B = std::max<int64_t>(1, std::min<int64_t>(J, ((int64_t)128 << 20) / (n * (int64_t)sizeof(float2))));
-    RFD_TRY(ensure(ctx->ws[1], (size_t)half * (sizeof(float2) + sizeof(float))));
+    const int64_t B = std::max<int64_t>(1, std::min<int64_t>(J, ((int64_t)64 << 20) / (n * (int64_t)sizeof(float2))));
+    RFD_TRY(ensure(ctx->ws[1], (size_t)half * sizeof(float4)));
     RFD_TRY(ensure(ctx->ws[2], (size_t)B * n * sizeof(float2)));
     RFD_TRY(ensure(ctx->ws[4], (size_t)B * 2048 * sizeof(double)));
     RFD_TRY(ensure(ctx->ws[5], (size_t)B * sizeof(double)));
-    float2 *G = (float2 *)ctx->ws[1].p;
-    float *Wt = (float *)(G + half);
+    float4 *GW = (float4 *)ctx->ws[1].p;
     RFD_TRY_CUDA(cudaMemsetAsync(count, 0, sizeof(int64_t), s));
-    k_fc_weights<<<(unsigned)((half + 255) / 256), 256, 0, s>>>(d, psd, g.df, g.k_lo, half, G, Wt);
+    k_fc_weights<<<(unsigned)((half + 255) / 256), 256, 0, s>>>(d, psd, g.df, g.k_lo, half, GW);
     RFD_LAUNCH_CHECK();
     for (int64_t j0 = 0; j0 < J; j0 += B) {
         const int64_t b = std::min<int64_t>(B, J - j0);
-        RFD_TRY(findchirp_fused(ctx, n, b, G, Wt, h + j0 * g.nf, g.nf, (int32_t)j0, thr, W, (float2 *)ctx->ws[2].p,
+        RFD_TRY(findchirp_fused(ctx, n, b, GW, h + j0 * g.nf, g.nf, (int32_t)j0, thr, W, (float2 *)ctx->ws[2].p,
                                 (double *)ctx->ws[4].p, (double *)ctx->ws[5].p, cand, cap, count, s));
     }
     return RFD_OK;
