@@ -30,8 +30,6 @@ rfd_status tl_launch(const rfd_plan *, const void *, const int32_t *, const int6
                      cudaStream_t);
 uint32_t tl_ystride(int32_t kpad_max);
 uint32_t tl_qwin(int32_t kpad_max);
-int tl_interleaved(int32_t kpad_max);
-uint32_t tl_tile_image_bytes(int32_t nch, int il);
 int tl_rows_per_item();
 int tl_tile_templates();
 rfd_status tc_launch(const rfd_plan *, const void *, const int32_t *, const int64_t *, rfd_candidate *, int64_t,
@@ -82,8 +80,6 @@ static rfd_status plan_tl_tiles(rfd_plan *p, const std::vector<int32_t> &order, 
     const int32_t nt = tl_tile_templates();
     int64_t taps_off = 0;
     int32_t kpad_max = 0;
-    for (int32_t j : order) kpad_max = std::max(kpad_max, 16 * ((p->k_of[j] + 15) / 16));
-    p->tl_il = tl_interleaved(kpad_max) != 0;
     size_t i = 0;
     while (i < order.size()) {
         const int32_t r = p->ref_of[order[i]];
@@ -102,9 +98,10 @@ static rfd_status plan_tl_tiles(rfd_plan *p, const std::vector<int32_t> &order, 
         t.kpad = 16 * t.nk16;
         t.nt = nt;
         t.nch = (t.kpad + 63) / 64;
-        t.taps_bytes = (int32_t)tl_tile_image_bytes(t.nch, p->tl_il ? 1 : 0);
+        t.taps_bytes = t.nch * 2 * 3 * nt * 128;
         t.taps_off = taps_off;
         taps_off += t.taps_bytes;
+        kpad_max = std::max(kpad_max, t.kpad);
         p->tl_tiles.push_back(t);
         p->executed_flops += (double)n_tb * t.nk16 * 6.0 * 2.0 * 128.0 * (double)tl_rows_per_item() * 16.0;
     }

@@ -232,7 +232,6 @@ struct rfd_plan {
     rfd::DevBuf d_tl_tiles, d_tl_ranges, d_tl_taps;
     int32_t tl_grid = 0;
     uint32_t tl_ystride = 0, tl_qwin = 0;
-    bool tl_il = false;              // interleaved real / imaginary rows (taps up to 256)
     rfd::DevBuf d_ranges;            // int64 [tc_grid + 1] item ranges per CTA
     uint32_t tc_taps_cap = 0, tc_win = 0;
     int32_t tc_grid = 0;

@@ -4,19 +4,11 @@
 // For a tile of 64 templates of one reference and one item of 256 output positions
 // u0 .. u0+255:
 //   D[row, u] = sum_k A[row, k] q[u0 + u + k]      (Eq. 3 with P = reversed, scaled taps)
-// where every row is the real or the imaginary part of one template:
-//   D = A1 Qr^T + A2 Qi^T,  A1 = Pr on real rows, Pi on imaginary rows,
-//                           A2 = -Pi on real rows, Pr on imaginary rows,
+// with rows 0..63 the real parts and rows 64..127 the imaginary parts of the 64 templates:
+//   D = [Pr; Pi] Qr^T + [-Pi; Pr] Qi^T,
 // each as three products hi*hi + hi*lo + lo*hi of the FP16 (BF16) splits, FP32 accumulation in
-// tensor memory; every MMA is M = 128, N = 256, K = 16 (full rate).  Two row layouts:
-//  * interleaved (the plan's taps up to 256): lane quarter g of tensor memory holds rows
-//    32 g .. 32 g + 15 = real parts of templates 16 g .. 16 g + 15 and the next 16 rows their
-//    imaginary parts; the taps image holds A1 and A2 as two 128-row blocks.  An epilogue warp
-//    then has both parts of its templates and swaps halves of each chunk by warp shuffles.
-//  * split (longer taps, where the larger image would not fit in shared memory): rows 0..63
-//    real, 64..127 imaginary; the image holds [-Pi; Pr; Pi] once and the two A operands are its
-//    rows 0..127 and 64..191; the real-row and imaginary-row warps swap halves through shared
-//    memory.  The products and their order are the same in both, so their sums are identical.
+// tensor memory.  The taps image holds the rows [-Pi; Pr; Pi] once, so the two A operands are
+// its rows 0..127 and 64..191; every MMA is M = 128, N = 256, K = 16 (full rate).
 //
 // The time operand B[u, k] = q[u0 + u + k] is a Hankel matrix.  It is not materialised:
 // shared memory holds Y[r] = q[u0 + r .. u0 + r + 7] (16 bytes per row, an eight-fold copy of
@@ -55,9 +47,8 @@ constexpr int kN = 256;                 // output positions per item (MMA N)
 constexpr int kNT = 64;                 // templates per tile
 constexpr int kThreads = 512;
 constexpr int kAStages = 2;
-// one 64-tap chunk of the taps image, hi or lo: 256 rows (interleaved) or 192 rows (split) of 128 B
-__host__ __device__ constexpr uint32_t chunk_img(int il) { return (il ? 4u : 3u) * kNT * 128u; }
-__host__ __device__ constexpr uint32_t chunk_bytes(int il) { return 2u * chunk_img(il); }  // hi + lo
+constexpr uint32_t kChunkImg = 3u * kNT * 128u;      // one 64-tap chunk, hi or lo: 24 KB
+constexpr uint32_t kChunkBytes = 2u * kChunkImg;     // hi + lo: 48 KB
 constexpr uint32_t kSpin = 1u << 22;
 constexpr uint32_t kSpinStall = 1u << 12;            // RFD_DEBUG_STALL_TAPS: give up quickly
 
@@ -144,16 +135,15 @@ __device__ __forceinline__ void emit_one(uint32_t j, uint32_t w, uint32_t pbits,
     }
 }
 
-template <int BF16, int IL>
+template <int BF16>
 __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
-    constexpr uint32_t kChunkImg = chunk_img(IL), kChunkBytes = chunk_bytes(IL);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *s_a = sm;                                              // kAStages x 48 KB
     uint8_t *s_y = sm + kAStages * kChunkBytes;                     // 2 buffers x 4 planes
     uint16_t *s_qw = (uint16_t *)(s_y + 2u * 4u * A.ystride);       // 2 buffers x 4 planes
-    float *s_x = (float *)(s_qw + 2u * 4u * A.qwin);                // split: 4 pairs x 2 x 32 x 17
-    uint64_t *bars = (uint64_t *)(s_x + (IL ? 0 : 4 * 2 * 32 * 17));
+    float *s_x = (float *)(s_qw + 2u * 4u * A.qwin);                // 4 pairs x 2 x 32 x 17
+    uint64_t *bars = (uint64_t *)(s_x + 4 * 2 * 32 * 17);
     uint32_t *s_misc = (uint32_t *)(bars + kNumBars);
     volatile uint32_t *abort_flag = &s_misc[1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -303,8 +293,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                         fence_after();
                     }
                     const uint32_t ah = a_base + st * kChunkBytes, al = ah + kChunkImg;
-                    // A1 (for Qr) and A2 (for Qi): two blocks of the image, or overlapping rows
-                    const uint32_t a1 = IL ? 0u : kNT * 128u, a2 = IL ? 2u * kNT * 128u : 0u;
                     const int s_end = min(4, T.nk16 - 4 * c);
                     for (int s = 0; s < s_end; ++s) {
                         if (c == T.nch - 1 && s == s_end - 1 && it + 1 < it1) {
@@ -318,8 +306,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                             go_seen = true;
                         }
                         const uint32_t o = (uint32_t)s * 32u;
-                        const uint64_t A2h = desc_sw128(ah + a2 + o), A2l = desc_sw128(al + a2 + o);
-                        const uint64_t A1h = desc_sw128(ah + a1 + o), A1l = desc_sw128(al + a1 + o);
+                        const uint64_t A2h = desc_sw128(ah + o), A2l = desc_sw128(al + o);               // [-Pi; Pr]
+                        const uint64_t A1h = desc_sw128(ah + kNT * 128u + o), A1l = desc_sw128(al + kNT * 128u + o);  // [Pr; Pi]
                         const uint32_t yk = y0 + (uint32_t)(64 * c + 16 * s) * 16u;
                         const uint64_t Qrh = desc_hankel(yk), Qih = desc_hankel(yk + A.ystride);
                         const uint64_t Qrl = desc_hankel(yk + 2u * A.ystride), Qil = desc_hankel(yk + 3u * A.ystride);
@@ -390,18 +378,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
             }
         }
     } else if (warp >= 8) {
-        // ------------------------------------------------------------ epilogue
+        // ------------------------------------------------------------ epilogue (pairs)
         const uint32_t lq = (uint32_t)warp & 3u;             // TMEM lane quarter
         const int half = (warp - 8) >> 2;                    // which 128 of the 256 columns
-        // interleaved: lanes 0..15 hold real rows, 16..31 the imaginary rows of the same 16
-        // templates; split: quarters 0, 1 real rows and 2, 3 imaginary rows, the two warps of a
-        // pair (same templates) swapping halves through shared memory
-        const bool is_re = IL ? lane < 16 : lq < 2u;
+        const bool is_re = lq < 2u;
         const int pair = (int)(lq & 1u) + 2 * half;
-        // split: Xs what this warp hands over (Re of columns 16..31, or Im of columns 0..15), Xr what it gets
+        // Xs: what this warp hands over (Re of columns 16..31, or Im of columns 0..15); Xr: what it gets
         float *Xs = s_x + (pair * 2 + (is_re ? 0 : 1)) * 32 * 17;
         const float *Xr = s_x + (pair * 2 + (is_re ? 1 : 0)) * 32 * 17;
-        const int col_off = is_re ? 0 : 16;                  // this lane's 16 columns of each chunk
+        const int col_off = is_re ? 0 : 16;                  // this warp's 16 columns of each chunk
         const uint32_t tlane = (lq * 32u) << 16;
         uint32_t li = 0;
         bool valid = false;
@@ -415,11 +400,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
         int64_t ti = it0 / A.n_tb, tb = it0 - ti * A.n_tb, prev = -1;
         for (int64_t it = it0; it < it1; ++it, ++li, tb = (tb + 1 == A.n_tb) ? 0 : tb + 1, ti += (tb == 0)) {
             if (ti != prev) {
-                // this lane's template: interleaved a = 16 quarter + lane mod 16; split a =
-                // 32 (quarter & 1) + lane, the same in both warps of the pair
+                // this lane's template: a = 32 (quarter & 1) + lane, the same in both warps of the pair
                 prev = ti;
                 const TcTile T = A.tiles[ti];
-                const int a = IL ? 16 * (int)lq + (lane & 15) : 32 * (int)(lq & 1u) + lane;
+                const int a = 32 * (int)(lq & 1u) + lane;
                 const int64_t slot = (int64_t)T.first + (a < T.count ? a : 0);
                 sc = a < T.count ? A.scale[slot] * ldexpf(1.0f, -A.qscale[T.ref]) : 0.f;
                 valid = a < T.count && sc > 0.f;
@@ -446,33 +430,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                 }
                 // static register indices only (a runtime index would put v in local memory)
                 float re[16], im[16];
-                if (IL) {
-                    // a real-row lane keeps its columns 0..15 and takes the imaginary parts of
-                    // them from lane + 16; an imaginary-row lane keeps its columns 16..31
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float lo = __uint_as_float(v[i]), hi = __uint_as_float(v[16 + i]);
-                        const float other = __shfl_xor_sync(0xffffffffu, is_re ? hi : lo, 16);
-                        re[i] = is_re ? lo : other;
-                        im[i] = is_re ? other : hi;
-                    }
-                } else {
+                for (int i = 0; i < 16; ++i) {
+                    const float lo = __uint_as_float(v[i]), hi = __uint_as_float(v[16 + i]);
+                    Xs[lane * 17 + i] = is_re ? hi : lo;
+                    re[i] = lo;       // the real warp keeps its columns 0..15,
+                    im[i] = hi;       // the imaginary warp its columns 16..31
+                }
+                named_sync(1u + (uint32_t)pair, 64u);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float lo = __uint_as_float(v[i]), hi = __uint_as_float(v[16 + i]);
-                        Xs[lane * 17 + i] = is_re ? hi : lo;
-                        re[i] = lo;       // the real warp keeps its columns 0..15,
-                        im[i] = hi;       // the imaginary warp its columns 16..31
-                    }
-                    named_sync(1u + (uint32_t)pair, 64u);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float other = Xr[lane * 17 + i];
-                        if (is_re) {
-                            im[i] = other;
-                        } else {
-                            re[i] = other;
-                        }
+                for (int i = 0; i < 16; ++i) {
+                    const float other = Xr[lane * 17 + i];
+                    if (is_re) {
+                        im[i] = other;
+                    } else {
+                        re[i] = other;
                     }
                 }
                 if (valid) {
@@ -520,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                         if (bw != 0xffffffffu) emit_one((uint32_t)j, bw, bp, bt, bzr, bzi, A.cand, A.cap, A.count);
                     }
                 }
-                if (!IL) named_sync(5u + (uint32_t)pair, 64u);     // the buffers are free for the next chunk
+                named_sync(5u + (uint32_t)pair, 64u);     // the buffers are free for the next chunk
             }
         }
     }
@@ -546,12 +518,10 @@ __device__ __forceinline__ float fromh(__half x) { return __half2float(x); }
 __device__ __forceinline__ float fromh(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // One block per tile: per-template power-of-two scale (max |component| * 2^e < 2^8), then the
-// A-operand image [chunk][hl][row][128 B]; element e of chunk c holds reversed tap k = 64 c + e,
-// 16-byte units XOR-swizzled by row % 8.  Rows, interleaved: A1 then A2, 128 rows each, row
-// 32 g + 16 m + i of a block belonging to template 16 g + i (m = 0 real-part row: A1 Pr, A2 -Pi;
-// m = 1 imaginary-part row: A1 Pi, A2 Pr); split: [-Pi (64); Pr (64); Pi (64)].  Also the per-slot
-// lag offset and normalisation.
-template <typename H, int IL>
+// A-operand image [chunk][hl][row][128 B], rows [-Pi (64); Pr (64); Pi (64)]; element e of
+// chunk c holds reversed tap k = 64 c + e, 16-byte units XOR-swizzled by row % 8.  Also the
+// per-slot lag offset and normalisation.
+template <typename H>
 __global__ void __launch_bounds__(256) k_pack_tl(const TcTile *__restrict__ tiles, const float2 *__restrict__ taps,
                                                  int32_t k_stride, const int32_t *__restrict__ perm,
                                                  const int32_t *__restrict__ kslot, const int32_t *__restrict__ lag,
@@ -586,7 +556,7 @@ __global__ void __launch_bounds__(256) k_pack_tl(const TcTile *__restrict__ tile
         }
     }
     __syncthreads();
-    const int rows = (IL ? 4 : 3) * kNT;
+    const int rows = 3 * kNT;
     const int64_t total = (int64_t)T.nch * 2 * rows * 64;
     uint8_t *img = out + T.taps_off;
     for (int64_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -596,15 +566,7 @@ __global__ void __launch_bounds__(256) k_pack_tl(const TcTile *__restrict__ tile
         const int64_t r2 = r1 / rows;
         const int hl = (int)(r2 & 1);
         const int c = (int)(r2 >> 1);
-        int a, part;                                   // part 0: -Pi, 1: Pr, 2: Pi
-        if (IL) {
-            const int blk = row >> 7, rr = row & 127, m = (rr >> 4) & 1;
-            a = 16 * (rr >> 5) + (rr & 15);
-            part = blk == 0 ? (m ? 2 : 1) : (m ? 1 : 0);
-        } else {
-            a = row % kNT;
-            part = row / kNT;
-        }
+        const int a = row % kNT, part = row / kNT;     // 0: -Pi, 1: Pr, 2: Pi
         const int k = 64 * c + e;
         uint16_t bits = 0;
         if (a < T.count && k < s_k[a]) {
@@ -631,14 +593,10 @@ __global__ void __launch_bounds__(256) k_pack_tl(const TcTile *__restrict__ tile
 uint32_t tl_ystride(int32_t kpad_max) { return (uint32_t)(kN - 8 + kpad_max) * 16u; }
 uint32_t tl_qwin(int32_t kpad_max) { return (uint32_t)(kN + kpad_max); }
 
-size_t tl_smem_bytes(uint32_t ystride, uint32_t qwin, int il) {
-    return 1024 + (size_t)kAStages * chunk_bytes(il) + 2u * 4u * ystride + 2u * 4u * qwin * 2u +
-           (il ? 0 : 4 * 2 * 32 * 17 * 4) + kNumBars * 8 + 16;
+size_t tl_smem_bytes(uint32_t ystride, uint32_t qwin) {
+    return 1024 + (size_t)kAStages * kChunkBytes + 2u * 4u * ystride + 2u * 4u * qwin * 2u + 4 * 2 * 32 * 17 * 4 +
+           kNumBars * 8 + 16;
 }
-
-// The interleaved layout when its larger taps image still fits in shared memory.
-int tl_interleaved(int32_t kpad_max) { return kpad_max <= 256 ? 1 : 0; }
-uint32_t tl_tile_image_bytes(int32_t nch, int il) { return (uint32_t)nch * chunk_bytes(il); }
 
 int tl_rows_per_item() { return kN; }
 int tl_tile_templates() { return kNT; }
@@ -647,20 +605,16 @@ rfd_status tl_pack(rfd_plan *plan, const float2 *taps, int32_t k_stride, const i
                    cudaStream_t s) {
     const unsigned ntiles = (unsigned)plan->tl_tiles.size();
     if (ntiles == 0) return RFD_OK;
-    const TcTile *tiles = (const TcTile *)plan->d_tl_tiles.p;
-    const int32_t *perm = (const int32_t *)plan->d_perm.p, *kslot = (const int32_t *)plan->d_kslot.p;
-    uint8_t *img = (uint8_t *)plan->d_tl_taps.p;
-    int32_t *off = (int32_t *)plan->d_off.p;
-    float *scale = (float *)plan->d_scale.p;
-    const int64_t n = plan->grid.n;
-#define RFD_PACK(H, IL) \
-    k_pack_tl<H, IL><<<ntiles, 256, 0, s>>>(tiles, taps, k_stride, perm, kslot, lag, sigma, n, img, off, scale)
-    if (plan->precision == RFD_PREC_FP16X3) {
-        if (plan->tl_il) RFD_PACK(__half, 1); else RFD_PACK(__half, 0);
-    } else {
-        if (plan->tl_il) RFD_PACK(__nv_bfloat16, 1); else RFD_PACK(__nv_bfloat16, 0);
-    }
-#undef RFD_PACK
+    if (plan->precision == RFD_PREC_FP16X3)
+        k_pack_tl<__half><<<ntiles, 256, 0, s>>>((const TcTile *)plan->d_tl_tiles.p, taps, k_stride,
+                                                  (const int32_t *)plan->d_perm.p, (const int32_t *)plan->d_kslot.p,
+                                                  lag, sigma, plan->grid.n, (uint8_t *)plan->d_tl_taps.p,
+                                                  (int32_t *)plan->d_off.p, (float *)plan->d_scale.p);
+    else
+        k_pack_tl<__nv_bfloat16><<<ntiles, 256, 0, s>>>(
+            (const TcTile *)plan->d_tl_tiles.p, taps, k_stride, (const int32_t *)plan->d_perm.p,
+            (const int32_t *)plan->d_kslot.p, lag, sigma, plan->grid.n, (uint8_t *)plan->d_tl_taps.p,
+            (int32_t *)plan->d_off.p, (float *)plan->d_scale.p);
     RFD_LAUNCH_CHECK();
     return RFD_OK;
 }
@@ -690,34 +644,22 @@ rfd_status tl_launch(const rfd_plan *plan, const void *q, const int32_t *qscale,
     a.qwin = plan->tl_qwin;
     a.stall = (plan->debug_flags & RFD_DEBUG_STALL_TAPS) ? 1u : 0u;
     a.spin = a.stall ? kSpinStall : kSpin;
-    const int il = plan->tl_il ? 1 : 0;
-    const size_t shm = tl_smem_bytes(a.ystride, a.qwin, il);
+    const size_t shm = tl_smem_bytes(a.ystride, a.qwin);
     const unsigned grid = (unsigned)plan->tl_grid;
-    // the attribute is raised once per device, precision and layout (never inside a capture:
-    // the search runs one step before it captures)
-    static size_t smem_set[64][2][2] = {};
+    static size_t smem_set[64][2] = {};
     const int dev = plan->ctx->device < 64 ? plan->ctx->device : 63;
     const int bf = plan->precision == RFD_PREC_FP16X3 ? 0 : 1;
-#define RFD_KERN(B, L) k_rf_tc_long<B, L>
-#define RFD_ATTR(B, L) \
-    RFD_TRY_CUDA(cudaFuncSetAttribute(RFD_KERN(B, L), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm))
-    if (shm > smem_set[dev][bf][il]) {
-        if (bf == 0) {
-            if (il) RFD_ATTR(0, 1); else RFD_ATTR(0, 0);
-        } else {
-            if (il) RFD_ATTR(1, 1); else RFD_ATTR(1, 0);
-        }
-        smem_set[dev][bf][il] = shm;
+    if (shm > smem_set[dev][bf]) {
+        if (bf == 0)
+            RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_tc_long<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        else
+            RFD_TRY_CUDA(cudaFuncSetAttribute(k_rf_tc_long<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        smem_set[dev][bf] = shm;
     }
-    if (bf == 0) {
-        if (il) k_rf_tc_long<0, 1><<<grid, kThreads, shm, s>>>(a);
-        else k_rf_tc_long<0, 0><<<grid, kThreads, shm, s>>>(a);
-    } else {
-        if (il) k_rf_tc_long<1, 1><<<grid, kThreads, shm, s>>>(a);
-        else k_rf_tc_long<1, 0><<<grid, kThreads, shm, s>>>(a);
-    }
-#undef RFD_ATTR
-#undef RFD_KERN
+    if (bf == 0)
+        k_rf_tc_long<0><<<grid, kThreads, shm, s>>>(a);
+    else
+        k_rf_tc_long<1><<<grid, kThreads, shm, s>>>(a);
     RFD_LAUNCH_CHECK();
     return RFD_OK;
 }
