@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--extra-configs", default="3,5",
                     help="also measure these configs (their own set-up, timed steps, e2e, roofline, oracle check) "
-                         "under 'more_configs' in a plain default run; '' for none")
+                         "under 'more_configs' in a plain default run; 'none' for none")
     ap.add_argument("--oracle-sample", type=int, default=0,
                     help="templates in the oracle check (0: 128 for banks up to 8192 templates, else 256)")
     ap.add_argument("--n-tmpl", type=int, default=None, help="smaller bank (profiling cases only)")
@@ -197,7 +197,9 @@ def roofline(prec, family, K, options, n, n_ref, secs, exec_flops, peaks, peak_k
         roof = {"bound": "tensor", "achieved": alg / secs / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
                 "peak_source": "%s bf16 dense %s (fp16 has the same dense rate)" % (
                     peak_kind, "sustained" if sustained else "burst"),
-                "ceiling_frac_three_products": 1.0 / 3.0 * peaks["bf16_tflops"] / peak_tf,
+                # three products per complex MAC: at most a third of the raw MMA rate (a probe measured
+                # 8188 flops per clock and SM for M = 128, N = 256, K = 16), here at 2070 MHz
+                "ceiling_frac_three_products": 8188.0 * 152 * 2.07e9 / 3.0 / (peak_tf * 1e12),
                 "executed_tflops": exec_flops / secs / 1e12,
                 "executed_frac": exec_flops / secs / 1e12 / peak_tf}
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -1077,8 +1079,20 @@ def measure(args, c, prec, precision_name, ws, rank, local, primary):
                                             "ms_per_step": fp32_ms, "ratio": (fp32_ms / ms_max)}
             s32.close()
         fc_value, fc_t, t_own, t_cufft, fc_n = findchirp_rate(cfg, bank, data, local)
+        peaks_fc, kind_fc = measured_peaks()
+        us_per = fc_t / fc_n * 1e6
+        # the bytes FINDCHIRP must move per template: its stored template (n/2 + 1 complex64);
+        # the two-pass intermediate of a 64 MB batch stays in L2
+        fc_bytes = 8.0 * (cfg.n // 2 + 1)
         comparisons["findchirp"] = {"value": fc_value, "unit": UNIT, "ms_per_step": fc_t * 1e3,
                                     "templates_timed": fc_n, "ratio": value / fc_value,
+                                    "us_per_template": us_per,
+                                    "roofline": {"bound": "hbm", "traffic_model": "template read, n/2+1 complex64",
+                                                 "bytes_per_template": fc_bytes,
+                                                 "achieved": fc_bytes / (us_per * 1e-6) / 1e9, "unit": "GB/s",
+                                                 "peak": peaks_fc["hbm_gbs"], "peak_source": kind_fc + " copy",
+                                                 "frac": fc_bytes / (us_per * 1e-6) / 1e9 / peaks_fc["hbm_gbs"]},
+                                    "vs_bare_ifft": us_per / (t_own * 1e6),
                                     "ifft_us_per_row_stockham": t_own * 1e6, "ifft_us_per_row_cufft": t_cufft * 1e6}
 
     cpu = err = None
@@ -1162,7 +1176,8 @@ def run_ours(args):
     line.update(head)
     # the larger single-GPU workloads, timed the same way, under their own key (the headline
     # stays the configured workload): only for a plain default run on one GPU
-    extra = [int(x) for x in args.extra_configs.split(",") if x.strip()] if args.extra_configs else []
+    ec = (args.extra_configs or "").strip().strip("'\"")
+    extra = [int(x) for x in ec.split(",") if x.strip()] if ec and ec != "none" else []
     plain = (args.config == 2 and not args.n_tmpl and not args.n_ref and not args.stream_block and args.taps ==
              "windowed" and args.long_k is None and args.fft_k is None and not args.no_graph)
     if ws == 1 and plain and extra:
