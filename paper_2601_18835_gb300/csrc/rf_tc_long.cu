@@ -18,19 +18,26 @@
 // 64-tap chunks by bulk copies; two accumulators in tensor memory let the epilogue drain one
 // item while the MMAs fill the next.
 //
-// Roles: warp 0 bulk copies (taps chunks and each item's q window), warp 1 issues the MMAs
-// (and owns the TMEM allocation), warps 4-7 expand the q window into Y (consecutive lanes on
-// consecutive rows: conflict-free), warps 8-15 drain: a warp of lane quarter 2/3 (imaginary
-// rows) and the warp of quarter 0/1 (real rows, same templates) swap half of each 32-column
-// chunk through shared memory, and each forms z, |z|^2 and the per-window maxima of its 16
-// columns.  The MMA thread waits once per item, on a barrier of the item's buffer that the
-// epilogue (accumulator free), the builders (Y built) and the producer (first taps chunk
-// landed) all arrive on; taps chunks already in their stage are not copied again.  Every wait
-// is bounded.  Each bulk copy completes on a barrier that only the producer arms (the first
-// chunk of an item on a barrier of its own, which the producer waits on before it arrives on
-// the item's barrier), so before the CTA ends the producer can wait for the last phase it
-// armed on each of them: no copy is still landing in shared memory when the CTA exits, also
-// after a wait has given up.
+// Roles: warp 0 bulk copies (taps chunks and each item's q window), lane 0 of warp 1 issues
+// the MMAs (warp 1 owns the TMEM allocation), warps 4-7 expand the q window into Y
+// (consecutive lanes on consecutive rows: conflict-free), warps 8-15 drain: a warp of lane
+// quarter 2/3 (imaginary rows) and the warp of quarter 0/1 (real rows, same templates) swap
+// half of each 32-column chunk through shared memory, and each forms z, |z|^2 and the
+// per-window maxima of its 16 columns.  The MMA thread waits once per item, on a barrier of
+// the item's buffer that the epilogue (accumulator free), the builders (Y built) and the
+// producer (first taps chunk landed) all arrive on.  The tensor pipe queues only a few MMAs
+// ahead of the issuing thread, so any hand-off that thread has to make between MMAs idles the
+// pipe; a tile of at most two 64-tap chunks (K <= 128) therefore stays resident in the two
+// stages, copied at its first item, with no per-chunk hand-off at all; longer taps stream
+// through the stages, each chunk released by a commit of the MMAs that read it.  At a tile
+// change the producer overwrites a stage only after a commit the MMA thread makes when it
+// leaves the previous tile, and it arrives on an item's go barrier only once the go phase of
+// the item two back (the same barrier) has completed.  Every wait is bounded.  Each bulk
+// copy completes on a barrier that only the producer arms (the first chunk of an item on a
+// barrier of its own, which the producer waits on before it arrives on the item's barrier),
+// so before the CTA ends the producer can wait for the last phase it armed on each of them:
+// no copy is still landing in shared memory when the CTA exits, also after a wait has given
+// up.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -63,7 +70,8 @@ enum {
     kBarQEmpty = 14,    // 2
     kBarDone = 16,
     kBarT0 = 17,        // 2: the first taps chunk of an item, per item buffer (producer only)
-    kNumBars = 19
+    kBarTile = 19,      // every MMA before a tile change has completed (one phase per change)
+    kNumBars = 20
 };
 
 struct TlArgs {
@@ -169,6 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
             mbar_init(BAR(kBarT0 + b), 1);
         }
         mbar_init(BAR(kBarDone), 1);
+        mbar_init(BAR(kBarTile), 1);
         s_misc[1] = 0u;
         mbar_fence_init();
     }
@@ -181,15 +190,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
     if (warp == 0) {
         // ------------------------------------------------------------ producer: taps chunks
         if (lane == 0) {
-            uint32_t ka = 0, li = 0;
+            uint32_t ka = 0, li = 0, ntc = 0;     // ka: streamed chunks so far; ntc: tile changes
             static_assert(kAStages == 2, "two A stages");
-            int64_t held0 = -1, held1 = -1;      // taps-image offset each A stage holds (-1: none)
             // phases armed so far on each barrier the copies complete on (for the final drain)
             uint32_t q_armed[2] = {0u, 0u}, a_armed[2] = {0u, 0u}, t0_armed[2] = {0u, 0u};
             int64_t ti = it0 / A.n_tb, tb = it0 - ti * A.n_tb, prev = -1;
             TcTile T{};
             for (int64_t it = it0; it < it1; ++it, ++li, tb = (tb + 1 == A.n_tb) ? 0 : tb + 1, ti += (tb == 0)) {
-                if (ti != prev) {
+                const bool first = ti != prev;    // the first item of a tile (tiles never recur in a range)
+                if (first) {
                     T = A.tiles[ti];
                     prev = ti;
                 }
@@ -204,34 +213,49 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                              A.q + (int64_t)(4 * T.ref + p) * A.ld + wrap_pos(ubase, tb * kN, A.n), wbytes,
                              BAR(kBarQFull + qb));
                 if (A.stall) continue;            // no taps: the item's go barrier never completes
+                const uint32_t ib = li & 1u;
+                // a new tile: every MMA before it has completed before a copy overwrites a stage
+                // (the MMA issuer commits once after the last item of each tile it leaves)
+                if (first && li > 0u) {
+                    if (!wait_bar(BAR(kBarTile), ntc & 1u, abort_flag, A.count, A.spin)) break;
+                    ++ntc;
+                }
+                // the go phase of item li - 2 (same barrier) has completed before this item's
+                // arrival below, so the arrivals of two items never meet in one phase
+                if (li >= 2u && !wait_bar(BAR(kBarGo + ib), ((li >> 1) & 1u) ^ 1u, abort_flag, A.count, A.spin))
+                    break;
                 bool ok = true;
+                if (T.nch <= kAStages) {
+                    // resident tile (K <= 128): chunk c stays in stage c for all of the tile's items,
+                    // copied at its first item (chunk 0 on the item's transaction barrier, chunk 1
+                    // on stage 1's); no per-chunk hand-off afterwards
+                    if (first) {
+                        for (int c = 0; c < T.nch; ++c) {
+                            const uint32_t full = c == 0 ? BAR(kBarT0 + ib) : BAR(kBarAFull + 1);
+                            mbar_arrive_expect_tx(full, kChunkBytes);
+                            const uint8_t *src = A.taps + T.taps_off + (int64_t)c * kChunkBytes;
+                            bulk_g2s(smem_u32(s_a + (uint32_t)c * kChunkBytes), src, kChunkImg, full);
+                            bulk_g2s(smem_u32(s_a + (uint32_t)c * kChunkBytes) + kChunkImg, src + kChunkImg, kChunkImg,
+                                     full);
+                            if (c > 0) ++a_armed[1];
+                        }
+                        const uint32_t par = t0_armed[ib]++ & 1u;
+                        if (!wait_bar(BAR(kBarT0 + ib), par, abort_flag, A.count, A.spin)) break;
+                    }
+                    mbar_arrive(BAR(kBarGo + ib));
+                    continue;
+                }
+                // streamed tile: chunks cycle through the stages, each released by the MMAs' commit
                 for (int c = 0; c < T.nch; ++c, ++ka) {
                     const uint32_t st = ka % kAStages, r = ka / kAStages;
                     if (!wait_bar(BAR(kBarAEmpty + st), (r & 1u) ^ 1u, abort_flag, A.count, A.spin)) {
                         ok = false;
                         break;
                     }
-                    const uint32_t ib = li & 1u;
-                    const int64_t want = T.taps_off + (int64_t)c * kChunkBytes;
-                    if ((st == 0u ? held0 : held1) == want) {
-                        // the stage already holds this chunk (a tile whose chunks all fit the
-                        // stages, as at K <= 128): no copy, only the phase
-                        if (c == 0) {
-                            mbar_arrive(BAR(kBarGo + ib));
-                        } else {
-                            mbar_arrive(BAR(kBarAFull + st));
-                            ++a_armed[st];
-                        }
-                        continue;
-                    }
-                    if (st == 0u)
-                        held0 = want;
-                    else
-                        held1 = want;
                     // chunk 0 completes on the item's own transaction barrier, later chunks on the stage's
                     const uint32_t full = c == 0 ? BAR(kBarT0 + ib) : BAR(kBarAFull + st);
                     mbar_arrive_expect_tx(full, kChunkBytes);
-                    const uint8_t *src = A.taps + want;
+                    const uint8_t *src = A.taps + T.taps_off + (int64_t)c * kChunkBytes;
                     bulk_g2s(smem_u32(s_a + st * kChunkBytes), src, kChunkImg, full);
                     bulk_g2s(smem_u32(s_a + st * kChunkBytes) + kChunkImg, src + kChunkImg, kChunkImg, full);
                     if (c == 0) {
@@ -263,17 +287,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            uint32_t ka = 0, li = 0, uf0 = 0, uf1 = 0;
+            uint32_t ka = 0, li = 0, uf0 = 0, uf1 = 0;      // ka: streamed chunks so far
             const uint32_t idn = idesc_f16(128, kN, BF16, 0);
             const uint32_t a_base = smem_u32(s_a), y_base = smem_u32(s_y);
+            const uint64_t yp = (uint64_t)(A.ystride >> 4);   // one Y plane in descriptor units
             int64_t ti = it0 / A.n_tb, tb = it0 - ti * A.n_tb, prev = -1;
             TcTile T{};
             bool go_seen = false;                 // the go barrier of this item was already waited on
             for (int64_t it = it0; it < it1; ++it, ++li, tb = (tb + 1 == A.n_tb) ? 0 : tb + 1, ti += (tb == 0)) {
-                if (ti != prev) {
+                const bool first = ti != prev;
+                if (first) {
                     prev = ti;
                     T = A.tiles[ti];
                 }
+                const bool resident = T.nch <= kAStages;
                 const uint32_t acc = li & 1u, yb = li & 1u, use = li >> 1;
                 // one wait: the accumulator is free, Y is built and chunk 0 of the taps is staged
                 if (!go_seen && !wait_bar(BAR(kBarGo + acc), use & 1u, abort_flag, A.count, A.spin)) break;
@@ -282,9 +309,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                 const uint32_t d = tmem + acc * (uint32_t)kN;
                 const uint32_t y0 = y_base + yb * 4u * A.ystride;
                 bool ok = true;
-                for (int c = 0; c < T.nch; ++c, ++ka) {
-                    const uint32_t st = ka % kAStages;
-                    if (c > 0) {
+                for (int c = 0; c < T.nch; ++c) {
+                    // a resident tile's chunk c sits in stage c (chunk 1 waited on at the tile's
+                    // first item only); a streamed chunk in stage ka mod 2
+                    const uint32_t st = resident ? (uint32_t)c : ka % kAStages;
+                    if (c > 0 && (!resident || first)) {
                         const uint32_t uf = st == 0u ? uf0++ : uf1++;
                         if (!wait_bar(BAR(kBarAFull + st), uf & 1u, abort_flag, A.count, A.spin)) {
                             ok = false;
@@ -292,12 +321,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                         }
                         fence_after();
                     }
+                    // descriptors of the chunk's first 16-tap step; a later step adds a constant
+                    // to the 14-bit start-address field (no carry: shared memory < 256 KB)
                     const uint32_t ah = a_base + st * kChunkBytes, al = ah + kChunkImg;
+                    const uint64_t dA2h = desc_sw128(ah), dA2l = desc_sw128(al);                              // [-Pi; Pr]
+                    const uint64_t dA1h = desc_sw128(ah + kNT * 128u), dA1l = desc_sw128(al + kNT * 128u);  // [Pr; Pi]
+                    const uint64_t dQ = desc_hankel(y0 + (uint32_t)(64 * c) * 16u);
                     const int s_end = min(4, T.nk16 - 4 * c);
                     for (int s = 0; s < s_end; ++s) {
-                        if (c == T.nch - 1 && s == s_end - 1 && it + 1 < it1) {
+                        if (c == T.nch - 1 && s == s_end - 1 && it + 1 < it1 && tb + 1 < A.n_tb) {
                             // the next item's go barrier, waited on while this item's earlier
-                            // MMAs still run (deadlock-free: it needs only work issued before)
+                            // MMAs still run (deadlock-free: it needs only work issued before;
+                            // not across a tile change, where the producer waits for this
+                            // item's MMAs before it arrives for the next one)
                             const uint32_t nli = li + 1u;
                             if (!wait_bar(BAR(kBarGo + (nli & 1u)), (nli >> 1) & 1u, abort_flag, A.count, A.spin)) {
                                 ok = false;
@@ -305,16 +341,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                             }
                             go_seen = true;
                         }
-                        const uint32_t o = (uint32_t)s * 32u;
-                        const uint64_t A2h = desc_sw128(ah + o), A2l = desc_sw128(al + o);               // [-Pi; Pr]
-                        const uint64_t A1h = desc_sw128(ah + kNT * 128u + o), A1l = desc_sw128(al + kNT * 128u + o);  // [Pr; Pi]
-                        const uint32_t yk = y0 + (uint32_t)(64 * c + 16 * s) * 16u;
-                        const uint64_t Qrh = desc_hankel(yk), Qih = desc_hankel(yk + A.ystride);
-                        const uint64_t Qrl = desc_hankel(yk + 2u * A.ystride), Qil = desc_hankel(yk + 3u * A.ystride);
-                        const uint32_t first = (c == 0 && s == 0) ? 0u : 1u;
+                        const uint64_t o = (uint64_t)(2 * s);            // 32 B along K in the taps rows
+                        const uint64_t A2h = dA2h + o, A2l = dA2l + o, A1h = dA1h + o, A1l = dA1l + o;
+                        const uint64_t Qrh = dQ + (uint64_t)(16 * s);    // 16 Y rows of 16 B
+                        const uint64_t Qih = Qrh + yp, Qrl = Qrh + 2u * yp, Qil = Qrh + 3u * yp;
+                        const uint32_t acc0 = (c == 0 && s == 0) ? 0u : 1u;
                         // the products and their order match the other kernel's (q_h p_h, q_h p_l,
                         // q_l p_h per plane), so both give bit-identical sums
-                        mma_ss(d, A1h, Qrh, idn, first);
+                        mma_ss(d, A1h, Qrh, idn, acc0);
                         mma_ss(d, A1l, Qrh, idn, 1u);
                         mma_ss(d, A1h, Qrl, idn, 1u);
                         mma_ss(d, A2h, Qih, idn, 1u);
@@ -322,11 +356,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                         mma_ss(d, A2h, Qil, idn, 1u);
                     }
                     if (!ok) break;
-                    mma_commit(BAR(kBarAEmpty + st));
+                    if (!resident) {
+                        mma_commit(BAR(kBarAEmpty + st));   // the stage may take the next chunk
+                        ++ka;
+                    }
                 }
                 if (!ok) break;
                 // one commit: the accumulator is full and Y buffer yb (= acc) is free again
                 mma_commit(BAR(kBarDFull + acc));
+                // leaving the tile: the producer may overwrite the stages once these complete
+                if (tb + 1 == A.n_tb && it + 1 < it1) mma_commit(BAR(kBarTile));
             }
             // every MMA this thread issued has completed before TMEM is released
             mma_commit(BAR(kBarDone));
