@@ -67,21 +67,45 @@ struct BitrevCopy<R, R> {
 };
 
 // One radix-2 butterfly (x, y) <- (x + w y, x - w y), w = root16^E (inverse) or its conjugate.
+// In single precision each (re, im) operation is one packed FP32 instruction (sm_100 and
+// later): the FP32 pipe does the same work, but in half the issue slots, which is what binds
+// the register transforms.  With ys = (y.im, y.re):
+//   E = 0:  x + y, x - y;
+//   E = 4:  x + s ys, x - s ys with s = (-1, 1) (inverse) or (1, -1);
+//   else:   x + (wr, wr) y + (-wi, wi) ys, x - (wr, wr) y - (-wi, wi) ys.
 template <typename T, bool INV, int E, typename T2>
 __device__ __forceinline__ void bfly(T2 &x, T2 &y) {
-    T2 yw;
-    if constexpr (E == 0) {
-        yw = y;
-    } else if constexpr (E == 4) {                       // times +i (inverse) or -i
-        yw = INV ? T2{-y.y, y.x} : T2{y.y, -y.x};
+    if constexpr (sizeof(T) == 4) {
+        const float2 xo = x;
+        if constexpr (E == 0) {
+            x = __fadd2_rn(xo, y);
+            y = __ffma2_rn(y, make_float2(-1.f, -1.f), xo);
+        } else if constexpr (E == 4) {
+            const float2 ys = make_float2(y.y, y.x);
+            x = __ffma2_rn(ys, INV ? make_float2(-1.f, 1.f) : make_float2(1.f, -1.f), xo);
+            y = __ffma2_rn(ys, INV ? make_float2(1.f, -1.f) : make_float2(-1.f, 1.f), xo);
+        } else {
+            constexpr float wr = (float)cos16(E);
+            constexpr float wi = INV ? (float)sin16(E) : -(float)sin16(E);
+            const float2 ys = make_float2(y.y, y.x);
+            x = __ffma2_rn(make_float2(wr, wr), y, __ffma2_rn(make_float2(-wi, wi), ys, xo));
+            y = __ffma2_rn(make_float2(-wr, -wr), y, __ffma2_rn(make_float2(wi, -wi), ys, xo));
+        }
     } else {
-        constexpr T wr = (T)cos16(E);
-        constexpr T wi = INV ? (T)sin16(E) : -(T)sin16(E);
-        yw = T2{y.x * wr - y.y * wi, y.x * wi + y.y * wr};
+        T2 yw;
+        if constexpr (E == 0) {
+            yw = y;
+        } else if constexpr (E == 4) {                       // times +i (inverse) or -i
+            yw = INV ? T2{-y.y, y.x} : T2{y.y, -y.x};
+        } else {
+            constexpr T wr = (T)cos16(E);
+            constexpr T wi = INV ? (T)sin16(E) : -(T)sin16(E);
+            yw = T2{y.x * wr - y.y * wi, y.x * wi + y.y * wr};
+        }
+        const T2 xo = x;
+        x = T2{xo.x + yw.x, xo.y + yw.y};
+        y = T2{xo.x - yw.x, xo.y - yw.y};
     }
-    const T2 xo = x;
-    x = T2{xo.x + yw.x, xo.y + yw.y};
-    y = T2{xo.x - yw.x, xo.y - yw.y};
 }
 
 // Butterflies I .. R/2-1 of the stage with span M: butterfly I pairs g + t and g + t + M/2,
