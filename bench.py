@@ -243,9 +243,15 @@ def measured_peaks():
 
 
 def kernel_source_hash(name):
-    path = os.path.join(ROOT, "paper_2601_18835_gb300", "csrc", name)
-    with open(path, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """sha256[:16] of a kernel's .cu file followed by every shared header of the sources (the
+    register DFTs, the PTX helpers, the epilogue): a figure taken on other sources is not
+    reported."""
+    csrc = os.path.join(ROOT, "paper_2601_18835_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in [name] + sorted(x for x in os.listdir(csrc) if x.endswith(".cuh")):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel, source, workload):
