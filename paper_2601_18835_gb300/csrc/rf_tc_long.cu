@@ -41,6 +41,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -58,6 +60,7 @@ constexpr uint32_t kChunkImg = 3u * kNT * 128u;      // one 64-tap chunk, hi or 
 constexpr uint32_t kChunkBytes = 2u * kChunkImg;     // hi + lo: 48 KB
 constexpr uint32_t kSpin = 1u << 22;
 constexpr uint32_t kSpinStall = 1u << 12;            // RFD_DEBUG_STALL_TAPS: give up quickly
+constexpr int kXPitch = 20;     // floats per lane of an exchange buffer: 16 used, 16-byte rows, no bank conflicts
 
 enum {
     kBarAFull = 0,      // kAStages
@@ -150,8 +153,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
     uint8_t *s_a = sm;                                              // kAStages x 48 KB
     uint8_t *s_y = sm + kAStages * kChunkBytes;                     // 2 buffers x 4 planes
     uint16_t *s_qw = (uint16_t *)(s_y + 2u * 4u * A.ystride);       // 2 buffers x 4 planes
-    float *s_x = (float *)(s_qw + 2u * 4u * A.qwin);                // 4 pairs x 2 x 32 x 17
-    uint64_t *bars = (uint64_t *)(s_x + 4 * 2 * 32 * 17);
+    float *s_x = (float *)(s_qw + 2u * 4u * A.qwin);                // 4 pairs x 2 x 32 x kXPitch
+    uint64_t *bars = (uint64_t *)(s_x + 4 * 2 * 32 * kXPitch);
     uint32_t *s_misc = (uint32_t *)(bars + kNumBars);
     volatile uint32_t *abort_flag = &s_misc[1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -423,20 +426,102 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
         const bool is_re = lq < 2u;
         const int pair = (int)(lq & 1u) + 2 * half;
         // Xs: what this warp hands over (Re of columns 16..31, or Im of columns 0..15); Xr: what it gets
-        float *Xs = s_x + (pair * 2 + (is_re ? 0 : 1)) * 32 * 17;
-        const float *Xr = s_x + (pair * 2 + (is_re ? 1 : 0)) * 32 * 17;
-        const int col_off = is_re ? 0 : 16;                  // this warp's 16 columns of each chunk
+        float *Xs = s_x + (pair * 2 + (is_re ? 0 : 1)) * 32 * kXPitch + lane * kXPitch;
+        const float *Xr = s_x + (pair * 2 + (is_re ? 1 : 0)) * 32 * kXPitch + lane * kXPitch;
         const uint32_t tlane = (lq * 32u) << 16;
         uint32_t li = 0;
         bool valid = false;
         float sc = 0.f, thr_raw = 0.f;
         int32_t j = 0, o = 0;
+        int64_t ti = it0 / A.n_tb, tb = it0 - ti * A.n_tb, prev = -1;
+        // One 32-column chunk of a warp's lane quarter (v: columns c0 .. c0 + 31 of its rows).  The
+        // real-row warp (RE) keeps columns 0..15 and hands 16..31 over, the imaginary-row warp the
+        // reverse; both then screen their 16 samples.  A warp-uniform branch picks the variant, so
+        // every register index is static (a runtime index would put v in local memory).
+        auto chunk = [&](auto re_tag, const uint32_t (&v)[32], uint32_t c0) {
+            constexpr bool RE = decltype(re_tag)::value;
+            float re[16], im[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int b0 = RE ? 16 + 4 * q : 4 * q;
+                reinterpret_cast<float4 *>(Xs)[q] = make_float4(__uint_as_float(v[b0]), __uint_as_float(v[b0 + 1]),
+                                                               __uint_as_float(v[b0 + 2]), __uint_as_float(v[b0 + 3]));
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if (RE)
+                    re[i] = __uint_as_float(v[i]);
+                else
+                    im[i] = __uint_as_float(v[16 + i]);
+            }
+            named_sync(1u + (uint32_t)pair, 64u);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 f = reinterpret_cast<const float4 *>(Xr)[q];
+                float *dst = RE ? im : re;
+                dst[4 * q] = f.x;
+                dst[4 * q + 1] = f.y;
+                dst[4 * q + 2] = f.z;
+                dst[4 * q + 3] = f.w;
+            }
+            named_sync(5u + (uint32_t)pair, 64u);     // both buffers read: free for the next chunk
+            if (!valid) return;
+            // screen: the largest unscaled |D|^2 of the 16 samples, two samples per packed FP32
+            // instruction (the same fma(re, re, im * im) per sample as the exact test below)
+            float pmax = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+                const float2 r2 = make_float2(re[i], re[i + 1]), i2 = make_float2(im[i], im[i + 1]);
+                const float2 p2 = __ffma2_rn(r2, r2, __fmul2_rn(i2, i2));
+                pmax = fmaxf(pmax, fmaxf(p2.x, p2.y));
+            }
+            if (!(pmax > thr_raw)) return;
+            // rare: the samples above the screen, then the running maximum of each window along
+            // u, one candidate per (window, run of samples); ties keep the earlier t
+            uint32_t hit = 0u;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float p_raw = fmaf(re[i], re[i], im[i] * im[i]);
+                hit |= (p_raw > thr_raw ? 1u : 0u) << i;
+            }
+            uint32_t bw = 0xffffffffu, bp = 0u, bt = 0u;
+            float bzr = 0.f, bzi = 0.f;
+            const int64_t u0 = wrap_pos(ubase, tb * kN, A.n) + c0 + (RE ? 0 : 16);
+#pragma unroll 1
+            for (int i = 0; i < 16; ++i) {
+                if (!((hit >> i) & 1u)) continue;
+                float zr = 0.f, zim = 0.f;
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (q == i) {
+                        zr = __fmul_rn(re[q], sc);
+                        zim = __fmul_rn(im[q], sc);
+                    }
+                // z and |z|^2 exactly as the other kernel forms them
+                const float p = __fadd_rn(__fmul_rn(zr, zr), __fmul_rn(zim, zim));
+                if (!(p > A.thr)) continue;
+                const uint32_t t = (uint32_t)((u0 + i + o) & (A.n - 1));
+                const uint32_t w = t / A.W;
+                if (w != bw) {
+                    if (bw != 0xffffffffu) emit_one((uint32_t)j, bw, bp, bt, bzr, bzi, A.cand, A.cap, A.count);
+                    bw = w;
+                    bp = 0u;
+                }
+                const uint32_t pb = __float_as_uint(p);
+                if (pb > bp || (pb == bp && t < bt)) {
+                    bp = pb;
+                    bt = t;
+                    bzr = zr;
+                    bzi = zim;
+                }
+            }
+            if (bw != 0xffffffffu) emit_one((uint32_t)j, bw, bp, bt, bzr, bzi, A.cand, A.cap, A.count);
+        };
         // both accumulators start free: this warp's share of the first phase of each go barrier
         if (lane == 0) {
             mbar_arrive(BAR(kBarGo + 0));
             mbar_arrive(BAR(kBarGo + 1));
         }
-        int64_t ti = it0 / A.n_tb, tb = it0 - ti * A.n_tb, prev = -1;
         for (int64_t it = it0; it < it1; ++it, ++li, tb = (tb + 1 == A.n_tb) ? 0 : tb + 1, ti += (tb == 0)) {
             if (ti != prev) {
                 // this lane's template: a = 32 (quarter & 1) + lane, the same in both warps of the pair
@@ -467,71 +552,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
                     __syncwarp();
                     if (lane == 0) mbar_arrive(BAR(kBarGo + acc));
                 }
-                // static register indices only (a runtime index would put v in local memory)
-                float re[16], im[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float lo = __uint_as_float(v[i]), hi = __uint_as_float(v[16 + i]);
-                    Xs[lane * 17 + i] = is_re ? hi : lo;
-                    re[i] = lo;       // the real warp keeps its columns 0..15,
-                    im[i] = hi;       // the imaginary warp its columns 16..31
-                }
-                named_sync(1u + (uint32_t)pair, 64u);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float other = Xr[lane * 17 + i];
-                    if (is_re) {
-                        im[i] = other;
-                    } else {
-                        re[i] = other;
-                    }
-                }
-                if (valid) {
-                    // screen the 16 samples first (no branch), one mask
-                    uint32_t hit = 0u;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float p_raw = fmaf(re[i], re[i], im[i] * im[i]);
-                        hit |= (p_raw > thr_raw ? 1u : 0u) << i;
-                    }
-                    if (hit) {
-                        // rare: the running maximum of each window along u, one candidate per
-                        // (window, run of samples); ties keep the earlier t
-                        uint32_t bw = 0xffffffffu, bp = 0u, bt = 0u;
-                        float bzr = 0.f, bzi = 0.f;
-                        const int64_t u0 = wrap_pos(ubase, tb * kN, A.n) + c0 + col_off;
-#pragma unroll 1
-                        for (int i = 0; i < 16; ++i) {
-                            if (!((hit >> i) & 1u)) continue;
-                            float zr = 0.f, zim = 0.f;
-#pragma unroll
-                            for (int q = 0; q < 16; ++q)
-                                if (q == i) {
-                                    zr = __fmul_rn(re[q], sc);
-                                    zim = __fmul_rn(im[q], sc);
-                                }
-                            // z and |z|^2 exactly as the other kernel forms them
-                            const float p = __fadd_rn(__fmul_rn(zr, zr), __fmul_rn(zim, zim));
-                            if (!(p > A.thr)) continue;
-                            const uint32_t t = (uint32_t)((u0 + i + o) & (A.n - 1));
-                            const uint32_t w = t / A.W;
-                            if (w != bw) {
-                                if (bw != 0xffffffffu) emit_one((uint32_t)j, bw, bp, bt, bzr, bzi, A.cand, A.cap, A.count);
-                                bw = w;
-                                bp = 0u;
-                            }
-                            const uint32_t pb = __float_as_uint(p);
-                            if (pb > bp || (pb == bp && t < bt)) {
-                                bp = pb;
-                                bt = t;
-                                bzr = zr;
-                                bzi = zim;
-                            }
-                        }
-                        if (bw != 0xffffffffu) emit_one((uint32_t)j, bw, bp, bt, bzr, bzi, A.cand, A.cap, A.count);
-                    }
-                }
-                named_sync(5u + (uint32_t)pair, 64u);     // the buffers are free for the next chunk
+                if (is_re)
+                    chunk(std::true_type{}, v, c0);
+                else
+                    chunk(std::false_type{}, v, c0);
             }
         }
     }
@@ -633,7 +657,7 @@ uint32_t tl_ystride(int32_t kpad_max) { return (uint32_t)(kN - 8 + kpad_max) * 1
 uint32_t tl_qwin(int32_t kpad_max) { return (uint32_t)(kN + kpad_max); }
 
 size_t tl_smem_bytes(uint32_t ystride, uint32_t qwin) {
-    return 1024 + (size_t)kAStages * kChunkBytes + 2u * 4u * ystride + 2u * 4u * qwin * 2u + 4 * 2 * 32 * 17 * 4 +
+    return 1024 + (size_t)kAStages * kChunkBytes + 2u * 4u * ystride + 2u * 4u * qwin * 2u + 4 * 2 * 32 * kXPitch * 4 +
            kNumBars * 8 + 16;
 }
 
