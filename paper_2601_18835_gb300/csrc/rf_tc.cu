@@ -298,6 +298,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
                 const bool my_valid = my_a < T.count && my_a < hi;
                 const int64_t my_slot = (int64_t)T.first + (my_valid ? my_a : 0);
                 const float my_sc = my_valid ? A.scale[my_slot] * esc : 0.f;
+                // screen factor: |z|^2 = |D|^2 sc^2 against thr lowered by 2^-10 (far above the
+                // few-ulp difference to the exact |z|^2 below); 0 for an invalid template
+                const float my_inv = my_valid ? (my_sc * my_sc) / (A.thr * (1.0f - 0.0009765625f)) : 0.f;
                 uint32_t re[32], im[32];
                 tmem_ld32(tmem + tlane + (uint32_t)a0, re);
                 tmem_ld32(tmem + tlane + (uint32_t)(T.nt + a0), im);
@@ -307,7 +310,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc(const TcArgs A) {
                     __syncwarp();
                     if (lane == 0) mbar_arrive(BAR(kBarDEmpty));
                 }
-                // z and |z|^2 exactly as the emitter forms them; one vote for the whole chunk
+                // screen the 32 templates of this sample, two per packed FP32 instruction: the
+                // largest |D|^2 sc^2 / thr' (a NaN from an invalid template or thr = 0 with
+                // |D| = 0 is ignored by the max; such a sample cannot trigger)
+                float smax = 0.f;
+#pragma unroll
+                for (int i = 0; i < 32; i += 2) {
+                    const float2 r2 = make_float2(__uint_as_float(re[i]), __uint_as_float(re[i + 1]));
+                    const float2 i2 = make_float2(__uint_as_float(im[i]), __uint_as_float(im[i + 1]));
+                    const float2 f2 = make_float2(__shfl_sync(0xffffffffu, my_inv, i), __shfl_sync(0xffffffffu, my_inv, i + 1));
+                    const float2 s2 = __fmul2_rn(__ffma2_rn(r2, r2, __fmul2_rn(i2, i2)), f2);
+                    smax = fmaxf(smax, fmaxf(s2.x, s2.y));
+                }
+                if (!__any_sync(0xffffffffu, smax > 1.0f)) continue;
+                // rare: z and |z|^2 exactly as the emitter forms them; one vote for the whole chunk
                 uint32_t hit = 0u;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {

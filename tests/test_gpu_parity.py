@@ -702,6 +702,52 @@ def test_full_series_ragged(ctx, label, prec, opts):
     assert worst <= EPS_SERIES[prec]
 
 
+@pytest.mark.parametrize("name,prec", TC_PRECISIONS)
+def test_full_series_tile_transitions_long_kernel(ctx, name, prec):
+    """Templates-on-M kernel with tiles of one and two 64-tap chunks (taps resident for the
+    tile) and of three and five chunks (streamed through the stages), interleaved along every
+    CTA's range: 4 references x 4 K classes (no K mixing inside a tile), 16 tiles of 256 items.
+    Five CTAs make each range cross resident -> resident, resident -> streamed, streamed ->
+    streamed and streamed -> resident tile changes; one CTA crosses all of them in turn.  An
+    item's arithmetic does not depend on which CTA runs it, so the whole series must be
+    bit-identical across the partitions; against the oracle, every sample lies within the
+    path's bound of the series' peak (the bank carries loud injections, so the rms is far
+    below the peak) and within the method's 1e-3 of its rms."""
+    cfg = workload.small_config(3, n=65536, n_tmpl=32, n_ref=4)
+    bank, data = workload.make_workload(cfg)
+    classes = np.array([48, 128, 192, 320], dtype=np.int32)
+    K = np.zeros(bank.n_tmpl, dtype=np.int32)
+    for r in range(bank.n_ref):                          # the K classes in turn within each reference
+        members = np.flatnonzero(bank.ref_of_tmpl == r)
+        K[members] = classes[np.arange(len(members)) % 4]
+    for r in range(bank.n_ref):                          # every reference holds every K class
+        assert set(K[bank.ref_of_tmpl == r].tolist()) == {48, 128, 192, 320}
+    ora, gpu = OracleRun(cfg, bank, data), GpuRun(cfg, bank, data, ctx=ctx)
+    t = gpu.make_taps(K, k_stride=320, match=False)
+    opts = {"long_k": 0, "mix_k": 0, "grid_ctas": 5}
+    plan = rfd.Plan(gpu.ctx, gpu.grid, bank.n_ref, bank.ref_of_tmpl, K, prec, cfg.window, cfg.threshold, 319,
+                    options=opts)
+    kinds = plan.template_kernels()
+    plan.close()
+    assert np.all(kinds == 2)                            # every template on the templates-on-M kernel
+    q, e, _ = gpu.filter_reference(319, prec)
+    z5, count = gpu.series(t, q, e, prec, 319, options=opts)
+    assert count == bank.n_tmpl * gpu.n                  # every sample of every template, once
+    z1, _ = gpu.series(t, q, e, prec, 319, options=dict(opts, grid_ctas=1))
+    zd, _ = gpu.series(t, q, e, prec, 319, options={"long_k": 0, "mix_k": 0})
+    assert np.array_equal(z5, z1) and np.array_equal(z5, zd)
+    worst_rms = worst_peak = 0.0
+    for j in range(bank.n_tmpl):
+        zo = ora.snr(j, ora.design(j, int(K[j]), with_match=False))
+        d = float(np.max(np.abs(z5[j] - zo)))
+        worst_rms = max(worst_rms, d / float(np.sqrt(np.mean(np.abs(zo) ** 2))))
+        worst_peak = max(worst_peak, d / float(np.max(np.abs(zo))))
+    print("full series tile transitions %s: max |dz| / rms |z| = %.3g, / peak |z| = %.3g" % (name, worst_rms,
+                                                                                             worst_peak))
+    assert worst_rms <= TOL_TC
+    assert worst_peak <= EPS[prec]
+
+
 # --------------------------------------------------------------------------- graph and autotuner
 @pytest.mark.parametrize("opts", [None, {"fft_k": 32}])
 def test_search_graph_matches_separate_calls(c1, opts):
