@@ -66,15 +66,13 @@ enum {
     kBarAFull = 0,      // kAStages
     kBarAEmpty = 2,     // kAStages
     kBarGo = 4,         // 2: accumulator free + Y built + chunk 0 staged, per item buffer
-    kBarYEmpty = 6,     // 2
-    kBarDFull = 8,      // 2
-    kBarUnused = 10,    // 2
-    kBarQFull = 12,     // 2
-    kBarQEmpty = 14,    // 2
-    kBarDone = 16,
-    kBarT0 = 17,        // 2: the first taps chunk of an item, per item buffer (producer only)
-    kBarTile = 19,      // every MMA before a tile change has completed (one phase per change)
-    kNumBars = 20
+    kBarDFull = 6,      // 2
+    kBarQFull = 8,      // 2
+    kBarQEmpty = 10,    // 2
+    kBarDone = 12,
+    kBarT0 = 13,        // 2: the first taps chunk of an item, per item buffer (producer only)
+    kBarTile = 15,      // every MMA before a tile change has completed (one phase per change)
+    kNumBars = 16
 };
 
 struct TlArgs {
@@ -172,9 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rf_tc_long(const TlArgs A) {
             // one phase per use of item buffer b: 8 epilogue warps (the accumulator is free),
             // 4 builder warps (Y is built), the producer (chunk 0 of the taps, with its bytes)
             mbar_init(BAR(kBarGo + b), 8 + 4 + 1);
-            mbar_init(BAR(kBarYEmpty + b), 1);
             mbar_init(BAR(kBarDFull + b), 1);
-            mbar_init(BAR(kBarUnused + b), 1);
             mbar_init(BAR(kBarQFull + b), 1);
             mbar_init(BAR(kBarQEmpty + b), 4);
             mbar_init(BAR(kBarT0 + b), 1);
