@@ -112,8 +112,16 @@ static rfd_status plan_tl_tiles(rfd_plan *p, const std::vector<int32_t> &order, 
                 p->halo, kpad_max - 1);
     p->tl_ystride = tl_ystride(kpad_max);
     p->tl_qwin = tl_qwin(kpad_max);
+    // cost of one item in SM cycles, measured on the kernel (uniform K, every SM busy): the MMAs
+    // take 768 cycles per 16-tap step plus ~370 of hand-offs, and no item takes less than about
+    // 3850 (the epilogue drains 128 x 256 accumulators per item whatever K is): 3864 cycles at
+    // K = 16, 4012 at 64, 4989 at 96, 6508 at 128.  Items of short-K tiles priced by their MMAs
+    // alone made the CTAs that hold them finish last.
     std::vector<double> cost(ntiles);
-    for (int64_t t = 0; t < ntiles; ++t) cost[t] = (double)p->tl_tiles[t].nk16 * 6.0 + 2.0;
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const double nk = (double)p->tl_tiles[t].nk16;
+        cost[t] = std::max(768.0 * nk + 370.0, 3850.0 + 40.0 * nk);
+    }
     const int64_t G = std::max<int64_t>(1, std::min<int64_t>(opt.grid_ctas > 0 ? opt.grid_ctas : num_sms,
                                                            ntiles * n_tb));
     const std::vector<int64_t> ranges = balanced_ranges(cost, n_tb, G);
