@@ -167,8 +167,11 @@ static rfd_status plan_fft_tiles(rfd_plan *p, const std::vector<int32_t> &order,
     p->fft_flops = (double)p->fft_nslots * p->fft_nb * M * (6.0 + 5.0 * log2m) +
                    (double)p->fft_refs.size() * p->fft_nb * M * 5.0 * log2m;
     const int64_t ntiles = (int64_t)p->fft_tiles.size();
+    // cost of one item in template-block groups: a per-CTA span fit on C3 and C5 gave 1.77 us
+    // per template-block group and 1.9-2.7 us per item (the block spectra loads, the ring's
+    // first copy), so an item costs about one group besides its templates
     std::vector<double> cost(ntiles);
-    for (int64_t t = 0; t < ntiles; ++t) cost[t] = (double)p->fft_tiles[t].count + 0.5;
+    for (int64_t t = 0; t < ntiles; ++t) cost[t] = (double)p->fft_tiles[t].count + 1.0;
     const int64_t G = std::max<int64_t>(1, std::min<int64_t>(opt.grid_ctas > 0 ? opt.grid_ctas : num_sms,
                                                            ntiles * p->fft_nbg));
     const std::vector<int64_t> ranges = balanced_ranges(cost, p->fft_nbg, G);
