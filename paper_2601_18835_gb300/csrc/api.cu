@@ -9,6 +9,19 @@
 
 #include "internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// A profiler-visible range (NVTX) over one C-ABI call, so that Nsight tools show the library's
+// calls by name; with no tool attached a push or pop costs a pointer test.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
+
 namespace rfd {
 
 // implemented in the kernel files
@@ -461,6 +474,7 @@ rfd_status rfd_make_taps(rfd_ctx *ctx, const rfd_grid *grid, const double *psd_d
                          const int32_t *buckets_host, int32_t n_buckets, double energy_frac, int32_t k_stride,
                          double tukey_alpha, void *taps_dev, int32_t *k_dev, int32_t *lag_dev, double *sigma_dev,
                          double *match_dev, void *stream) {
+    NvtxRange nvtx_range("rfd_make_taps");
     RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
     Grid g;
     RFD_TRY(check_grid(grid, &g));
@@ -505,6 +519,7 @@ rfd_status rfd_make_taps_fit(rfd_ctx *ctx, const rfd_grid *grid, const double *p
                              int32_t n_tmpl, const int32_t *k_host, const int32_t *buckets_host, int32_t n_buckets,
                              double match_target, double ridge, int32_t k_stride, double tukey_alpha, void *taps_dev,
                              int32_t *k_dev, int32_t *lag_dev, double *sigma_dev, double *match_dev, void *stream) {
+    NvtxRange nvtx_range("rfd_make_taps_fit");
     RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
     Grid g;
     RFD_TRY(check_grid(grid, &g));
@@ -552,6 +567,7 @@ rfd_status rfd_make_taps_at_lag(rfd_ctx *ctx, const rfd_grid *grid, const double
                                 const int32_t *ref_of_tmpl_host, int32_t n_tmpl, const int32_t *k_host,
                                 const int32_t *lag_host, int32_t k_stride, double tukey_alpha, void *taps_dev,
                                 double *sigma_dev, double *match_dev, void *stream) {
+    NvtxRange nvtx_range("rfd_make_taps_at_lag");
     RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
     Grid g;
     RFD_TRY(check_grid(grid, &g));
@@ -585,6 +601,7 @@ rfd_status rfd_make_taps_at_lag(rfd_ctx *ctx, const rfd_grid *grid, const double
 rfd_status rfd_filter_reference(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev,
                                 const double *psd_dev, const void *href_dev, int32_t n_ref, int32_t halo,
                                 int32_t precision, void *qref_dev, int32_t *qscale_dev, void *stream) {
+    NvtxRange nvtx_range("rfd_filter_reference");
     RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
     Grid g;
     RFD_TRY(check_grid(grid, &g));
@@ -624,6 +641,7 @@ rfd_status rfd_plan_create_ex(rfd_ctx *ctx, const rfd_grid *grid, int32_t n_ref,
                               const int32_t *ref_of_tmpl_host, const int32_t *k_host, int32_t precision,
                               int32_t window, float threshold, int32_t halo, const rfd_plan_options *options,
                               rfd_plan **out) {
+    NvtxRange nvtx_range("rfd_plan_create_ex");
     rfd_plan_options opt;
     rfd_plan_options_default(&opt);
     if (options) opt = *options;
@@ -824,6 +842,7 @@ void rfd_plan_destroy(rfd_plan *plan) {
 
 rfd_status rfd_plan_set_taps(rfd_plan *plan, const void *taps_dev, int32_t k_stride, const int32_t *lag_dev,
                              const double *sigma_dev, void *stream) {
+    NvtxRange nvtx_range("rfd_plan_set_taps");
     RFD_REQUIRE(plan, RFD_ERR_ARG, "plan is NULL");
     RFD_REQUIRE(taps_dev && lag_dev && sigma_dev, RFD_ERR_ARG, "NULL argument");
     RFD_REQUIRE(k_stride >= plan->k_max, RFD_ERR_SHAPE, "k_stride=%d < max K=%d", k_stride, plan->k_max);
@@ -861,6 +880,7 @@ extern "C" {
 rfd_status rfd_ratio_filter_batch(rfd_plan *plan, const void *qref_dev, const int32_t *qscale_dev,
                                   rfd_candidate *cand_dev, int64_t cand_capacity, int64_t *cand_count_dev,
                                   void *stream) {
+    NvtxRange nvtx_range("rfd_ratio_filter_batch");
     RFD_REQUIRE(plan, RFD_ERR_ARG, "plan is NULL");
     RFD_REQUIRE(plan->taps_set, RFD_ERR_ARG, "rfd_plan_set_taps has not been called");
     RFD_REQUIRE(qref_dev && cand_count_dev && (cand_dev || cand_capacity == 0), RFD_ERR_ARG, "NULL argument");
@@ -875,6 +895,7 @@ rfd_status rfd_ratio_filter_batch(rfd_plan *plan, const void *qref_dev, const in
 rfd_status rfd_ratio_filter_window(rfd_plan *plan, const void *qref_dev, const int32_t *qscale_dev,
                                    const int64_t *u_begin_dev, rfd_candidate *cand_dev, int64_t cand_capacity,
                                    int64_t *cand_count_dev, void *stream) {
+    NvtxRange nvtx_range("rfd_ratio_filter_window");
     RFD_REQUIRE(plan, RFD_ERR_ARG, "plan is NULL");
     RFD_REQUIRE(plan->taps_set, RFD_ERR_ARG, "rfd_plan_set_taps has not been called");
     RFD_REQUIRE(qref_dev && u_begin_dev && cand_count_dev && (cand_dev || cand_capacity == 0), RFD_ERR_ARG,
@@ -907,6 +928,7 @@ rfd_status rfd_plan_template_kernels(const rfd_plan *plan, int32_t *kernel_host)
 rfd_status rfd_find_triggers(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *cand_dev,
                              const int64_t *cand_count_dev, int64_t cand_capacity, rfd_trigger *trig_dev,
                              int64_t trig_capacity, int64_t *n_trig_host, void *stream) {
+    NvtxRange nvtx_range("rfd_find_triggers");
     RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
     RFD_REQUIRE(n_tmpl >= 1, RFD_ERR_SHAPE, "n_tmpl must be >= 1");
     RFD_REQUIRE(cand_count_dev && n_trig_host && (cand_dev || cand_capacity == 0) &&
@@ -921,6 +943,7 @@ rfd_status rfd_find_triggers(rfd_ctx *ctx, int32_t n_tmpl, const rfd_candidate *
 rfd_status rfd_findchirp(rfd_ctx *ctx, const rfd_grid *grid, const void *dtilde_dev, const double *psd_dev,
                          const void *h_dev, int32_t n_tmpl, int32_t window, float threshold,
                          rfd_candidate *cand_dev, int64_t cand_capacity, int64_t *cand_count_dev, void *stream) {
+    NvtxRange nvtx_range("rfd_findchirp");
     RFD_REQUIRE(ctx, RFD_ERR_ARG, "ctx is NULL");
     Grid g;
     RFD_TRY(check_grid(grid, &g));

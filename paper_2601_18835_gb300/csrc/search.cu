@@ -5,6 +5,19 @@
 // run replays the graph, waits for it and checks the counts.
 #include "internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// A profiler-visible range (NVTX) over one C-ABI call, so that Nsight tools show the library's
+// calls by name; with no tool attached a push or pop costs a pointer test.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
+
 namespace rfd {
 rfd_status filter_reference_impl(rfd_ctx *, const Grid &, const float2 *, const double *, const float2 *,
                                  int64_t, int32_t, int32_t, void *, int32_t *, cudaStream_t);
@@ -86,6 +99,7 @@ rfd_status rfd_search_create(rfd_plan *plan, const void *dtilde_dev, const doubl
                              void *qref_dev, int32_t *qscale_dev, rfd_candidate *cand_dev, int64_t cand_capacity,
                              int64_t *cand_count_dev, rfd_trigger *trig_dev, int64_t trig_capacity, void *stream,
                              rfd_search **out) {
+    NvtxRange nvtx_range("rfd_search_create");
     RFD_REQUIRE(plan && out, RFD_ERR_ARG, "NULL plan or out");
     *out = nullptr;
     RFD_REQUIRE(plan->taps_set, RFD_ERR_ARG, "rfd_plan_set_taps has not been called");
@@ -168,6 +182,7 @@ rfd_status rfd_search_create(rfd_plan *plan, const void *dtilde_dev, const doubl
 }
 
 rfd_status rfd_search_run_at(rfd_search *S, int64_t u_begin, void *stream, int64_t *n_trig_host) {
+    NvtxRange nvtx_range("rfd_search_run_at");
     RFD_REQUIRE(S && n_trig_host, RFD_ERR_ARG, "NULL argument");
     RFD_REQUIRE(u_begin >= 0 && u_begin < S->plan->grid.n && u_begin % 512 == 0, RFD_ERR_ARG,
                 "u_begin=%lld must be a multiple of 512 in [0, n)", (long long)u_begin);
@@ -179,6 +194,7 @@ rfd_status rfd_search_run_at(rfd_search *S, int64_t u_begin, void *stream, int64
 }
 
 rfd_status rfd_search_run(rfd_search *S, void *stream, int64_t *n_trig_host) {
+    NvtxRange nvtx_range("rfd_search_run");
     RFD_REQUIRE(S && n_trig_host, RFD_ERR_ARG, "NULL argument");
     RFD_TRY_CUDA(cudaSetDevice(S->plan->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -190,6 +206,7 @@ rfd_status rfd_search_run(rfd_search *S, void *stream, int64_t *n_trig_host) {
 
 rfd_status rfd_search_run_host(rfd_search *S, const void *dtilde_host, rfd_trigger *trig_host,
                                int64_t trig_host_capacity, void *stream, int64_t *n_trig_host) {
+    NvtxRange nvtx_range("rfd_search_run_host");
     RFD_REQUIRE(S && dtilde_host && n_trig_host && (trig_host || trig_host_capacity == 0), RFD_ERR_ARG,
                 "NULL argument");
     RFD_REQUIRE(trig_host_capacity >= 0, RFD_ERR_SHAPE, "negative trigger capacity");
