@@ -386,8 +386,8 @@ void rfd_search_destroy(rfd_search *search);
  * the calling thread's current device.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress).  Under CUDA's lazy module loading that lookup is
  * also what loads librfd's device code on that device and backs the array, which can
- * synchronise the device: make the first call on each device during set-up, before any
- * stream capture; later calls only reuse the cached address.
+ * synchronise the device: make the first call on each device during set-up; later calls only
+ * reuse the cached address.
  * n_tmpl > RFD_NOALLOC_MAX_TEMPLATES or cand_capacity > RFD_NOALLOC_MAX_CANDIDATES is
  * rejected with RFD_ERR_SHAPE before anything runs.  Every call on a device shares the one
  * array: each call clears the counters it needs, but calls that overlap on the GPU (other
