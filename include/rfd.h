@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define RFD_VERSION 4
+#define RFD_VERSION 5
 
 typedef enum {
     RFD_OK = 0,
@@ -187,6 +187,50 @@ rfd_status rfd_make_taps_at_lag(rfd_ctx *ctx, const rfd_grid *grid, const double
                                 int32_t n_tmpl, const int32_t *k_host, const int32_t *lag_host,
                                 int32_t k_stride, double tukey_alpha, void *taps_dev,
                                 double *sigma_dev, double *match_dev, void *stream);
+
+/* ------------------------------------------------------------------ tap banks on disk
+ * Tap extraction (Sec. V) is the set-up's dominant cost, and its outputs depend only on its
+ * inputs, so a bank's taps can be stored once and read back by later runs.
+ *
+ * rfd_taps_key writes to key_out (32 bytes) the SHA-256 digest (FIPS 180-4) of this
+ * serialisation of rfd_make_taps' inputs, native little-endian (other hosts get
+ * RFD_ERR_UNSUPPORTED), no padding between fields:
+ *   the 12 bytes "librfd-taps" and its NUL; int32 RFD_VERSION; int32 mode (0: k_host given,
+ *   1: bucket list); grid fs (double), n (int64), f_low (double), pn_flags (int32); int32
+ *   n_ref, n_tmpl, k_stride; double tukey_alpha; double energy_frac (0 in mode 0); int32
+ *   n_buckets (0 in mode 0); refs_host [n_ref] and tmpl_host [n_tmpl] as rfd_params (five
+ *   doubles each); ref_of_tmpl_host int32 [n_tmpl]; k_host int32 [n_tmpl] (mode 0) or
+ *   buckets_host int32 [n_buckets] (mode 1); psd_host double [n/2+1].
+ * Host only; arguments as for rfd_make_taps except that the PSD is a host array. */
+rfd_status rfd_taps_key(const rfd_grid *grid, const double *psd_host, const rfd_params *refs_host,
+                        int32_t n_ref, const rfd_params *tmpl_host, const int32_t *ref_of_tmpl_host,
+                        int32_t n_tmpl, const int32_t *k_host, const int32_t *buckets_host,
+                        int32_t n_buckets, double energy_frac, int32_t k_stride, double tukey_alpha,
+                        uint8_t *key_out);
+/* rfd_make_taps through a cache directory.  The bank's key (rfd_taps_key, with the PSD read
+ * back from psd_dev) names the file <cache_dir>/<key as 64 hex digits>.rfdtaps.  When that
+ * file holds this key, n_tmpl and k_stride (and a match section, when match_dev is given), its
+ * taps, K, lags, sigma_eff and match are copied to the outputs and *hit_host = 1.  Otherwise
+ * rfd_make_taps runs with the same arguments, its outputs are written to that file (under a
+ * temporary name, then renamed, so a reader never sees a partial file; cache_dir is created
+ * if missing, one level) and *hit_host = 0.  A file that is truncated, holds another key or
+ * fails the checks on its contents (1 <= K <= k_stride, lag in [-n/2, n/2), finite
+ * sigma_eff >= 0) is recomputed and replaced.  The file: the 8-byte magic "RFDTAPS" 0x01, a
+ * little-endian uint64 header length, a JSON header (key, n_tmpl, k_stride, has_match, and
+ * per section its name, dtype, shape, offset and bytes), then the sections, 64-byte aligned
+ * from the end of the header: taps complex64 [n_tmpl][k_stride], K int32 [n_tmpl], lag int32
+ * [n_tmpl], sigma_eff float64 [n_tmpl] and, when present, match float64 [n_tmpl].
+ * Outputs as for rfd_make_taps (k_dev and match_dev may be NULL).  When the taps were
+ * extracted but the file cannot be written, the outputs are valid and RFD_ERR_ARG reports the
+ * write.  Synchronises the stream. */
+rfd_status rfd_make_taps_cached(const char *cache_dir, rfd_ctx *ctx, const rfd_grid *grid,
+                                const double *psd_dev, const rfd_params *refs_host, int32_t n_ref,
+                                const rfd_params *tmpl_host, const int32_t *ref_of_tmpl_host,
+                                int32_t n_tmpl, const int32_t *k_host, const int32_t *buckets_host,
+                                int32_t n_buckets, double energy_frac, int32_t k_stride,
+                                double tukey_alpha, void *taps_dev, int32_t *k_dev, int32_t *lag_dev,
+                                double *sigma_dev, double *match_dev, int32_t *hit_host,
+                                void *stream);
 
 /* ------------------------------------------------------------------ filter_reference
  * The reference SNR series of Eq. 3, (s|h)_ref, one per reference (Eq. 1 discretised):

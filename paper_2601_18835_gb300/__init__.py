@@ -13,6 +13,7 @@ step of the method runs in the library's CUDA kernels.  Names follow include/rfd
   Mlp                learned taps: per-reference networks, training, inference Eq. 4 through Eqs. 5-6
 """
 import ctypes
+import os
 
 import numpy as np
 import torch
@@ -23,7 +24,7 @@ from ._native import (CANDIDATE_DTYPE, PN_SO, PN_TIDAL, PREC_BF16X3, PREC_FP16X3
 
 __all__ = ["Context", "Plan", "Search", "Mlp", "Subband", "grid", "gen_templates", "make_taps", "make_taps_fit",
            "make_taps_at_lag",
-           "filter_reference",
+           "make_taps_cached", "taps_key", "filter_reference",
            "find_triggers", "find_triggers_noalloc", "findchirp", "ifft_c2c", "qref_ld", "candidates_to_numpy",
            "triggers_to_numpy", "CANDIDATE_DTYPE", "TRIGGER_DTYPE"]
 
@@ -125,6 +126,44 @@ def make_taps(ctx, g, psd, refs, tmpl, ref_of, k, k_stride, alpha, taps, lag, si
     check(_lib().rfd_make_taps(ctx.handle, ctypes.byref(g), _ptr(psd), ra, nr, ta, rop, nt, kp, bkp, nbk,
                                float(energy_frac), int(k_stride), float(alpha), _ptr(taps), _ptr(k_out),
                                _ptr(lag), _ptr(sigma), _ptr(match), _stream(stream)))
+
+
+def _k_policy(k, buckets):
+    """(array kept alive by the caller, k pointer, bucket pointer, bucket count)."""
+    if k is None:
+        bk, bkp = _i32_host(buckets)
+        return bk, None, bkp, len(bk)
+    kk, kp = _i32_host(k)
+    return kk, kp, None, 0
+
+
+def taps_key(g, psd, refs, tmpl, ref_of, k, k_stride, alpha, buckets=None, energy_frac=0.999):
+    """SHA-256 digest (32 bytes) of a tap bank's inputs (rfd_taps_key); psd: host float64 [n/2+1]."""
+    ra, nr = _params(refs)
+    ta, nt = _params(tmpl)
+    ro, rop = _i32_host(ref_of)
+    keep, kp, bkp, nbk = _k_policy(k, buckets)
+    ps = np.ascontiguousarray(np.asarray(psd, dtype=np.float64))
+    out = (ctypes.c_uint8 * 32)()
+    check(_lib().rfd_taps_key(ctypes.byref(g), ps.ctypes.data_as(ctypes.c_void_p), ra, nr, ta, rop, nt, kp, bkp, nbk,
+                              float(energy_frac), int(k_stride), float(alpha), out))
+    return bytes(out)
+
+
+def make_taps_cached(cache_dir, ctx, g, psd, refs, tmpl, ref_of, k, k_stride, alpha, taps, lag, sigma, match=None,
+                     stream=None, buckets=None, energy_frac=0.999, k_out=None):
+    """make_taps through the tap-bank files under cache_dir (rfd_make_taps_cached).  Returns True
+    when the taps were read from a file, False when they were extracted (and stored)."""
+    ra, nr = _params(refs)
+    ta, nt = _params(tmpl)
+    ro, rop = _i32_host(ref_of)
+    keep, kp, bkp, nbk = _k_policy(k, buckets)
+    hit = ctypes.c_int32(0)
+    check(_lib().rfd_make_taps_cached(os.fsencode(cache_dir), ctx.handle, ctypes.byref(g), _ptr(psd), ra, nr, ta,
+                                      rop, nt, kp, bkp, nbk, float(energy_frac), int(k_stride), float(alpha),
+                                      _ptr(taps), _ptr(k_out), _ptr(lag), _ptr(sigma), _ptr(match),
+                                      ctypes.byref(hit), _stream(stream)))
+    return bool(hit.value)
 
 
 def make_taps_fit(ctx, g, psd, refs, tmpl, ref_of, k, k_stride, alpha, taps, lag, sigma, match, ridge=1e-6,

@@ -100,6 +100,10 @@ SIGNATURES = {
     "rfd_fft_c2c": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp]),
     "rfd_make_taps_at_lag": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _i32,
                                     _dbl, _vp, _vp, _vp, _vp]),
+    "rfd_taps_key": (_i32, [ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _dbl, _i32, _dbl,
+                            _vp]),
+    "rfd_make_taps_cached": (_i32, [ctypes.c_char_p, _vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp,
+                                    _vp, _i32, _dbl, _i32, _dbl, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i32), _vp]),
     "rfd_make_taps_fit": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _dbl,
                                  _dbl, _i32, _dbl, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rfd_subband_create": (_i32, [_vp, ctypes.POINTER(Grid), _vp, _vp, _i32, _i32, ctypes.POINTER(_vp)]),
