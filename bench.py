@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--chisq", type=int, default=0,
                     help="also time the sub-band chi^2 (this many bands) of each step's triggers")
     ap.add_argument("--ridge", type=float, default=1e-6)
+    ap.add_argument("--taps-cache", default=None,
+                    help="directory of tap-bank files: windowed taps are read from it when present, else "
+                         "extracted and stored there (set-up only; off by default)")
     ap.add_argument("--long-k", type=int, default=None,
                     help="fix the plan's long_k instead of autotuning (profiling cases)")
     ap.add_argument("--stream-block", type=int, default=0,
@@ -666,8 +669,10 @@ class GpuSearch:
     """Set-up (templates, taps, autotuned plan) and the per-segment search as one CUDA graph."""
 
     def __init__(self, cfg, bank, data, precision, device, use_graph=True, autotune_cache=None, learned=None,
-                 options=None, reuse=None, fit=None):
+                 options=None, reuse=None, fit=None, taps_cache=None):
         self.learned = learned
+        self.taps_cache = taps_cache
+        self.taps_cache_hit = None
         self.reuse = reuse
         self.fit = fit
         self.fixed_options = options
@@ -722,6 +727,12 @@ class GpuSearch:
                 cfg, bank, self.ctx, self.grid, self.psd, self.stream, **self.learned)
             self.match = None
             kout.fill_(k_stride)
+        elif self.taps_cache:
+            self.taps_cache_hit = rfd.make_taps_cached(
+                self.taps_cache, self.ctx, self.grid, self.psd, bank.ref_params(), bank.params(), bank.ref_of_tmpl,
+                None if bucketed else np.full(J, cfg.k, dtype=np.int32), k_stride, cfg.tukey_alpha, self.taps,
+                self.lag, self.sig, self.match, stream=self.stream, buckets=list(cfg.k_buckets) if bucketed else None,
+                k_out=kout)
         else:
             rfd.make_taps(self.ctx, self.grid, self.psd, bank.ref_params(), bank.params(), bank.ref_of_tmpl,
                           None if bucketed else np.full(J, cfg.k, dtype=np.int32), k_stride, cfg.tukey_alpha,
@@ -955,7 +966,7 @@ def measure(args, c, prec, precision_name, ws, rank, local, primary):
         if args.fft_k is not None:
             fixed["fft_k"] = args.fft_k
     s = GpuSearch(cfg, bank, data, prec, local, use_graph=not args.no_graph, autotune_cache=tune_cache,
-                  learned=learned, options=fixed, fit=fit)
+                  learned=learned, options=fixed, fit=fit, taps_cache=args.taps_cache)
     J, dur = bank.n_tmpl, cfg.duration
     step_dur = s.out_len / cfg.fs          # seconds of SNR series per template and step
 
@@ -1151,7 +1162,8 @@ def measure(args, c, prec, precision_name, ws, rank, local, primary):
         "autotune": {"options": s.options, "candidates_ms": [c["ms"] for c in (s.tuning or {}).get("candidates", [])]},
         "setup": {"make_taps_s": s.make_taps_s,
                   "taps_match_ge_0p99": float(np.mean(match >= 0.99)) if match is not None else None,
-                  "taps_match_median": float(np.median(match)) if match is not None else None},
+                  "taps_match_median": float(np.median(match)) if match is not None else None,
+                  "taps_cache": None if s.taps_cache_hit is None else ("hit" if s.taps_cache_hit else "stored")},
         "triggers_per_step": int(ntrig),
     }
     if s.learned_report is not None:
